@@ -1,0 +1,928 @@
+// TEST INFRASTRUCTURE ONLY -- the CPU oracle for segment-based mortar integration.
+//
+// A plain, slow, step-by-step CPU restatement of what Mayr & Popp, "Scalable
+// computational kernels for mortar finite element methods" (arXiv 2202.03933)
+// compute on the hot path.  Only the test-suite, the smoke check and the CPU
+// baseline of the benchmark call it; the product path never does.  It shares no
+// code with the CUDA library.
+//
+// What it follows:
+//   * Eq. (AnsatzDiscretization), Sec. 2.2: isoparametric quad4 / tri3 shape
+//     functions on slave and master surfaces.
+//   * Eq. (AnsatzDiscretizationLagrangeMult), Sec. 2.2: Lagrange multiplier
+//     shape functions, standard (Phi = N) or dual (biorthogonal to N, which
+//     makes D diagonal).
+//   * Eq. (DiscreteWeakFormInterfaceFlux), Sec. 2.2: D[j,k] = int Phi_j N_k and
+//     M[j,l] = int Phi_j (N_l o chi_h), both over the discrete slave surface.
+//   * Sec. 2.3: integration on a piecewise flat approximation of the slave
+//     surface (one auxiliary plane per slave element with point x_0 and normal
+//     n_0, Fig. 1), projection along n_0, mortar segments = clip polygons.
+//   * Algorithm 1: for each slave element and each nearby master element --
+//     project, clip, triangulate into cells, quadrature.
+//   * Sec. 3.3 / Algorithm 2: Cartesian bins covering the interface's bounding
+//     box, elements sorted into bins, neighbours of a bin searched.
+//   * Sec. 1 (consistent linearisation): derivatives of the weighted gap
+//     functional by forward-mode dual numbers (exact to rounding).
+//
+// Readings where the paper is silent (each also listed in the design notes):
+// Sutherland-Hodgman clipping of the master polygon by the slave window with an
+// absolute inside tolerance eps_in = clip_tol_rel * h_s^2; merge of consecutive
+// vertices closer than merge_tol_rel * h_s; discard of polygons with fewer than
+// 3 vertices or area < area_tol_rel * A_s; centroid-fan triangulation; the
+// 7-point degree-5 triangle rule; Newton back-projection from xi = 0 with
+// one extra update after |dxi|_inf <= tol; dual basis built on the whole slave
+// element with a 3x3 Gauss-Legendre rule (quad4) or the 7-point rule (tri3).
+//
+// Scalar type T is double, Dual<N> (forward-mode derivatives) or Counted (flop
+// counting: + - * / sqrt each count 1).  All branch decisions use val(x).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace orc {
+
+// --------------------------------------------------------------------------
+// scalar types
+// --------------------------------------------------------------------------
+inline double val(double x) { return x; }
+
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+  Dual() : v(0) { for (int i = 0; i < N; ++i) d[i] = 0; }
+  Dual(double x) : v(x) { for (int i = 0; i < N; ++i) d[i] = 0; }
+  static Dual seed(double x, int k) { Dual r(x); r.d[k] = 1.0; return r; }
+};
+template <int N> inline double val(const Dual<N>& x) { return x.v; }
+template <int N> inline Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r; r.v = a.v + b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i]; return r;
+}
+template <int N> inline Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r; r.v = a.v - b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i]; return r;
+}
+template <int N> inline Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> r; r.v = -a.v; for (int i = 0; i < N; ++i) r.d[i] = -a.d[i]; return r;
+}
+template <int N> inline Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r; r.v = a.v * b.v; for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r;
+}
+template <int N> inline Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r; r.v = a.v / b.v;
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+  return r;
+}
+template <int N> inline Dual<N> sqrt(const Dual<N>& a) {
+  Dual<N> r; r.v = std::sqrt(a.v); for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / (2.0 * r.v); return r;
+}
+template <int N> inline Dual<N>& operator+=(Dual<N>& a, const Dual<N>& b) { a = a + b; return a; }
+template <int N> inline Dual<N>& operator-=(Dual<N>& a, const Dual<N>& b) { a = a - b; return a; }
+template <int N> inline Dual<N> operator+(double a, const Dual<N>& b) { return Dual<N>(a) + b; }
+template <int N> inline Dual<N> operator+(const Dual<N>& a, double b) { return a + Dual<N>(b); }
+template <int N> inline Dual<N> operator-(double a, const Dual<N>& b) { return Dual<N>(a) - b; }
+template <int N> inline Dual<N> operator-(const Dual<N>& a, double b) { return a - Dual<N>(b); }
+template <int N> inline Dual<N> operator*(double a, const Dual<N>& b) {
+  Dual<N> r; r.v = a * b.v; for (int i = 0; i < N; ++i) r.d[i] = a * b.d[i]; return r;
+}
+template <int N> inline Dual<N> operator*(const Dual<N>& a, double b) { return b * a; }
+template <int N> inline Dual<N> operator/(const Dual<N>& a, double b) { return a / Dual<N>(b); }
+template <int N> inline Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
+
+// Flop-counting scalar: every + - * / sqrt on a Counted value counts one.
+static thread_local uint64_t g_flops = 0;
+struct Counted {
+  double v;
+  Counted() : v(0) {}
+  Counted(double x) : v(x) {}
+};
+inline double val(const Counted& x) { return x.v; }
+inline Counted operator+(Counted a, Counted b) { ++g_flops; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { ++g_flops; return Counted(a.v - b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+inline Counted operator*(Counted a, Counted b) { ++g_flops; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { ++g_flops; return Counted(a.v / b.v); }
+inline Counted sqrt(Counted a) { ++g_flops; return Counted(std::sqrt(a.v)); }
+inline Counted& operator+=(Counted& a, Counted b) { a = a + b; return a; }
+inline Counted& operator-=(Counted& a, Counted b) { a = a - b; return a; }
+inline Counted operator+(double a, Counted b) { return Counted(a) + b; }
+inline Counted operator+(Counted a, double b) { return a + Counted(b); }
+inline Counted operator-(double a, Counted b) { return Counted(a) - b; }
+inline Counted operator-(Counted a, double b) { return a - Counted(b); }
+inline Counted operator*(double a, Counted b) { return Counted(a) * b; }
+inline Counted operator*(Counted a, double b) { return a * Counted(b); }
+inline Counted operator/(Counted a, double b) { return a / Counted(b); }
+
+using std::sqrt;
+
+template <class T> inline T tabs(const T& x) { return val(x) < 0 ? -x : x; }
+
+// --------------------------------------------------------------------------
+// options and small geometry helpers
+// --------------------------------------------------------------------------
+struct Opts {
+  int32_t lm;            // 0 standard, 1 dual
+  int32_t d_domain;      // 0 element (D over the whole slave surface), 1 segment
+  int32_t tri_rule;      // 7 = 7-point degree-5 rule, 25 = collapsed 5x5 Gauss-Legendre
+  int32_t fan;           // 0 = centroid fan, 1 = ear fan from vertex 0
+  int32_t newton_max_iter;
+  int32_t n_threads;
+  double delta;          // search inflation
+  double newton_tol;
+  double clip_tol_rel, merge_tol_rel, area_tol_rel;
+};
+
+template <class T> struct V3 { T x, y, z; };
+template <class T> struct V2 { T u, v; };
+
+template <class T> inline V3<T> sub(const V3<T>& a, const V3<T>& b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T> inline T dot(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> inline V3<T> cross(const V3<T>& a, const V3<T>& b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <class T> inline V3<T> scale(const T& s, const V3<T>& a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class T> inline T cross2(const V2<T>& a, const V2<T>& b) { return a.u * b.v - a.v * b.u; }
+template <class T> inline V2<T> sub2(const V2<T>& a, const V2<T>& b) { return {a.u - b.u, a.v - b.v}; }
+
+// --------------------------------------------------------------------------
+// shape functions (Eq. AnsatzDiscretization)
+// quad4 corners (-1,-1), (1,-1), (1,1), (-1,1); tri3 N = (1-xi-eta, xi, eta)
+// --------------------------------------------------------------------------
+static const double kQuadCorner[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+
+template <class T> void shape(int nen, const T& xi, const T& eta, T N[4]) {
+  if (nen == 4) {
+    for (int a = 0; a < 4; ++a)
+      N[a] = 0.25 * (1.0 + kQuadCorner[a][0] * xi) * (1.0 + kQuadCorner[a][1] * eta);
+  } else {
+    N[0] = 1.0 - xi - eta; N[1] = xi; N[2] = eta; N[3] = T(0.0);
+  }
+}
+template <class T> void shape_deriv(int nen, const T& xi, const T& eta, T dN[4][2]) {
+  if (nen == 4) {
+    for (int a = 0; a < 4; ++a) {
+      dN[a][0] = 0.25 * kQuadCorner[a][0] * (1.0 + kQuadCorner[a][1] * eta);
+      dN[a][1] = 0.25 * kQuadCorner[a][1] * (1.0 + kQuadCorner[a][0] * xi);
+    }
+  } else {
+    dN[0][0] = T(-1.0); dN[0][1] = T(-1.0);
+    dN[1][0] = T(1.0);  dN[1][1] = T(0.0);
+    dN[2][0] = T(0.0);  dN[2][1] = T(1.0);
+    dN[3][0] = T(0.0);  dN[3][1] = T(0.0);
+  }
+}
+
+// --------------------------------------------------------------------------
+// quadrature rules
+// --------------------------------------------------------------------------
+struct TriPoint { double l0, l1, l2, w; };  // barycentric point, weight (sum 1)
+
+// 7-point degree-5 rule on a triangle (Radon 1948; Stroud T2:5-1): centroid
+// plus two 3-point orbits with abscissae built from sqrt(15).
+static std::vector<TriPoint> rule_tri7() {
+  const double r = std::sqrt(15.0);
+  const double a1 = (6.0 - r) / 21.0, b1 = (9.0 + 2.0 * r) / 21.0, w1 = (155.0 - r) / 1200.0;
+  const double a2 = (6.0 + r) / 21.0, b2 = (9.0 - 2.0 * r) / 21.0, w2 = (155.0 + r) / 1200.0;
+  return {{1.0 / 3, 1.0 / 3, 1.0 / 3, 9.0 / 40.0},
+          {a1, a1, b1, w1}, {a1, b1, a1, w1}, {b1, a1, a1, w1},
+          {a2, a2, b2, w2}, {a2, b2, a2, w2}, {b2, a2, a2, w2}};
+}
+
+// n-point Gauss-Legendre on [-1, 1]: Newton on P_n from the Chebyshev guess.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0); w.assign(n, 0.0);
+  const double pi = std::acos(-1.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) { double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) { double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Collapsed (Duffy) n x n Gauss-Legendre rule on a triangle: exact for
+// polynomials of total degree <= 2n - 2.  Used only to cross-check the
+// 7-point rule where integrands are polynomial.
+static std::vector<TriPoint> rule_tri_duffy(int n) {
+  std::vector<double> x, w;
+  gauss_legendre(n, x, w);
+  std::vector<TriPoint> out;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.5 * (x[i] + 1.0), t = 0.5 * (x[j] + 1.0);
+      double l1 = s, l2 = t * (1.0 - s);
+      // area of reference triangle is 1/2 -> normalised weight = 2 * (w/4) * (1-s)
+      out.push_back({1.0 - l1 - l2, l1, l2, 2.0 * 0.25 * w[i] * w[j] * (1.0 - s)});
+    }
+  return out;
+}
+
+// Element rule on the parameter domain: points (xi, eta) and weights summing
+// to the parameter-domain area (4 for quad4, 1/2 for tri3).
+struct ElemPoint { double xi, eta, w; };
+static std::vector<ElemPoint> element_rule(int nen) {
+  std::vector<ElemPoint> r;
+  if (nen == 4) {
+    const double g = std::sqrt(0.6);
+    const double p[3] = {-g, 0.0, g}, w[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) r.push_back({p[i], p[j], w[i] * w[j]});
+  } else {
+    for (const TriPoint& q : rule_tri7()) r.push_back({q.l1, q.l2, 0.5 * q.w});
+  }
+  return r;
+}
+
+// --------------------------------------------------------------------------
+// slave element data: auxiliary plane, dual basis, element D
+// --------------------------------------------------------------------------
+template <class T> struct SlaveData {
+  int nen;
+  V3<T> X[4];           // nodes
+  V3<T> x0, n0, t1, t2; // auxiliary plane and in-plane basis
+  T A[4][4];            // LM coefficients: Phi_a = sum_b A[a][b] N_b
+};
+
+template <class T>
+void slave_frame(SlaveData<T>& S) {
+  const int nen = S.nen;
+  T N[4], dN[4][2];
+  const double xc = nen == 4 ? 0.0 : 1.0 / 3.0;
+  shape<T>(nen, T(xc), T(xc), N);
+  shape_deriv<T>(nen, T(xc), T(xc), dN);
+  V3<T> x0{T(0.0), T(0.0), T(0.0)}, g1 = x0, g2 = x0;
+  for (int a = 0; a < nen; ++a) {
+    x0 = {x0.x + N[a] * S.X[a].x, x0.y + N[a] * S.X[a].y, x0.z + N[a] * S.X[a].z};
+    g1 = {g1.x + dN[a][0] * S.X[a].x, g1.y + dN[a][0] * S.X[a].y, g1.z + dN[a][0] * S.X[a].z};
+    g2 = {g2.x + dN[a][1] * S.X[a].x, g2.y + dN[a][1] * S.X[a].y, g2.z + dN[a][1] * S.X[a].z};
+  }
+  V3<T> n = cross(g1, g2);
+  T ln = sqrt(dot(n, n));
+  S.x0 = x0;
+  S.n0 = {n.x / ln, n.y / ln, n.z / ln};
+  V3<T> e = sub(S.X[1], S.X[0]);
+  T en = dot(e, S.n0);
+  V3<T> ep = sub(e, scale(en, S.n0));
+  T le = sqrt(dot(ep, ep));
+  S.t1 = {ep.x / le, ep.y / le, ep.z / le};
+  S.t2 = cross(S.n0, S.t1);
+}
+
+// Gaussian elimination with partial pivoting: solve K X = B (n x n, n rhs).
+template <class T>
+void solve_dense(int n, T K[4][4], T B[4][4]) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(val(K[r][c])) > std::fabs(val(K[piv][c]))) piv = r;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) { std::swap(K[c][k], K[piv][k]); std::swap(B[c][k], B[piv][k]); }
+    for (int r = c + 1; r < n; ++r) {
+      T f = K[r][c] / K[c][c];
+      for (int k = c; k < n; ++k) K[r][k] = K[r][k] - f * K[c][k];
+      for (int k = 0; k < n; ++k) B[r][k] = B[r][k] - f * B[c][k];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c)
+    for (int k = 0; k < n; ++k) {
+      T s = B[c][k];
+      for (int j = c + 1; j < n; ++j) s = s - K[c][j] * B[j][k];
+      B[c][k] = s / K[c][c];
+    }
+}
+
+template <class T>
+T surface_jacobian(int nen, const V3<T> X[4], const T dN[4][2]) {
+  V3<T> g1{T(0.0), T(0.0), T(0.0)}, g2 = g1;
+  for (int a = 0; a < nen; ++a) {
+    g1 = {g1.x + dN[a][0] * X[a].x, g1.y + dN[a][0] * X[a].y, g1.z + dN[a][0] * X[a].z};
+    g2 = {g2.x + dN[a][1] * X[a].x, g2.y + dN[a][1] * X[a].y, g2.z + dN[a][1] * X[a].z};
+  }
+  V3<T> n = cross(g1, g2);
+  return sqrt(dot(n, n));
+}
+
+// LM coefficients.  Standard: A = I.  Dual (biorthogonal, Sec. 2.2): with
+// Me[a][b] = int_e N_a N_b and Dh = diag(int_e N_a), A = Dh Me^{-1}, so that
+// int_e Phi_a N_b = delta_ab int_e N_b.
+template <class T>
+void lm_coefficients(SlaveData<T>& S, int lm) {
+  const int n = S.nen;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) S.A[a][b] = T(a == b ? 1.0 : 0.0);
+  if (lm == 0) return;
+  T Me[4][4], Dh[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) { Me[a][b] = T(0.0); Dh[a][b] = T(0.0); }
+  for (const ElemPoint& q : element_rule(n)) {
+    T N[4], dN[4][2];
+    shape<T>(n, T(q.xi), T(q.eta), N);
+    shape_deriv<T>(n, T(q.xi), T(q.eta), dN);
+    T wj = q.w * surface_jacobian<T>(n, S.X, dN);
+    for (int a = 0; a < n; ++a) {
+      Dh[a][a] = Dh[a][a] + wj * N[a];
+      for (int b = 0; b < n; ++b) Me[a][b] = Me[a][b] + wj * N[a] * N[b];
+    }
+  }
+  // Me symmetric: Me A^T = Dh  ->  solve for A^T column by column
+  solve_dense<T>(n, Me, Dh);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) S.A[a][b] = Dh[b][a];
+}
+
+// Element-domain D (Eq. DiscreteWeakFormInterfaceFlux integrated over the whole
+// slave element): De[a][b] = sum_q w_q J(xi_q) Phi_a(xi_q) N_b(xi_q).
+template <class T>
+void element_D(const SlaveData<T>& S, T De[4][4]) {
+  const int n = S.nen;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) De[a][b] = T(0.0);
+  for (const ElemPoint& q : element_rule(n)) {
+    T N[4], dN[4][2];
+    shape<T>(n, T(q.xi), T(q.eta), N);
+    shape_deriv<T>(n, T(q.xi), T(q.eta), dN);
+    T wj = q.w * surface_jacobian<T>(n, S.X, dN);
+    for (int a = 0; a < n; ++a) {
+      T phi = T(0.0);
+      for (int c = 0; c < n; ++c) phi = phi + S.A[a][c] * N[c];
+      for (int b = 0; b < n; ++b) De[a][b] = De[a][b] + wj * phi * N[b];
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// back-projection chi_h: solve sum_a N_a(xi) p_a = x in the auxiliary plane
+// --------------------------------------------------------------------------
+struct Stats {
+  int64_t pairs = 0, nonempty = 0, gauss_points = 0, newton_fail = 0, xi_out_of_range = 0,
+          clip_overflow = 0, cells = 0;
+};
+
+template <class T>
+void invert_map(int nen, const V2<T> p[4], const V2<T>& x, const Opts& o, T xi[2], Stats& st) {
+  if (nen == 3) {
+    V2<T> e1 = sub2(p[1], p[0]), e2 = sub2(p[2], p[0]), r = sub2(x, p[0]);
+    T det = e1.u * e2.v - e2.u * e1.v;
+    xi[0] = (r.u * e2.v - e2.u * r.v) / det;
+    xi[1] = (e1.u * r.v - r.u * e1.v) / det;
+  } else {
+    xi[0] = T(0.0); xi[1] = T(0.0);
+    bool converged = false, last = false;
+    for (int it = 0; it < o.newton_max_iter; ++it) {
+      T N[4], dN[4][2];
+      shape<T>(4, xi[0], xi[1], N);
+      shape_deriv<T>(4, xi[0], xi[1], dN);
+      T ru = -x.u, rv = -x.v, J00 = T(0.0), J01 = T(0.0), J10 = T(0.0), J11 = T(0.0);
+      for (int a = 0; a < 4; ++a) {
+        ru = ru + N[a] * p[a].u;
+        rv = rv + N[a] * p[a].v;
+        J00 = J00 + dN[a][0] * p[a].u; J01 = J01 + dN[a][1] * p[a].u;
+        J10 = J10 + dN[a][0] * p[a].v; J11 = J11 + dN[a][1] * p[a].v;
+      }
+      T det = J00 * J11 - J01 * J10;
+      T d0 = -(J11 * ru - J01 * rv) / det;
+      T d1 = -(J00 * rv - J10 * ru) / det;
+      xi[0] = xi[0] + d0;
+      xi[1] = xi[1] + d1;
+      if (last) { converged = true; break; }
+      if (std::max(std::fabs(val(d0)), std::fabs(val(d1))) <= o.newton_tol) last = true;
+    }
+    if (!converged) st.newton_fail++;
+  }
+  double lim = 1.0 + 1e-8;
+  if (nen == 4) {
+    if (std::fabs(val(xi[0])) > lim || std::fabs(val(xi[1])) > lim) st.xi_out_of_range++;
+  } else {
+    if (val(xi[0]) < -1e-8 || val(xi[1]) < -1e-8 || val(xi[0]) + val(xi[1]) > lim) st.xi_out_of_range++;
+  }
+}
+
+// --------------------------------------------------------------------------
+// one slave/master pair (Algorithm 1 body)
+// --------------------------------------------------------------------------
+template <class T> struct PairOut {
+  bool nonempty = false;
+  int nverts = 0;
+  T M[4][4];
+  T D[4][4];
+};
+
+template <class T>
+T polygon_signed_area2(const std::vector<V2<T>>& P) {  // twice the signed area
+  T s = T(0.0);
+  const size_t n = P.size();
+  for (size_t k = 0; k < n; ++k) s = s + cross2(P[k], P[(k + 1) % n]);
+  return s;
+}
+
+template <class T>
+void integrate_pair(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const Opts& o,
+                    PairOut<T>& out, Stats& st) {
+  const int nen_s = S.nen;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) { out.M[a][b] = T(0.0); out.D[a][b] = T(0.0); }
+  out.nonempty = false;
+  out.nverts = 0;
+  st.pairs++;
+
+  // tolerances from the real slave geometry (diameter, projected area)
+  double h_s = 0.0;
+  for (int a = 0; a < nen_s; ++a)
+    for (int b = a + 1; b < nen_s; ++b) {
+      double dx = val(S.X[a].x) - val(S.X[b].x), dy = val(S.X[a].y) - val(S.X[b].y),
+             dz = val(S.X[a].z) - val(S.X[b].z);
+      h_s = std::max(h_s, std::sqrt(dx * dx + dy * dy + dz * dz));
+    }
+  const double eps_in = o.clip_tol_rel * h_s * h_s;
+  const double eps_merge = o.merge_tol_rel * h_s;
+
+  // (1) project all nodes onto the auxiliary plane; in-plane coordinates
+  V2<T> ps[4], pm[4];
+  for (int a = 0; a < nen_s; ++a) {
+    V3<T> d = sub(S.X[a], S.x0);
+    ps[a] = {dot(d, S.t1), dot(d, S.t2)};
+  }
+  for (int l = 0; l < nen_m; ++l) {
+    V3<T> d = sub(Xm[l], S.x0);
+    pm[l] = {dot(d, S.t1), dot(d, S.t2)};
+  }
+  std::vector<V2<T>> win(ps, ps + nen_s), poly(pm, pm + nen_m);
+  T as2 = polygon_signed_area2(win);
+  if (val(as2) < 0) std::reverse(win.begin(), win.end());
+  if (val(polygon_signed_area2(poly)) < 0) std::reverse(poly.begin(), poly.end());
+  const double A_s = 0.5 * std::fabs(val(as2));
+  const double eps_area = o.area_tol_rel * A_s;
+
+  // (2) clip: Sutherland-Hodgman, master polygon against the slave window
+  for (int i = 0; i < nen_s && !poly.empty(); ++i) {
+    const V2<T>& a = win[i];
+    const V2<T>& b = win[(i + 1) % nen_s];
+    V2<T> e = sub2(b, a);
+    std::vector<V2<T>> next;
+    const size_t n = poly.size();
+    for (size_t k = 0; k < n; ++k) {
+      const V2<T>& p = poly[k];
+      const V2<T>& q = poly[(k + 1) % n];
+      T dp = cross2(e, sub2(p, a));
+      T dq = cross2(e, sub2(q, a));
+      double vp = val(dp), vq = val(dq);
+      if ((vp > eps_in && vq < -eps_in) || (vp < -eps_in && vq > eps_in)) {
+        T t = dp / (dp - dq);
+        next.push_back({p.u + t * (q.u - p.u), p.v + t * (q.v - p.v)});
+      }
+      if (vq >= -eps_in) next.push_back(q);
+    }
+    poly.swap(next);
+  }
+  if (poly.size() > 16) st.clip_overflow++;
+
+  // (3) merge consecutive (cyclic) vertices closer than eps_merge
+  std::vector<V2<T>> P;
+  const double em2 = eps_merge * eps_merge;
+  auto close = [&](const V2<T>& x, const V2<T>& y) {
+    double du = val(x.u) - val(y.u), dv = val(x.v) - val(y.v);
+    return du * du + dv * dv < em2;
+  };
+  for (const V2<T>& v : poly)
+    if (P.empty() || !close(v, P.back())) P.push_back(v);
+  while (P.size() > 1 && close(P.back(), P.front())) P.pop_back();
+  if (P.size() < 3) return;
+  if (0.5 * std::fabs(val(polygon_signed_area2(P))) < eps_area) return;
+  out.nonempty = true;
+  out.nverts = (int)P.size();
+  st.nonempty++;
+
+  // (4) triangulate into integration cells
+  struct Cell { V2<T> a, b, c; };
+  std::vector<Cell> cells;
+  const size_t nv = P.size();
+  if (nv == 3) {
+    cells.push_back({P[0], P[1], P[2]});
+  } else if (o.fan == 1) {
+    for (size_t i = 1; i + 1 < nv; ++i) cells.push_back({P[0], P[i], P[i + 1]});
+  } else {
+    V2<T> c{T(0.0), T(0.0)};
+    for (const V2<T>& v : P) { c.u = c.u + v.u; c.v = c.v + v.v; }
+    c.u = c.u / double(nv);
+    c.v = c.v / double(nv);
+    for (size_t i = 0; i < nv; ++i) cells.push_back({c, P[i], P[(i + 1) % nv]});
+  }
+  st.cells += (int64_t)cells.size();
+
+  // (5) quadrature on each cell with back-projection to both elements
+  const std::vector<TriPoint> rule = o.tri_rule == 25 ? rule_tri_duffy(5) : rule_tri7();
+  for (const Cell& C : cells) {
+    T ar2 = cross2(sub2(C.b, C.a), sub2(C.c, C.a));
+    T area = 0.5 * tabs(ar2);
+    for (const TriPoint& q : rule) {
+      V2<T> xg{q.l0 * C.a.u + q.l1 * C.b.u + q.l2 * C.c.u, q.l0 * C.a.v + q.l1 * C.b.v + q.l2 * C.c.v};
+      T W = q.w * area;
+      T xs[2], xm[2];
+      invert_map<T>(nen_s, ps, xg, o, xs, st);
+      invert_map<T>(nen_m, pm, xg, o, xm, st);
+      T Ns[4], Nm[4], Phi[4];
+      shape<T>(nen_s, xs[0], xs[1], Ns);
+      shape<T>(nen_m, xm[0], xm[1], Nm);
+      for (int a = 0; a < nen_s; ++a) {
+        Phi[a] = T(0.0);
+        for (int c = 0; c < nen_s; ++c) Phi[a] = Phi[a] + S.A[a][c] * Ns[c];
+      }
+      for (int a = 0; a < nen_s; ++a) {
+        T wp = W * Phi[a];
+        for (int l = 0; l < nen_m; ++l) out.M[a][l] = out.M[a][l] + wp * Nm[l];
+        if (o.d_domain == 1)
+          for (int b = 0; b < nen_s; ++b) out.D[a][b] = out.D[a][b] + wp * Ns[b];
+      }
+      st.gauss_points++;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// contact search
+// --------------------------------------------------------------------------
+struct Box { double lo[3], hi[3]; };
+
+static Box element_box(const double* X, const int32_t* conn, int nen, double delta) {
+  Box b;
+  for (int d = 0; d < 3; ++d) { b.lo[d] = X[3 * conn[0] + d]; b.hi[d] = b.lo[d]; }
+  for (int a = 1; a < nen; ++a)
+    for (int d = 0; d < 3; ++d) {
+      double x = X[3 * conn[a] + d];
+      b.lo[d] = std::min(b.lo[d], x);
+      b.hi[d] = std::max(b.hi[d], x);
+    }
+  for (int d = 0; d < 3; ++d) { b.lo[d] = b.lo[d] - delta; b.hi[d] = b.hi[d] + delta; }
+  return b;
+}
+
+static bool boxes_overlap(const Box& a, const Box& b) {
+  for (int d = 0; d < 3; ++d)
+    if (!(a.lo[d] <= b.hi[d] && b.lo[d] <= a.hi[d])) return false;
+  return true;
+}
+
+static double element_diameter(const double* X, const int32_t* conn, int nen) {
+  double h = 0.0;
+  for (int a = 0; a < nen; ++a)
+    for (int b = a + 1; b < nen; ++b) {
+      double s = 0.0;
+      for (int d = 0; d < 3; ++d) { double t = X[3 * conn[a] + d] - X[3 * conn[b] + d]; s += t * t; }
+      h = std::max(h, std::sqrt(s));
+    }
+  return h;
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+namespace {
+
+template <class T>
+void load_slave(SlaveData<T>& S, const double* xs, const int32_t* cs, int nen, int64_t e, int lm) {
+  S.nen = nen;
+  for (int a = 0; a < nen; ++a) {
+    const double* p = xs + 3 * (int64_t)cs[nen * e + a];
+    S.X[a] = {T(p[0]), T(p[1]), T(p[2])};
+  }
+  for (int a = nen; a < 4; ++a) S.X[a] = {T(0.0), T(0.0), T(0.0)};
+  slave_frame<T>(S);
+  lm_coefficients<T>(S, lm);
+}
+
+void add_stats(int64_t* out, const Stats& s) {
+  out[0] += s.pairs; out[1] += s.nonempty; out[2] += s.gauss_points; out[3] += s.newton_fail;
+  out[4] += s.xi_out_of_range; out[5] += s.clip_overflow; out[6] += s.cells;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Brute-force candidate search (the definition): all (s, m) whose
+// delta-inflated bounding boxes overlap, closed comparison, sorted by (s, m).
+// Returns the number of pairs; writes at most `cap` of them.
+int64_t oracle_search_bruteforce(const double* xs, int64_t Ns, const int32_t* cs, int64_t Es, int32_t nen_s,
+                                 const double* xm, int64_t Nm, const int32_t* cm, int64_t Em, int32_t nen_m,
+                                 double delta, int32_t* s_out, int32_t* m_out, int64_t cap) {
+  (void)Ns; (void)Nm;
+  std::vector<Box> bm(Em);
+  for (int64_t m = 0; m < Em; ++m) bm[m] = element_box(xm, cm + nen_m * m, nen_m, delta);
+  int64_t n = 0;
+  for (int64_t s = 0; s < Es; ++s) {
+    Box b = element_box(xs, cs + nen_s * s, nen_s, delta);
+    for (int64_t m = 0; m < Em; ++m)
+      if (boxes_overlap(b, bm[m])) {
+        if (n < cap) { s_out[n] = (int32_t)s; m_out[n] = (int32_t)m; }
+        ++n;
+      }
+  }
+  return n;
+}
+
+// Binned candidate search (Algorithm 2 on one device): Cartesian bins over the
+// interface's bounding box, expanded by the minimal bin size
+//   beta_min = (1 + 1e-9) * max element diameter (both sides) + 2 * delta;
+// n_d = max(1, floor(L_d / beta_min)) bins per direction.  Each element is
+// binned by its bounding-box centre; each slave element tests the master
+// elements of its own bin and its 26 neighbours.  Same result as brute force.
+int64_t oracle_search_binned(const double* xs, int64_t Ns, const int32_t* cs, int64_t Es, int32_t nen_s,
+                             const double* xm, int64_t Nm, const int32_t* cm, int64_t Em, int32_t nen_m,
+                             double delta, int32_t* s_out, int32_t* m_out, int64_t cap) {
+  double lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) { lo[d] = INFINITY; hi[d] = -INFINITY; }
+  for (int64_t i = 0; i < Ns; ++i)
+    for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], xs[3 * i + d]); hi[d] = std::max(hi[d], xs[3 * i + d]); }
+  for (int64_t i = 0; i < Nm; ++i)
+    for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], xm[3 * i + d]); hi[d] = std::max(hi[d], xm[3 * i + d]); }
+  double hmax = 0.0;
+  for (int64_t e = 0; e < Es; ++e) hmax = std::max(hmax, element_diameter(xs, cs + nen_s * e, nen_s));
+  for (int64_t e = 0; e < Em; ++e) hmax = std::max(hmax, element_diameter(xm, cm + nen_m * e, nen_m));
+  const double beta_min = (1.0 + 1e-9) * hmax + 2.0 * delta;
+  int64_t nb[3];
+  double beta[3], org[3];
+  for (int d = 0; d < 3; ++d) {
+    org[d] = lo[d] - beta_min;
+    double L = (hi[d] + beta_min) - org[d];
+    nb[d] = std::max<int64_t>(1, (int64_t)std::floor(L / beta_min));
+    beta[d] = L / (double)nb[d];
+  }
+  auto bin_of = [&](const Box& b, int64_t ijk[3]) {
+    for (int d = 0; d < 3; ++d) {
+      double c = 0.5 * (b.lo[d] + b.hi[d]);
+      int64_t i = (int64_t)std::floor((c - org[d]) / beta[d]);
+      ijk[d] = std::min<int64_t>(std::max<int64_t>(i, 0), nb[d] - 1);
+    }
+  };
+  std::vector<Box> bm(Em);
+  // sparse bins: sorted (bin id, element) list
+  std::vector<std::pair<int64_t, int32_t>> keyed(Em);
+  for (int64_t m = 0; m < Em; ++m) {
+    bm[m] = element_box(xm, cm + nen_m * m, nen_m, delta);
+    int64_t ijk[3];
+    bin_of(bm[m], ijk);
+    keyed[m] = {(ijk[2] * nb[1] + ijk[1]) * nb[0] + ijk[0], (int32_t)m};
+  }
+  std::sort(keyed.begin(), keyed.end());
+  int64_t n = 0;
+  std::vector<int32_t> found;
+  for (int64_t s = 0; s < Es; ++s) {
+    Box b = element_box(xs, cs + nen_s * s, nen_s, delta);
+    int64_t ijk[3];
+    bin_of(b, ijk);
+    found.clear();
+    for (int64_t dz = -1; dz <= 1; ++dz)
+      for (int64_t dy = -1; dy <= 1; ++dy)
+        for (int64_t dx = -1; dx <= 1; ++dx) {
+          int64_t i = ijk[0] + dx, j = ijk[1] + dy, k = ijk[2] + dz;
+          if (i < 0 || j < 0 || k < 0 || i >= nb[0] || j >= nb[1] || k >= nb[2]) continue;
+          int64_t key = (k * nb[1] + j) * nb[0] + i;
+          auto it = std::lower_bound(keyed.begin(), keyed.end(), std::make_pair(key, (int32_t)-1));
+          for (; it != keyed.end() && it->first == key; ++it)
+            if (boxes_overlap(b, bm[it->second])) found.push_back(it->second);
+        }
+    std::sort(found.begin(), found.end());
+    for (int32_t m : found) {
+      if (n < cap) { s_out[n] = (int32_t)s; m_out[n] = m; }
+      ++n;
+    }
+  }
+  return n;
+}
+
+// Per-slave-element LM coefficients A (Es x 16, row-major 4x4) and
+// element-domain D blocks (Es x 16).
+int oracle_element_blocks(const double* xs, const int32_t* cs, int64_t Es, int32_t nen_s, int32_t lm,
+                          double* A_out, double* De_out) {
+  for (int64_t e = 0; e < Es; ++e) {
+    SlaveData<double> S;
+    load_slave<double>(S, xs, cs, nen_s, e, lm);
+    double De[4][4];
+    element_D<double>(S, De);
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        if (A_out) A_out[16 * e + 4 * a + b] = S.A[a][b];
+        if (De_out) De_out[16 * e + 4 * a + b] = De[a][b];
+      }
+  }
+  return 0;
+}
+
+// Per-pair integration (Algorithm 1 body) for an explicit pair list.
+// M_out, D_out: P x 16 (row a = slave local node, column = master / slave
+// local node); nonempty: P bytes; stats: 7 counters
+// (pairs, nonempty, gauss points, newton failures, xi out of range,
+//  clip overflow, cells).
+int oracle_pair_blocks(const double* xs, const int32_t* cs, int32_t nen_s,
+                       const double* xm, const int32_t* cm, int32_t nen_m,
+                       const Opts* o, const int32_t* ps, const int32_t* pm, int64_t P,
+                       double* M_out, double* D_out, uint8_t* nonempty, int64_t* stats) {
+  for (int k = 0; k < 7; ++k) stats[k] = 0;
+  int nt = o->n_threads > 0 ? o->n_threads : 1;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+  {
+    Stats st;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 256)
+#endif
+    for (int64_t p = 0; p < P; ++p) {
+      SlaveData<double> S;
+      load_slave<double>(S, xs, cs, nen_s, ps[p], o->lm);
+      V3<double> Xm[4];
+      for (int l = 0; l < 4; ++l) Xm[l] = {0.0, 0.0, 0.0};
+      for (int l = 0; l < nen_m; ++l) {
+        const double* q = xm + 3 * (int64_t)cm[(int64_t)nen_m * pm[p] + l];
+        Xm[l] = {q[0], q[1], q[2]};
+      }
+      PairOut<double> r;
+      integrate_pair<double>(S, Xm, nen_m, *o, r, st);
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          M_out[16 * p + 4 * a + b] = r.M[a][b];
+          if (D_out) D_out[16 * p + 4 * a + b] = r.D[a][b];
+        }
+      nonempty[p] = r.nonempty ? 1 : 0;
+    }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+    add_stats(stats, st);
+  }
+  (void)nt;
+  return 0;
+}
+
+// Algorithmic flop count of the per-pair integration (+ - * / sqrt = 1 each)
+// for the given pairs, with the slave element data taken as given (the
+// auxiliary plane and LM coefficients are element-level precomputation).
+int64_t oracle_count_pair_flops(const double* xs, const int32_t* cs, int32_t nen_s,
+                                const double* xm, const int32_t* cm, int32_t nen_m,
+                                const Opts* o, const int32_t* ps, const int32_t* pm, int64_t P) {
+  uint64_t total = 0;
+  Stats st;
+  for (int64_t p = 0; p < P; ++p) {
+    SlaveData<double> Sd;
+    load_slave<double>(Sd, xs, cs, nen_s, ps[p], o->lm);
+    SlaveData<Counted> S;
+    S.nen = Sd.nen;
+    for (int a = 0; a < 4; ++a) {
+      S.X[a] = {Counted(Sd.X[a].x), Counted(Sd.X[a].y), Counted(Sd.X[a].z)};
+      for (int b = 0; b < 4; ++b) S.A[a][b] = Counted(Sd.A[a][b]);
+    }
+    S.x0 = {Sd.x0.x, Sd.x0.y, Sd.x0.z};
+    S.n0 = {Sd.n0.x, Sd.n0.y, Sd.n0.z};
+    S.t1 = {Sd.t1.x, Sd.t1.y, Sd.t1.z};
+    S.t2 = {Sd.t2.x, Sd.t2.y, Sd.t2.z};
+    V3<Counted> Xm[4];
+    for (int l = 0; l < 4; ++l) Xm[l] = {Counted(0.0), Counted(0.0), Counted(0.0)};
+    for (int l = 0; l < nen_m; ++l) {
+      const double* q = xm + 3 * (int64_t)cm[(int64_t)nen_m * pm[p] + l];
+      Xm[l] = {Counted(q[0]), Counted(q[1]), Counted(q[2])};
+    }
+    PairOut<Counted> r;
+    g_flops = 0;
+    integrate_pair<Counted>(S, Xm, nen_m, *o, r, st);
+    total += g_flops;
+  }
+  return (int64_t)total;
+}
+
+// Weighted gap functional J = sum_j lambda_j . ((D X_s)_j - (M X_m)_j) and its
+// gradient with respect to every slave and master coordinate, by forward-mode
+// dual numbers: Dual<24> over the 8 nodes of each pair, Dual<12> over the
+// slave nodes for the element-domain D.  Contributions are summed in pair
+// order, then element order.
+int oracle_weighted_gap_grad(const double* xs, int64_t Ns, const int32_t* cs, int64_t Es, int32_t nen_s,
+                             const double* xm, int64_t Nm, const int32_t* cm, int32_t nen_m,
+                             const Opts* o, const int32_t* ps, const int32_t* pm, int64_t P,
+                             const double* lambda, double* J_out, double* gs, double* gm) {
+  for (int64_t i = 0; i < 3 * Ns; ++i) gs[i] = 0.0;
+  for (int64_t i = 0; i < 3 * Nm; ++i) gm[i] = 0.0;
+  double J = 0.0;
+  typedef Dual<24> D24;
+  Stats st;
+  for (int64_t p = 0; p < P; ++p) {
+    const int32_t s = ps[p], m = pm[p];
+    SlaveData<D24> S;
+    S.nen = nen_s;
+    V3<D24> Xm[4];
+    for (int a = 0; a < 4; ++a) S.X[a] = {D24(0.0), D24(0.0), D24(0.0)};
+    for (int l = 0; l < 4; ++l) Xm[l] = {D24(0.0), D24(0.0), D24(0.0)};
+    for (int a = 0; a < nen_s; ++a) {
+      const double* q = xs + 3 * (int64_t)cs[(int64_t)nen_s * s + a];
+      S.X[a] = {D24::seed(q[0], 3 * a), D24::seed(q[1], 3 * a + 1), D24::seed(q[2], 3 * a + 2)};
+    }
+    for (int l = 0; l < nen_m; ++l) {
+      const double* q = xm + 3 * (int64_t)cm[(int64_t)nen_m * m + l];
+      Xm[l] = {D24::seed(q[0], 12 + 3 * l), D24::seed(q[1], 12 + 3 * l + 1), D24::seed(q[2], 12 + 3 * l + 2)};
+    }
+    slave_frame<D24>(S);
+    lm_coefficients<D24>(S, o->lm);
+    PairOut<D24> r;
+    integrate_pair<D24>(S, Xm, nen_m, *o, r, st);
+    if (!r.nonempty) continue;
+    D24 Jp(0.0);
+    for (int a = 0; a < nen_s; ++a) {
+      const double* lam = lambda + 3 * (int64_t)cs[(int64_t)nen_s * s + a];
+      for (int l = 0; l < nen_m; ++l) {
+        D24 g = lam[0] * Xm[l].x + lam[1] * Xm[l].y + lam[2] * Xm[l].z;
+        Jp = Jp - r.M[a][l] * g;
+      }
+      if (o->d_domain == 1)
+        for (int b = 0; b < nen_s; ++b) {
+          D24 g = lam[0] * S.X[b].x + lam[1] * S.X[b].y + lam[2] * S.X[b].z;
+          Jp = Jp + r.D[a][b] * g;
+        }
+    }
+    J += Jp.v;
+    for (int a = 0; a < nen_s; ++a)
+      for (int c = 0; c < 3; ++c) gs[3 * (int64_t)cs[(int64_t)nen_s * s + a] + c] += Jp.d[3 * a + c];
+    for (int l = 0; l < nen_m; ++l)
+      for (int c = 0; c < 3; ++c) gm[3 * (int64_t)cm[(int64_t)nen_m * m + l] + c] += Jp.d[12 + 3 * l + c];
+  }
+  if (o->d_domain == 0) {
+    typedef Dual<12> D12;
+    for (int64_t e = 0; e < Es; ++e) {
+      SlaveData<D12> S;
+      S.nen = nen_s;
+      for (int a = 0; a < 4; ++a) S.X[a] = {D12(0.0), D12(0.0), D12(0.0)};
+      for (int a = 0; a < nen_s; ++a) {
+        const double* q = xs + 3 * (int64_t)cs[(int64_t)nen_s * e + a];
+        S.X[a] = {D12::seed(q[0], 3 * a), D12::seed(q[1], 3 * a + 1), D12::seed(q[2], 3 * a + 2)};
+      }
+      slave_frame<D12>(S);
+      lm_coefficients<D12>(S, o->lm);
+      D12 De[4][4];
+      element_D<D12>(S, De);
+      D12 Je(0.0);
+      for (int a = 0; a < nen_s; ++a) {
+        const double* lam = lambda + 3 * (int64_t)cs[(int64_t)nen_s * e + a];
+        for (int b = 0; b < nen_s; ++b) {
+          D12 g = lam[0] * S.X[b].x + lam[1] * S.X[b].y + lam[2] * S.X[b].z;
+          Je = Je + De[a][b] * g;
+        }
+      }
+      J += Je.v;
+      for (int a = 0; a < nen_s; ++a)
+        for (int c = 0; c < 3; ++c) gs[3 * (int64_t)cs[(int64_t)nen_s * e + a] + c] += Je.d[3 * a + c];
+    }
+  }
+  *J_out = J;
+  return 0;
+}
+
+// Slave auxiliary planes (x0, n0, t1, t2) per element: Es x 12.
+int oracle_slave_frames(const double* xs, const int32_t* cs, int64_t Es, int32_t nen_s, double* out) {
+  for (int64_t e = 0; e < Es; ++e) {
+    SlaveData<double> S;
+    load_slave<double>(S, xs, cs, nen_s, e, 0);
+    double* o = out + 12 * e;
+    o[0] = S.x0.x; o[1] = S.x0.y; o[2] = S.x0.z;
+    o[3] = S.n0.x; o[4] = S.n0.y; o[5] = S.n0.z;
+    o[6] = S.t1.x; o[7] = S.t1.y; o[8] = S.t1.z;
+    o[9] = S.t2.x; o[10] = S.t2.y; o[11] = S.t2.z;
+  }
+  return 0;
+}
+
+// Quadrature rules as used above, for unit checks: which = 7 or 25.
+int oracle_tri_rule(int32_t which, double* out, int32_t cap) {
+  std::vector<TriPoint> r = which == 25 ? rule_tri_duffy(5) : rule_tri7();
+  int n = (int)r.size();
+  for (int i = 0; i < n && i < cap; ++i) {
+    out[4 * i] = r[i].l0; out[4 * i + 1] = r[i].l1; out[4 * i + 2] = r[i].l2; out[4 * i + 3] = r[i].w;
+  }
+  return n;
+}
+
+// Back-projection on its own (for the Newton pin): p: 4 (or 3) in-plane nodes
+// (u, v), x: query point; writes xi[2]; returns 1 if converged.
+int oracle_invert_map(int32_t nen, const double* p, const double* x, const Opts* o, double* xi) {
+  V2<double> q[4];
+  for (int a = 0; a < 4; ++a) q[a] = {0.0, 0.0};
+  for (int a = 0; a < nen; ++a) q[a] = {p[2 * a], p[2 * a + 1]};
+  Stats st;
+  invert_map<double>(nen, q, V2<double>{x[0], x[1]}, *o, xi, st);
+  return st.newton_fail == 0 ? 1 : 0;
+}
+
+}  // extern "C"
