@@ -1,0 +1,215 @@
+/*
+ * mortar.h -- C ABI of the GB300 mortar-integration library.
+ *
+ * Computes the mortar coupling matrices of a non-matching 3D surface interface
+ * (Mayr & Popp, arXiv 2202.03933, Sec. 2.2, Eq. DiscreteWeakFormInterfaceFlux):
+ *
+ *   D[j,k] = int_{Gamma_s,h} Phi_j N_k  dGamma      (slave x slave)
+ *   M[j,l] = int_{Gamma_s,h} Phi_j (N_l o chi_h) dGamma (slave x master)
+ *
+ * with isoparametric quad4/tri3 shape functions N (Eq. AnsatzDiscretization),
+ * standard or dual Lagrange-multiplier shape functions Phi
+ * (Eq. AnsatzDiscretizationLagrangeMult), segment-based integration on one
+ * auxiliary plane per slave element (Sec. 2.3, Algorithm 1: project, clip,
+ * triangulate, quadrature), a binned contact search (Sec. 3.3, Algorithm 2),
+ * and the gradient of the weighted gap functional
+ *   J = sum_j lambda_j . ( (D X_s)_j - (M X_m)_j )
+ * with respect to every slave and master nodal coordinate (the consistent
+ * linearisation the method needs, Sec. 1).
+ *
+ * Conventions shared by every call:
+ *  - All functions return an int status: MORTAR_OK (0) or a negative
+ *    mortar_status code; mortar_status_string() names it.
+ *  - Coordinates are FP64, row-major (N x 3): x0 y0 z0 x1 y1 z1 ...
+ *  - Connectivity is int32, row-major (E x nen), nen = 4 (quad4) or 3 (tri3),
+ *    0-based node ids, nodes counter-clockwise about the surface normal
+ *    (quad4 corners in the order of the parameter corners (-1,-1), (1,-1),
+ *    (1,1), (-1,1)).  Master elements may have either orientation.
+ *  - `on_device` = 1: the pointer is CUDA device memory of the current device;
+ *    0: host memory.  Input buffers are only read during the call; the
+ *    library keeps its own copies.  Output buffers belong to the caller.
+ *  - All device work runs on the stream given to mortar_create() (NULL = the
+ *    legacy default stream).  Calls returning host data synchronise that
+ *    stream only.
+ *  - The library owns the context, its device workspaces and any captured
+ *    CUDA graph; mortar_destroy() releases them.
+ *  - Calls on one context are not thread-safe; distinct contexts are
+ *    independent.
+ */
+#ifndef MORTAR_H
+#define MORTAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mortar_status {
+  MORTAR_OK = 0,
+  MORTAR_ERR_INVALID_ARG = -1, /* null pointer, bad element type, node id out of range, bad size */
+  MORTAR_ERR_DEGENERATE = -2,  /* zero-area, non-finite or inverted slave element */
+  MORTAR_ERR_NEWTON = -3,      /* a back-projection did not converge; results are still written */
+  MORTAR_ERR_CAPACITY = -4,    /* caller buffer too small; nothing written */
+  MORTAR_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+  MORTAR_ERR_OOM = -6,         /* device allocation failed */
+  MORTAR_ERR_TIMEOUT = -7,     /* a bounded device loop hit its cap */
+  MORTAR_ERR_STATE = -8,       /* call out of order (e.g. copy before evaluate) */
+  MORTAR_ERR_NOT_BUILT = -9    /* functionality not available in this build */
+} mortar_status;
+
+enum { MORTAR_TRI3 = 3, MORTAR_QUAD4 = 4 };
+enum { MORTAR_LM_STANDARD = 0, MORTAR_LM_DUAL = 1 };
+/* Domain of D: ELEMENT integrates D over the whole slave element (the
+ * definition in Eq. DiscreteWeakFormInterfaceFlux, so sum(D) is the slave
+ * area); SEGMENT integrates it over the clip polygons inside the pair loop of
+ * Algorithm 1 (then sum(D) = sum(M)). */
+enum { MORTAR_D_ELEMENT = 0, MORTAR_D_SEGMENT = 1 };
+enum { MORTAR_MATRIX_D = 0, MORTAR_MATRIX_M = 1 };
+
+typedef struct mortar_options {
+  int32_t lm;               /* MORTAR_LM_STANDARD or MORTAR_LM_DUAL */
+  int32_t d_domain;         /* MORTAR_D_ELEMENT (default) or MORTAR_D_SEGMENT */
+  int32_t newton_max_iter;  /* back-projection Newton cap (20) */
+  int32_t block_size;       /* threads per block of the pair kernels, 0 = tuned default */
+  double search_inflation;  /* delta: absolute AABB inflation of the search (1e-9) */
+  double newton_tol;        /* stop when |dxi|_inf <= tol, then one more update (1e-14) */
+  double clip_tol_rel;      /* inside tolerance eps_in = clip_tol_rel * h_s^2 (1e-12) */
+  double merge_tol_rel;     /* vertex merge distance = merge_tol_rel * h_s (1e-10) */
+  double area_tol_rel;      /* discard polygons below area_tol_rel * slave area (1e-14) */
+} mortar_options;
+
+typedef struct mortar_stats {
+  int64_t n_interfaces;
+  int64_t n_pairs;          /* candidate pairs from the search */
+  int64_t n_nonempty;       /* pairs with a non-empty clip polygon */
+  int64_t n_gauss_points;
+  int64_t n_cells;
+  int64_t n_newton_fail;
+  int64_t n_xi_out_of_range;
+  int64_t n_clip_overflow;
+  int64_t nnz_D, nnz_M;
+  int64_t n_bins;
+  int64_t reruns;           /* capacity-driven re-executions of the last run */
+  float ms_search, ms_integrate, ms_assemble, ms_adjoint, ms_total; /* last run, CUDA events */
+} mortar_stats;
+
+typedef struct mortar_ctx mortar_ctx;
+
+/* Fill `o` with the defaults listed above. */
+int mortar_default_options(mortar_options* o);
+
+/* Create a context.  `stream` is a cudaStream_t (NULL = default stream) that
+ * every later call on this context uses.  Uses the current CUDA device. */
+int mortar_create(mortar_ctx** ctx, const mortar_options* o, void* stream);
+
+/* Release the context, its workspaces and graphs.  NULL is ignored. */
+void mortar_destroy(mortar_ctx* ctx);
+
+/* Define one interface (Eq. AnsatzDiscretization: slave and master node
+ * coordinates and connectivity).  type_s / type_m: MORTAR_QUAD4 or
+ * MORTAR_TRI3.  Copies the data; node ids are checked against the node
+ * counts (MORTAR_ERR_INVALID_ARG).  Empty meshes are allowed. */
+int mortar_set_interface(mortar_ctx* ctx,
+                         const double* xs, int64_t n_slave_nodes,
+                         const int32_t* conn_s, int64_t n_slave_elems, int32_t type_s,
+                         const double* xm, int64_t n_master_nodes,
+                         const int32_t* conn_m, int64_t n_master_elems, int32_t type_m,
+                         int32_t on_device);
+
+/* Define a batch of independent interfaces, integrated together.  The
+ * arrays are the interfaces' arrays concatenated; offsets have
+ * n_interfaces + 1 entries (node and element offsets of each side), and
+ * connectivity holds GLOBAL node ids into the concatenated node arrays, each
+ * element referencing only nodes of its own interface.  Pairs never cross
+ * interfaces.  D and M of the batch are block diagonal over interfaces. */
+int mortar_set_batch(mortar_ctx* ctx, int32_t n_interfaces,
+                     const int64_t* slave_node_off, const int64_t* slave_elem_off,
+                     const int64_t* master_node_off, const int64_t* master_elem_off,
+                     const double* xs, const int32_t* conn_s, int32_t type_s,
+                     const double* xm, const int32_t* conn_m, int32_t type_m,
+                     int32_t on_device);
+
+/* Replace node coordinates (same topology), e.g. for a moved configuration.
+ * Either pointer may be NULL to keep that side. */
+int mortar_set_coordinates(mortar_ctx* ctx, const double* xs, const double* xm, int32_t on_device);
+
+/* Contact search (Algorithm 2 on one device): element bounding boxes, uniform
+ * bins per interface, candidate pairs (s, m) whose search_inflation-inflated
+ * boxes overlap, sorted by (s, m).  Writes the pair count. */
+int mortar_search(mortar_ctx* ctx, int64_t* n_pairs);
+
+/* Copy the candidate pairs of the last search (slave element, master element
+ * ids).  capacity < n_pairs -> MORTAR_ERR_CAPACITY. */
+int mortar_get_pairs(mortar_ctx* ctx, int32_t* s_ids, int32_t* m_ids, int64_t capacity,
+                     int32_t on_device);
+
+/* Segment-based integration (Algorithm 1) over all pairs and deterministic
+ * assembly of D and M into CSR.  Runs the search first if the coordinates
+ * changed since the last search.  Returns MORTAR_ERR_NEWTON (results still
+ * valid) if a back-projection failed to converge. */
+int mortar_evaluate(mortar_ctx* ctx);
+
+/* Size of D (which = MORTAR_MATRIX_D: n_slave_nodes^2) or M
+ * (MORTAR_MATRIX_M: n_slave_nodes x n_master_nodes) of the last evaluation. */
+int mortar_csr_size(mortar_ctx* ctx, int32_t which, int64_t* nrows, int64_t* ncols, int64_t* nnz);
+
+/* Copy a CSR matrix: rowptr (nrows + 1, int64), colidx (nnz, int32, sorted
+ * within each row), vals (nnz, FP64).  capacity_nnz < nnz ->
+ * MORTAR_ERR_CAPACITY.  A structural entry exists iff some non-empty pair
+ * (or, for element-domain D, some slave element) touches it. */
+int mortar_csr_copy(mortar_ctx* ctx, int32_t which, int64_t* rowptr, int32_t* colidx, double* vals,
+                    int64_t capacity_nnz, int32_t on_device);
+
+/* Per-pair blocks of the last evaluation, in pair order: M_blocks and D_blocks
+ * are (n_pairs x 16) FP64, row a = slave local node, column = master (or
+ * slave) local node, 4x4 padded with zeros; nonempty is n_pairs bytes.
+ * D_blocks is filled only in segment mode (may be NULL). */
+int mortar_get_pair_blocks(mortar_ctx* ctx, double* M_blocks, double* D_blocks, uint8_t* nonempty,
+                           int64_t capacity, int32_t on_device);
+
+/* Weighted gap J = sum_j lambda_j . ((D X_s)_j - (M X_m)_j) and its gradient
+ * (adjoint kernel: per-pair forward recomputation, reverse sweep through
+ * quadrature, back-projection, triangulation, clipping, projection and the
+ * dual basis).  lambda: n_slave_nodes x 3.  grad_xs: n_slave_nodes x 3,
+ * grad_xm: n_master_nodes x 3 (overwritten).  J: one double.  Uses the pairs
+ * of the last evaluation (evaluates first if needed). */
+int mortar_weighted_gap_grad(mortar_ctx* ctx, const double* lambda, double* J,
+                             double* grad_xs, double* grad_xm, int32_t on_device);
+
+/* Run search + integration + assembly (+ the adjoint if lambda != NULL) as
+ * one stream-ordered sequence with device-side sizes, captured once into a
+ * CUDA graph and replayed on later calls.  Buffers grow and the graph is
+ * re-captured when a capacity is exceeded.  Results are read with the calls
+ * above (mortar_csr_copy, mortar_get_gradient). */
+int mortar_run_graph(mortar_ctx* ctx, const double* lambda, int32_t on_device);
+
+/* Gradient and J of the last adjoint run (mortar_run_graph with lambda). */
+int mortar_get_gradient(mortar_ctx* ctx, double* J, double* grad_xs, double* grad_xm, int32_t on_device);
+
+/* Counters and phase timings of the last run. */
+int mortar_get_stats(mortar_ctx* ctx, mortar_stats* out);
+
+/* Enable (1) / disable (0) CUDA-event phase timing (default 0). */
+int mortar_set_timing(mortar_ctx* ctx, int32_t enabled);
+
+/* Set the pair kernels' block size and pairs per work item (0 = defaults);
+ * used by the autotuner. */
+int mortar_set_launch(mortar_ctx* ctx, int32_t block_size, int32_t chunk_pairs);
+
+/* Name of a status code. */
+const char* mortar_status_string(int status);
+
+/* Measurement utility, not part of the method: runs a chain of FP64 fused
+ * multiply-adds (`iters` per thread, 8 independent chains) over `blocks` x
+ * `threads` threads on `stream` and writes one value per thread to `sink`
+ * (device, blocks*threads doubles) so that nothing is optimised away.
+ * active_lanes (1..32) masks lanes per warp to test divergence cost. */
+int mortar_probe_dfma(void* stream, int32_t blocks, int32_t threads, int64_t iters,
+                      int32_t active_lanes, double* sink);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MORTAR_H */

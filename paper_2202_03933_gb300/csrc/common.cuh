@@ -1,0 +1,209 @@
+// Shared device-side definitions of the GB300 mortar library (sm_103a).
+//
+// Geometry conventions (Mayr & Popp, arXiv 2202.03933, Sec. 2.2-2.3):
+//   quad4 shape functions N_a(xi) = 1/4 (1 + xi xi_a)(1 + eta eta_a) with
+//   corners (-1,-1), (1,-1), (1,1), (-1,1); tri3 N = (1 - xi - eta, xi, eta).
+//   One auxiliary plane per slave element: point x0 = x(xi_c), unit normal n0
+//   at xi_c (Fig. 1), in-plane basis t1 = normalised projected first edge,
+//   t2 = n0 x t1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mortar {
+
+constexpr int kMaxPoly = 16;   // polygon vertex cap; convex quad vs quad needs <= 8
+constexpr int kMaxRow = 256;   // CSR entries gathered per row before the slow path
+
+// Per-run numeric parameters, passed by value to the kernels.
+struct RunParams {
+  int32_t lm;
+  int32_t d_domain;
+  int32_t newton_max_iter;
+  int32_t pad;
+  double newton_tol;
+  double clip_tol_rel;
+  double merge_tol_rel;
+  double area_tol_rel;
+  double delta;
+};
+
+// Slave element record (FP64 words).  Written once per evaluation by the
+// precompute kernel, read by every pair of that element.
+enum SlaveRec : int {
+  SR_X0 = 0,      // x0 (3)
+  SR_T1 = 3,      // t1 (3)
+  SR_T2 = 6,      // t2 (3)
+  SR_N0 = 9,      // n0 (3)
+  SR_C = 12,      // bilinear coefficients of the projected slave element c0..c3 (8)
+  SR_PS = 20,     // projected slave nodes in window (CCW) order (8)
+  SR_EPSIN = 28,  // inside tolerance
+  SR_EPSM2 = 29,  // squared merge distance
+  SR_EPSA = 30,   // area threshold
+  SR_REV = 31,    // 1 if the window order is the reverse of the node order
+  SR_A = 32,      // LM coefficients A[a][b] (16)
+  SR_STRIDE = 48
+};
+
+// Device-side counters and sizes of one run (read back once per run).
+struct DevStatus {
+  unsigned long long n_pairs;
+  unsigned long long nnz_D;
+  unsigned long long nnz_M;
+  unsigned long long n_bins;
+  unsigned long long nonempty;
+  unsigned long long gauss_points;
+  unsigned long long cells;
+  unsigned long long newton_fail;
+  unsigned long long xi_oor;
+  unsigned long long clip_overflow;
+  unsigned long long over_pairs;   // pair buffer too small (needed size in n_pairs)
+  unsigned long long over_nnz;     // CSR buffer too small
+  unsigned long long over_bins;    // bin table too small
+  unsigned long long degenerate;
+  unsigned long long timeout;
+  unsigned long long row_slow;     // rows assembled by the slow (unbuffered) path
+  unsigned long long over_mlist;   // master pair-list buffer too small
+  unsigned long long work_ctr;     // work counter of the persistent integration kernel
+  unsigned long long work_ctr2;    // work counter of the persistent adjoint kernel
+  double J;
+};
+
+// Per-interface search grid.
+struct GridParams {
+  double org[3];
+  double beta[3];
+  int32_t nb[3];
+  int32_t pad;
+  int64_t bin_off;   // first bin of this interface in the global bin table
+  int64_t n_bins;
+};
+
+// ---------------------------------------------------------------------------
+// small math
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cross2(double au, double av, double bu, double bv) {
+  return au * bv - av * bu;
+}
+
+template <int NEN>
+__device__ __forceinline__ void shape_fn(double xi, double eta, double N[4]) {
+  if constexpr (NEN == 4) {
+    const double a = 1.0 - xi, b = 1.0 + xi, c = 1.0 - eta, d = 1.0 + eta;
+    N[0] = 0.25 * a * c;
+    N[1] = 0.25 * b * c;
+    N[2] = 0.25 * b * d;
+    N[3] = 0.25 * a * d;
+  } else {
+    N[0] = 1.0 - xi - eta;
+    N[1] = xi;
+    N[2] = eta;
+    N[3] = 0.0;
+  }
+}
+
+// Bilinear (quad4) or affine (tri3) map of an element in the auxiliary plane:
+//   x(xi, eta) = c0 + c1 xi + c2 eta + c3 xi eta    (c3 = 0 for tri3)
+struct PlaneMap {
+  double c0u, c0v, c1u, c1v, c2u, c2v, c3u, c3v;
+};
+
+template <int NEN>
+__device__ __forceinline__ PlaneMap plane_map(const double* pu, const double* pv) {
+  PlaneMap m;
+  if constexpr (NEN == 4) {
+    m.c0u = 0.25 * ((pu[0] + pu[1]) + (pu[2] + pu[3]));
+    m.c0v = 0.25 * ((pv[0] + pv[1]) + (pv[2] + pv[3]));
+    m.c1u = 0.25 * ((pu[1] - pu[0]) + (pu[2] - pu[3]));
+    m.c1v = 0.25 * ((pv[1] - pv[0]) + (pv[2] - pv[3]));
+    m.c2u = 0.25 * ((pu[2] - pu[1]) + (pu[3] - pu[0]));
+    m.c2v = 0.25 * ((pv[2] - pv[1]) + (pv[3] - pv[0]));
+    m.c3u = 0.25 * ((pu[0] - pu[1]) + (pu[2] - pu[3]));
+    m.c3v = 0.25 * ((pv[0] - pv[1]) + (pv[2] - pv[3]));
+  } else {
+    m.c0u = pu[0];
+    m.c0v = pv[0];
+    m.c1u = pu[1] - pu[0];
+    m.c1v = pv[1] - pv[0];
+    m.c2u = pu[2] - pu[0];
+    m.c2v = pv[2] - pv[0];
+    m.c3u = 0.0;
+    m.c3v = 0.0;
+  }
+  return m;
+}
+
+// Back-projection chi_h: solve x(xi) = (xu, xv).  quad4: Newton from xi = 0,
+// stop once |dxi|_inf <= tol and apply one more update; tri3: one linear solve.
+// Returns false if Newton did not converge within max_iter updates.
+template <int NEN>
+__device__ __forceinline__ bool invert_plane_map(const PlaneMap& m, double xu, double xv, double tol,
+                                                 int max_iter, double& xi, double& eta) {
+  if constexpr (NEN == 3) {
+    const double ru = xu - m.c0u, rv = xv - m.c0v;
+    const double det = m.c1u * m.c2v - m.c2u * m.c1v;
+    const double inv = 1.0 / det;
+    xi = (ru * m.c2v - m.c2u * rv) * inv;
+    eta = (m.c1u * rv - ru * m.c1v) * inv;
+    return true;
+  } else {
+    xi = 0.0;
+    eta = 0.0;
+    bool last = false;
+    for (int it = 0; it < max_iter; ++it) {
+      const double ru = m.c0u + m.c1u * xi + m.c2u * eta + m.c3u * xi * eta - xu;
+      const double rv = m.c0v + m.c1v * xi + m.c2v * eta + m.c3v * xi * eta - xv;
+      const double j00 = m.c1u + m.c3u * eta, j01 = m.c2u + m.c3u * xi;
+      const double j10 = m.c1v + m.c3v * eta, j11 = m.c2v + m.c3v * xi;
+      const double inv = 1.0 / (j00 * j11 - j01 * j10);
+      const double d0 = -(j11 * ru - j01 * rv) * inv;
+      const double d1 = -(j00 * rv - j10 * ru) * inv;
+      xi += d0;
+      eta += d1;
+      if (last) return true;
+      if (fmax(fabs(d0), fabs(d1)) <= tol) last = true;
+    }
+    return false;
+  }
+}
+
+template <int NEN>
+__device__ __forceinline__ bool xi_out_of_range(double xi, double eta) {
+  const double lim = 1.0 + 1e-8;
+  if constexpr (NEN == 4) {
+    return fabs(xi) > lim || fabs(eta) > lim;
+  } else {
+    return xi < -1e-8 || eta < -1e-8 || xi + eta > lim;
+  }
+}
+
+// 7-point degree-5 triangle rule (Radon; Stroud T2:5-1): barycentric
+// (l0, l1, l2) and weights summing to one.
+struct Tri7 {
+  static constexpr double a1 = 0.10128650732345633, b1 = 0.7974269853530872, w1 = 0.12593918054482717;
+  static constexpr double a2 = 0.47014206410511505, b2 = 0.05971587178976981, w2 = 0.13239415278850616;
+  static constexpr double w0 = 0.225;
+};
+
+__device__ __forceinline__ void tri7_point(int q, double& l1, double& l2, double& w) {
+  // point 0: centroid; 1-3: orbit (a1,a1,b1); 4-6: orbit (a2,a2,b2);
+  // (l0, l1, l2) = (a,a,b), (a,b,a), (b,a,a)
+  switch (q) {
+    case 0: l1 = 1.0 / 3.0; l2 = 1.0 / 3.0; w = Tri7::w0; break;
+    case 1: l1 = Tri7::a1; l2 = Tri7::b1; w = Tri7::w1; break;
+    case 2: l1 = Tri7::b1; l2 = Tri7::a1; w = Tri7::w1; break;
+    case 3: l1 = Tri7::a1; l2 = Tri7::a1; w = Tri7::w1; break;
+    case 4: l1 = Tri7::a2; l2 = Tri7::b2; w = Tri7::w2; break;
+    case 5: l1 = Tri7::b2; l2 = Tri7::a2; w = Tri7::w2; break;
+    default: l1 = Tri7::a2; l2 = Tri7::a2; w = Tri7::w2; break;
+  }
+}
+
+// Block-wide sum of an unsigned counter, one atomic per block.
+__device__ __forceinline__ void block_count_add(unsigned long long* dst, unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+}  // namespace mortar

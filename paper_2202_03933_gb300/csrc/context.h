@@ -1,0 +1,133 @@
+// Host-side context of the mortar library: device workspaces, sizes, and the
+// launchers of every kernel (implemented in the k_*.cu translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/mortar.h"
+#include "common.cuh"
+
+namespace mortar {
+
+// Grow-only device buffer.  Contents are not preserved on growth.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+int buf_reserve(DevBuf& b, size_t bytes);   // MORTAR_OK or MORTAR_ERR_OOM / CUDA
+void buf_free(DevBuf& b);
+
+struct Chunk {          // contiguous element range of one interface and side
+  int32_t iface;
+  int32_t side;         // 0 slave, 1 master
+  int64_t begin, end;
+};
+
+}  // namespace mortar
+
+struct mortar_ctx {
+  mortar_options opt{};
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  int device = 0;
+  int n_sm = 0;
+  bool timing = false;
+  int32_t block_size = 0;     // pair kernels (0 = default)
+  int32_t chunk_pairs = 0;    // pairs per work item (0 = default)
+
+  // ---- interface definition
+  bool have_interface = false;
+  int32_t n_if = 0;
+  int32_t nen_s = 4, nen_m = 4;
+  int64_t Ns = 0, Es = 0, Nm = 0, Em = 0;
+  std::vector<int64_t> h_sn_off, h_se_off, h_mn_off, h_me_off;
+  mortar::DevBuf xs, xm, conn_s, conn_m;
+  mortar::DevBuf se_off, me_off;            // element offsets per interface (int64, n_if+1)
+  mortar::DevBuf elem_if_s;                 // interface id of each slave element (int32)
+  mortar::DevBuf chunks;                    // mortar::Chunk[n_chunks]
+  mortar::DevBuf chunk_ptr;                 // per interface: first chunk (int32, n_if+1)
+  int64_t n_chunks = 0;
+  mortar::DevBuf bin_cap_off;               // per interface bin capacity offsets (int64, n_if+1)
+  int64_t bin_cap = 0;
+
+  // topology: node -> (element, local index) adjacency, sorted by element
+  mortar::DevBuf n2e_s_ptr, n2e_s_ent, n2e_m_ptr, n2e_m_ent;
+
+  // ---- per-evaluation workspaces
+  mortar::DevBuf srec, De, box_s, box_m;    // slave records, element D, boxes (lo3 hi3 h pad)
+  mortar::DevBuf chunk_red;                 // per chunk: lo3 hi3 hmax pad
+  mortar::DevBuf grid;                      // GridParams per interface
+  mortar::DevBuf mkey;                      // master bin key (int64)
+  mortar::DevBuf bin_cnt, bin_start;        // int32 counts, int64 starts (bin_cap + 1)
+  mortar::DevBuf bin_elems;                 // int32 (Em)
+  mortar::DevBuf cand_cnt, pair_off;        // int32 (Es), int64 (Es + 1)
+  mortar::DevBuf pairs_s, pairs_m;          // int32 (pair_cap)
+  int64_t pair_cap = 0;
+  mortar::DevBuf Mblk, Dblk, flag;          // FP64 16/pair, uint8/pair
+  mortar::DevBuf row_cnt;                   // int32 (max(Ns, Nm))
+  mortar::DevBuf rowptr_D, col_D, val_D;
+  mortar::DevBuf rowptr_M, col_M, val_M;
+  int64_t nnz_cap_D = 0, nnz_cap_M = 0;
+  mortar::DevBuf scan_tmp;                  // block partials of the scans
+
+  // ---- adjoint workspaces
+  mortar::DevBuf lambda;                    // Ns x 3
+  mortar::DevBuf gs_pair, gm_pair, abar_pair, J_pair;   // per pair
+  mortar::DevBuf ge_elem;                   // per slave element 4x3 + J
+  mortar::DevBuf mp_cnt, mp_off, mp_list;   // master element -> pairs
+  mortar::DevBuf grad_s, grad_m;            // Ns x 3, Nm x 3
+  mortar::DevBuf J_part;                    // block partial sums of J
+
+  // ---- status / bookkeeping
+  mortar::DevBuf dstat;                     // mortar::DevStatus
+  mortar::DevStatus* hstat = nullptr;       // pinned host copy
+  bool search_valid = false;
+  bool eval_valid = false;
+  bool grad_valid = false;
+  int64_t n_pairs = 0, nnz_D = 0, nnz_M = 0;
+  mortar_stats stats{};
+  cudaEvent_t ev[8] = {};
+
+  // ---- graph
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_with_adjoint = false;
+};
+
+namespace mortar {
+
+// ---- launchers (all stream-ordered on ctx->stream) ----
+// k_scan.cu
+int64_t scan_temp_words(int64_t n_max);
+void launch_exclusive_scan_i32(const int32_t* in, int64_t* out, const int64_t* n_dev, int64_t n_max,
+                               int64_t* tmp, cudaStream_t st);
+
+// k_precompute.cu
+void launch_slave_precompute(mortar_ctx* c, const RunParams& rp);
+void launch_master_boxes(mortar_ctx* c, const RunParams& rp);
+void launch_grid_params(mortar_ctx* c, const RunParams& rp);
+
+// k_search.cu
+void launch_bin_masters(mortar_ctx* c);
+void launch_candidates(mortar_ctx* c);
+
+// k_integrate.cu
+void launch_integrate(mortar_ctx* c, const RunParams& rp);
+
+// k_assemble.cu
+void launch_topology(mortar_ctx* c);
+void launch_assemble(mortar_ctx* c, const RunParams& rp);
+void launch_finalize_status(mortar_ctx* c);
+
+// k_adjoint.cu
+int prepare_adjoint_buffers(mortar_ctx* c);   // sizes per-pair adjoint buffers from n_pairs
+void launch_adjoint(mortar_ctx* c, const RunParams& rp);
+
+RunParams run_params(const mortar_ctx* c);
+
+}  // namespace mortar

@@ -1,0 +1,836 @@
+// Adjoint (reverse-mode gradient) of the weighted gap functional
+//     J = sum_j lambda_j . ( (D X_s)_j - (M X_m)_j )
+// with respect to every slave and master nodal coordinate -- the consistent
+// linearisation of the mortar terms (Sec. 1 of arXiv 2202.03933).
+//
+// Per pair, J_pair = sum over quadrature points of W * Lh . q with
+//   Lh = sum_c Lambda_c N_c(xi_s),  Lambda_c = sum_a A[a][c] lambda_a,
+//   q  = [segment D] x_s(xi_s) - x_m(xi_m)   (x_s, x_m: isoparametric
+//        interpolation of the ORIGINAL 3D nodes).
+// The kernel recomputes the pair's geometry (nothing is stored between the
+// forward and the adjoint) while recording the Sutherland-Hodgman stages, then
+// runs the reverse sweep:
+//   quadrature point -> back-projection (implicit function theorem at the
+//   converged xi: dxi = J^-1 (dx - d map)) -> cell vertices and cell area ->
+//   centroid fan -> merge (selection) -> clipping stages (vertex copies and
+//   edge intersections x = p + t (q - p), t = d_p / (d_p - d_q)) -> in-plane
+//   coordinates u = (X - x0).t1, v = (X - x0).t2 -> auxiliary plane (x0, n0,
+//   t1, t2 as functions of the slave nodes).
+// The LM coefficients A (dual basis, A = Dh Me^-1) depend on the slave
+// element only: each pair emits dJ/dA, a per-element kernel sums it over the
+// element's pairs, adds the element-domain D term and propagates both through
+// A and the element integrals to the slave nodes.  Per-pair and per-element
+// gradient blocks are then gathered per node in a fixed order (no floating
+// point atomics), and J is reduced with a fixed tree: results are bitwise
+// reproducible.
+#include <algorithm>
+
+#include "context.h"
+
+namespace mortar {
+
+namespace {
+
+constexpr int kPolyA = 12;   // vertex cap per clipping stage (convex quads need <= 8)
+constexpr int kThreads = 128;
+
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 v3(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+template <int NEN>
+__device__ __forceinline__ void shape_grad(double xi, double eta, double dN[4][2]) {
+  if constexpr (NEN == 4) {
+    dN[0][0] = -0.25 * (1.0 - eta); dN[0][1] = -0.25 * (1.0 - xi);
+    dN[1][0] = 0.25 * (1.0 - eta);  dN[1][1] = -0.25 * (1.0 + xi);
+    dN[2][0] = 0.25 * (1.0 + eta);  dN[2][1] = 0.25 * (1.0 + xi);
+    dN[3][0] = -0.25 * (1.0 + eta); dN[3][1] = 0.25 * (1.0 - xi);
+  } else {
+    dN[0][0] = -1.0; dN[0][1] = -1.0;
+    dN[1][0] = 1.0;  dN[1][1] = 0.0;
+    dN[2][0] = 0.0;  dN[2][1] = 1.0;
+    dN[3][0] = 0.0;  dN[3][1] = 0.0;
+  }
+}
+
+// Reverse of the back-projection at a converged xi: accumulates the adjoint of
+// the query point (xb) and of the map coefficients (cb[8] = c0u c0v c1u c1v ...).
+__device__ __forceinline__ void invert_map_reverse(const PlaneMap& m, double xi, double eta, double xib0,
+                                                   double xib1, double& xbu, double& xbv, double* cb) {
+  const double j00 = m.c1u + m.c3u * eta, j01 = m.c2u + m.c3u * xi;
+  const double j10 = m.c1v + m.c3v * eta, j11 = m.c2v + m.c3v * xi;
+  const double inv = 1.0 / (j00 * j11 - j01 * j10);
+  const double mu = (j11 * xib0 - j10 * xib1) * inv;   // mu = J^-T xib
+  const double mv = (-j01 * xib0 + j00 * xib1) * inv;
+  xbu += mu;
+  xbv += mv;
+  const double xe = xi * eta;
+  cb[0] -= mu;      cb[1] -= mv;
+  cb[2] -= xi * mu; cb[3] -= xi * mv;
+  cb[4] -= eta * mu; cb[5] -= eta * mv;
+  cb[6] -= xe * mu; cb[7] -= xe * mv;
+}
+
+// Map-coefficient adjoint -> in-plane node adjoints.
+template <int NEN>
+__device__ __forceinline__ void map_coeff_reverse(const double* cb, double* pbu, double* pbv) {
+  if constexpr (NEN == 4) {
+    const double s1[4] = {-1.0, 1.0, 1.0, -1.0}, s2[4] = {-1.0, -1.0, 1.0, 1.0};
+    for (int a = 0; a < 4; ++a) {
+      pbu[a] += 0.25 * (cb[0] + s1[a] * cb[2] + s2[a] * cb[4] + s1[a] * s2[a] * cb[6]);
+      pbv[a] += 0.25 * (cb[1] + s1[a] * cb[3] + s2[a] * cb[5] + s1[a] * s2[a] * cb[7]);
+    }
+  } else {
+    pbu[0] += cb[0] - cb[2] - cb[4];
+    pbv[0] += cb[1] - cb[3] - cb[5];
+    pbu[1] += cb[2]; pbv[1] += cb[3];
+    pbu[2] += cb[4]; pbv[2] += cb[5];
+  }
+}
+
+struct AdjCounters {
+  unsigned long long clip_over = 0, newton_fail = 0;
+};
+
+template <int NS, int NM, bool SEG, bool DUAL>
+__device__ void adjoint_one(int64_t p, const int32_t* __restrict__ ps, const int32_t* __restrict__ pm,
+                            const double* __restrict__ srec, const double* __restrict__ xs,
+                            const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
+                            const int32_t* __restrict__ conn_m, const double* __restrict__ lambda,
+                            const RunParams& rp, double* __restrict__ gs_out, double* __restrict__ gm_out,
+                            double* __restrict__ ab_out, double* __restrict__ J_out, AdjCounters& ctr) {
+  const int32_t s = ps[p], m = pm[p];
+  const double* r = srec + (int64_t)SR_STRIDE * s;
+  double gX[4][3], gY[4][3], Lb[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) { gX[a][k] = 0.0; gY[a][k] = 0.0; Lb[a][k] = 0.0; }
+  double Jp = 0.0;
+  const double eps_in = r[SR_EPSIN];
+  bool nonempty = false;
+  V3 X[4], Y[4], lam[4], Lam[4];
+  if (eps_in >= 0.0) {
+    for (int a = 0; a < NS; ++a) {
+      const int64_t n = conn_s[(int64_t)NS * s + a];
+      X[a] = v3(xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]);
+      lam[a] = v3(lambda[3 * n], lambda[3 * n + 1], lambda[3 * n + 2]);
+    }
+    for (int l = 0; l < NM; ++l) {
+      const int64_t n = conn_m[(int64_t)NM * m + l];
+      Y[l] = v3(xm[3 * n], xm[3 * n + 1], xm[3 * n + 2]);
+    }
+    const V3 x0 = v3(r[SR_X0], r[SR_X0 + 1], r[SR_X0 + 2]);
+    const V3 t1 = v3(r[SR_T1], r[SR_T1 + 1], r[SR_T1 + 2]);
+    const V3 t2 = v3(r[SR_T2], r[SR_T2 + 1], r[SR_T2 + 2]);
+    // ---- forward: projection, maps, orientation (as in the integration kernel)
+    double mu[4], mv[4];
+    for (int l = 0; l < NM; ++l) {
+      const double dx = Y[l].x - x0.x, dy = Y[l].y - x0.y, dz = Y[l].z - x0.z;
+      mu[l] = dx * t1.x + dy * t1.y + dz * t1.z;
+      mv[l] = dx * t2.x + dy * t2.y + dz * t2.z;
+    }
+    const PlaneMap mmap = plane_map<NM>(mu, mv);
+    PlaneMap smap;
+    smap.c0u = r[SR_C + 0]; smap.c0v = r[SR_C + 1]; smap.c1u = r[SR_C + 2]; smap.c1v = r[SR_C + 3];
+    smap.c2u = r[SR_C + 4]; smap.c2v = r[SR_C + 5]; smap.c3u = r[SR_C + 6]; smap.c3v = r[SR_C + 7];
+    double ma2 = 0.0;
+    for (int l = 0; l < NM; ++l) ma2 += cross2(mu[l], mv[l], mu[(l + 1) % NM], mv[(l + 1) % NM]);
+    const bool mrev = ma2 < 0.0;
+    const bool srev = r[SR_REV] != 0.0;
+    // ---- forward clip with recorded stages
+    double Vu[NS + 1][kPolyA], Vv[NS + 1][kPolyA], tt[NS][kPolyA];
+    int8_t src[NS][kPolyA];   // output vertex o of stage i: input edge k; +64 if intersection
+    int nv[NS + 1];
+    for (int k = 0; k < NM; ++k) {
+      const int l = mrev ? NM - 1 - k : k;
+      Vu[0][k] = mu[l];
+      Vv[0][k] = mv[l];
+    }
+    nv[0] = NM;
+    int last = 0;
+    bool overflow = false;
+    for (int i = 0; i < NS; ++i) {
+      const int n = nv[i];
+      if (n == 0) break;
+      const int i1 = i + 1 == NS ? 0 : i + 1;
+      const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
+      const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
+      double d[kPolyA];
+      for (int k = 0; k < n; ++k) d[k] = cross2(eu, ev, Vu[i][k] - au, Vv[i][k] - av);
+      int o = 0;
+      for (int k = 0; k < n; ++k) {
+        const int k1 = k + 1 == n ? 0 : k + 1;
+        const double dp = d[k], dq = d[k1];
+        if ((dp > eps_in && dq < -eps_in) || (dp < -eps_in && dq > eps_in)) {
+          const double t = dp / (dp - dq);
+          if (o < kPolyA) {
+            Vu[i + 1][o] = Vu[i][k] + t * (Vu[i][k1] - Vu[i][k]);
+            Vv[i + 1][o] = Vv[i][k] + t * (Vv[i][k1] - Vv[i][k]);
+            tt[i][o] = t;
+            src[i][o] = (int8_t)(k + 64);
+          }
+          ++o;
+        }
+        if (dq >= -eps_in) {
+          if (o < kPolyA) {
+            Vu[i + 1][o] = Vu[i][k1];
+            Vv[i + 1][o] = Vv[i][k1];
+            src[i][o] = (int8_t)k;
+          }
+          ++o;
+        }
+      }
+      if (o > kPolyA) { overflow = true; o = kPolyA; }
+      nv[i + 1] = o;
+      last = i + 1;
+    }
+    if (overflow) ctr.clip_over++;
+    // ---- merge (selection of vertices of the last stage)
+    const double em2 = r[SR_EPSM2];
+    int sel[kPolyA];
+    int nr = 0;
+    const int nl = nv[last];
+    const bool clipped = last == NS;
+    for (int k = 0; clipped && k < nl; ++k) {
+      if (nr > 0) {
+        const double du = Vu[last][k] - Vu[last][sel[nr - 1]], dv = Vv[last][k] - Vv[last][sel[nr - 1]];
+        if (du * du + dv * dv < em2) continue;
+      }
+      sel[nr++] = k;
+    }
+    while (nr > 1) {
+      const double du = Vu[last][sel[nr - 1]] - Vu[last][sel[0]], dv = Vv[last][sel[nr - 1]] - Vv[last][sel[0]];
+      if (du * du + dv * dv < em2) --nr; else break;
+    }
+    double pa2 = 0.0;
+    for (int k = 0; k < nr; ++k) {
+      const int k1 = k + 1 == nr ? 0 : k + 1;
+      pa2 += cross2(Vu[last][sel[k]], Vv[last][sel[k]], Vu[last][sel[k1]], Vv[last][sel[k1]]);
+    }
+    nonempty = clipped && nr >= 3 && !(0.5 * fabs(pa2) < r[SR_EPSA]);
+    if (nonempty) {
+      // LM-weighted multipliers Lambda_c
+      double A[4][4];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) A[a][b] = r[SR_A + 4 * a + b];
+      for (int c = 0; c < NS; ++c) {
+        if (DUAL) {
+          V3 acc = v3(0, 0, 0);
+          for (int a = 0; a < NS; ++a) acc = acc + A[a][c] * lam[a];
+          Lam[c] = acc;
+        } else {
+          Lam[c] = lam[c];
+        }
+      }
+      double Ru[kPolyA], Rv[kPolyA], Rbu[kPolyA], Rbv[kPolyA];
+      for (int k = 0; k < nr; ++k) {
+        Ru[k] = Vu[last][sel[k]];
+        Rv[k] = Vv[last][sel[k]];
+        Rbu[k] = 0.0;
+        Rbv[k] = 0.0;
+      }
+      double cu = 0.0, cv = 0.0, cbu = 0.0, cbv = 0.0;
+      int ncell = 1;
+      if (nr > 3) {
+        double su = 0.0, sv = 0.0;
+        for (int k = 0; k < nr; ++k) { su += Ru[k]; sv += Rv[k]; }
+        cu = su / (double)nr;
+        cv = sv / (double)nr;
+        ncell = nr;
+      }
+      double smb[8] = {0, 0, 0, 0, 0, 0, 0, 0}, mmb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int cI = 0; cI < ncell; ++cI) {
+        int ib, iw;
+        double au, av;
+        if (nr == 3) {
+          au = Ru[0]; av = Rv[0]; ib = 1; iw = 2;
+        } else {
+          au = cu; av = cv; ib = cI; iw = cI + 1 == nr ? 0 : cI + 1;
+        }
+        const double e1u = Ru[ib] - au, e1v = Rv[ib] - av, e2u = Ru[iw] - au, e2v = Rv[iw] - av;
+        const double cr = cross2(e1u, e1v, e2u, e2v);
+        const double area = 0.5 * fabs(cr);
+        double area_b = 0.0, e1bu = 0.0, e1bv = 0.0, e2bu = 0.0, e2bv = 0.0, abu = 0.0, abv = 0.0;
+#pragma unroll 1
+        for (int q = 0; q < 7; ++q) {
+          double l1, l2, w;
+          tri7_point(q, l1, l2, w);
+          const double xu = au + l1 * e1u + l2 * e2u;
+          const double xv = av + l1 * e1v + l2 * e2v;
+          const double W = w * area;
+          double xs1, xs2, xm1, xm2;
+          if (!invert_plane_map<NS>(smap, xu, xv, rp.newton_tol, rp.newton_max_iter, xs1, xs2)) ctr.newton_fail++;
+          if (!invert_plane_map<NM>(mmap, xu, xv, rp.newton_tol, rp.newton_max_iter, xm1, xm2)) ctr.newton_fail++;
+          double Ns[4], Nm[4];
+          shape_fn<NS>(xs1, xs2, Ns);
+          shape_fn<NM>(xm1, xm2, Nm);
+          V3 Lh = v3(0, 0, 0), xsI = v3(0, 0, 0), xmI = v3(0, 0, 0);
+          for (int c = 0; c < NS; ++c) Lh = Lh + Ns[c] * Lam[c];
+          if (SEG)
+            for (int b = 0; b < NS; ++b) xsI = xsI + Ns[b] * X[b];
+          for (int l = 0; l < NM; ++l) xmI = xmI + Nm[l] * Y[l];
+          const V3 qv = xsI - xmI;
+          const double f = dot(Lh, qv);
+          Jp += W * f;
+          // ---- reverse of this quadrature point
+          area_b += w * f;
+          const V3 Lhb = W * qv, qb = W * Lh;
+          double Nsb[4] = {0, 0, 0, 0}, Nmb[4] = {0, 0, 0, 0};
+          for (int c = 0; c < NS; ++c) {
+            Lb[c][0] += Ns[c] * Lhb.x; Lb[c][1] += Ns[c] * Lhb.y; Lb[c][2] += Ns[c] * Lhb.z;
+            Nsb[c] += dot(Lam[c], Lhb);
+          }
+          if (SEG)
+            for (int b = 0; b < NS; ++b) {
+              gX[b][0] += Ns[b] * qb.x; gX[b][1] += Ns[b] * qb.y; gX[b][2] += Ns[b] * qb.z;
+              Nsb[b] += dot(X[b], qb);
+            }
+          for (int l = 0; l < NM; ++l) {
+            gY[l][0] -= Nm[l] * qb.x; gY[l][1] -= Nm[l] * qb.y; gY[l][2] -= Nm[l] * qb.z;
+            Nmb[l] -= dot(Y[l], qb);
+          }
+          double dNs[4][2], dNm[4][2];
+          shape_grad<NS>(xs1, xs2, dNs);
+          shape_grad<NM>(xm1, xm2, dNm);
+          double xsb0 = 0.0, xsb1 = 0.0, xmb0 = 0.0, xmb1 = 0.0;
+          for (int c = 0; c < NS; ++c) { xsb0 += Nsb[c] * dNs[c][0]; xsb1 += Nsb[c] * dNs[c][1]; }
+          for (int l = 0; l < NM; ++l) { xmb0 += Nmb[l] * dNm[l][0]; xmb1 += Nmb[l] * dNm[l][1]; }
+          double xbu = 0.0, xbv = 0.0;
+          invert_map_reverse(smap, xs1, xs2, xsb0, xsb1, xbu, xbv, smb);
+          invert_map_reverse(mmap, xm1, xm2, xmb0, xmb1, xbu, xbv, mmb);
+          abu += xbu; abv += xbv;
+          e1bu += l1 * xbu; e1bv += l1 * xbv;
+          e2bu += l2 * xbu; e2bv += l2 * xbv;
+        }
+        // area = |cr| / 2
+        const double crb = 0.5 * (cr < 0.0 ? -area_b : area_b);
+        e1bu += crb * e2v; e1bv -= crb * e2u;
+        e2bu -= crb * e1v; e2bv += crb * e1u;
+        Rbu[ib] += e1bu; Rbv[ib] += e1bv;
+        Rbu[iw] += e2bu; Rbv[iw] += e2bv;
+        abu -= e1bu + e2bu;
+        abv -= e1bv + e2bv;
+        if (nr == 3) { Rbu[0] += abu; Rbv[0] += abv; } else { cbu += abu; cbv += abv; }
+      }
+      if (nr > 3) {
+        const double inv = 1.0 / (double)nr;
+        for (int k = 0; k < nr; ++k) { Rbu[k] += cbu * inv; Rbv[k] += cbv * inv; }
+      }
+      // ---- reverse merge: adjoints onto the last stage
+      double Bu[NS + 1][kPolyA], Bv[NS + 1][kPolyA];
+      for (int k = 0; k < nl; ++k) { Bu[last][k] = 0.0; Bv[last][k] = 0.0; }
+      for (int k = 0; k < nr; ++k) { Bu[last][sel[k]] += Rbu[k]; Bv[last][sel[k]] += Rbv[k]; }
+      // ---- reverse clipping stages
+      double Wbu[4] = {0, 0, 0, 0}, Wbv[4] = {0, 0, 0, 0};
+      for (int i = NS - 1; i >= 0; --i) {
+        const int n = nv[i];
+        const int i1 = i + 1 == NS ? 0 : i + 1;
+        const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
+        const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
+        for (int k = 0; k < n; ++k) { Bu[i][k] = 0.0; Bv[i][k] = 0.0; }
+        double abu2 = 0.0, abv2 = 0.0, ebu = 0.0, ebv = 0.0;
+        for (int o = 0; o < nv[i + 1]; ++o) {
+          const double gbu = Bu[i + 1][o], gbv = Bv[i + 1][o];
+          const int code = src[i][o];
+          const int k = code & 63;
+          const int k1 = k + 1 == n ? 0 : k + 1;
+          if (code < 64) {
+            Bu[i][k1] += gbu;
+            Bv[i][k1] += gbv;
+            continue;
+          }
+          const double t = tt[i][o];
+          const double pu = Vu[i][k], pv = Vv[i][k], qu = Vu[i][k1], qv = Vv[i][k1];
+          Bu[i][k] += (1.0 - t) * gbu; Bv[i][k] += (1.0 - t) * gbv;
+          Bu[i][k1] += t * gbu;        Bv[i][k1] += t * gbv;
+          const double tb = gbu * (qu - pu) + gbv * (qv - pv);
+          const double dp = cross2(eu, ev, pu - au, pv - av);
+          const double dq = cross2(eu, ev, qu - au, qv - av);
+          const double den = dp - dq;
+          const double i2 = 1.0 / (den * den);
+          const double dpb = -tb * dq * i2, dqb = tb * dp * i2;
+          // d = eu (y_v - a_v) - ev (y_u - a_u) for y = p, q
+          Bu[i][k] += -ev * dpb;  Bv[i][k] += eu * dpb;
+          Bu[i][k1] += -ev * dqb; Bv[i][k1] += eu * dqb;
+          abu2 += ev * (dpb + dqb);
+          abv2 += -eu * (dpb + dqb);
+          ebu += (pv - av) * dpb + (qv - av) * dqb;
+          ebv += -(pu - au) * dpb - (qu - au) * dqb;
+        }
+        Wbu[i] += abu2 - ebu; Wbv[i] += abv2 - ebv;
+        Wbu[i1] += ebu;       Wbv[i1] += ebv;
+      }
+      // ---- in-plane node adjoints
+      double sbu[4] = {0, 0, 0, 0}, sbv[4] = {0, 0, 0, 0}, mbu[4] = {0, 0, 0, 0}, mbv[4] = {0, 0, 0, 0};
+      for (int k = 0; k < NS; ++k) {
+        const int a = srev ? NS - 1 - k : k;
+        sbu[a] += Wbu[k];
+        sbv[a] += Wbv[k];
+      }
+      for (int k = 0; k < NM; ++k) {
+        const int l = mrev ? NM - 1 - k : k;
+        mbu[l] += Bu[0][k];
+        mbv[l] += Bv[0][k];
+      }
+      map_coeff_reverse<NS>(smb, sbu, sbv);
+      map_coeff_reverse<NM>(mmb, mbu, mbv);
+      // ---- projection u = (P - x0).t1, v = (P - x0).t2
+      V3 x0b = v3(0, 0, 0), t1b = v3(0, 0, 0), t2b = v3(0, 0, 0);
+      for (int a = 0; a < NS; ++a) {
+        const V3 d = X[a] - x0;
+        const V3 db = sbu[a] * t1 + sbv[a] * t2;
+        gX[a][0] += db.x; gX[a][1] += db.y; gX[a][2] += db.z;
+        x0b = x0b - db;
+        t1b = t1b + sbu[a] * d;
+        t2b = t2b + sbv[a] * d;
+      }
+      for (int l = 0; l < NM; ++l) {
+        const V3 d = Y[l] - x0;
+        const V3 db = mbu[l] * t1 + mbv[l] * t2;
+        gY[l][0] += db.x; gY[l][1] += db.y; gY[l][2] += db.z;
+        x0b = x0b - db;
+        t1b = t1b + mbu[l] * d;
+        t2b = t2b + mbv[l] * d;
+      }
+      // ---- auxiliary plane as a function of the slave nodes
+      const V3 n0 = v3(r[SR_N0], r[SR_N0 + 1], r[SR_N0 + 2]);
+      V3 g1, g2;
+      if constexpr (NS == 4) {
+        g1 = 0.25 * ((X[1] - X[0]) + (X[2] - X[3]));
+        g2 = 0.25 * ((X[2] - X[1]) + (X[3] - X[0]));
+      } else {
+        g1 = X[1] - X[0];
+        g2 = X[2] - X[0];
+      }
+      const V3 nn = cross(g1, g2);
+      const double ln = sqrt(dot(nn, nn));
+      const V3 ed = X[1] - X[0];
+      const double en = dot(ed, n0);
+      const V3 ep = ed - en * n0;
+      const double le = sqrt(dot(ep, ep));
+      V3 n0b = cross(t1, t2b);            // t2 = n0 x t1
+      t1b = t1b + cross(t2b, n0);
+      const V3 epb = (1.0 / le) * (t1b - dot(t1, t1b) * t1);
+      V3 edb = epb;
+      const double enb = -dot(epb, n0);
+      n0b = n0b - en * epb;
+      edb = edb + enb * n0;
+      n0b = n0b + enb * ed;
+      const V3 nb = (1.0 / ln) * (n0b - dot(n0, n0b) * n0);
+      const V3 g1b = cross(g2, nb), g2b = cross(nb, g1);
+      V3 Xb[4];
+      for (int a = 0; a < 4; ++a) Xb[a] = v3(0, 0, 0);
+      Xb[1] = Xb[1] + edb;
+      Xb[0] = Xb[0] - edb;
+      if constexpr (NS == 4) {
+        const V3 a1 = 0.25 * g1b, a2 = 0.25 * g2b, ax = 0.25 * x0b;
+        Xb[0] = Xb[0] - a1 - a2 + ax;
+        Xb[1] = Xb[1] + a1 - a2 + ax;
+        Xb[2] = Xb[2] + a1 + a2 + ax;
+        Xb[3] = Xb[3] - a1 + a2 + ax;
+      } else {
+        const V3 ax = (1.0 / 3.0) * x0b;
+        Xb[0] = Xb[0] - g1b - g2b + ax;
+        Xb[1] = Xb[1] + g1b + ax;
+        Xb[2] = Xb[2] + g2b + ax;
+      }
+      for (int a = 0; a < NS; ++a) {
+        gX[a][0] += Xb[a].x; gX[a][1] += Xb[a].y; gX[a][2] += Xb[a].z;
+      }
+    }
+  }
+  double* go = gs_out + 12 * p;
+  double* gmo = gm_out + 12 * p;
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) {
+      go[3 * a + k] = gX[a][k];
+      gmo[3 * a + k] = gY[a][k];
+    }
+  if (DUAL) {
+    double* ab = ab_out + 16 * p;
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c)
+        ab[4 * a + c] = (nonempty && a < NS && c < NS)
+                            ? lam[a].x * Lb[c][0] + lam[a].y * Lb[c][1] + lam[a].z * Lb[c][2]
+                            : 0.0;
+  }
+  J_out[p] = Jp;
+}
+
+template <int NS, int NM, bool SEG, bool DUAL>
+__global__ void __launch_bounds__(kThreads) k_adjoint_pairs(
+    const int32_t* __restrict__ ps, const int32_t* __restrict__ pm, const double* __restrict__ srec,
+    const double* __restrict__ xs, const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
+    const int32_t* __restrict__ conn_m, const double* __restrict__ lambda, RunParams rp, int64_t pair_cap,
+    int32_t chunk, double* __restrict__ gs_out, double* __restrict__ gm_out, double* __restrict__ ab_out,
+    double* __restrict__ J_out, DevStatus* st) {
+  AdjCounters ctr;
+  const int lane = threadIdx.x & 31;
+  const bool ok = st->over_pairs == 0 && st->over_bins == 0;
+  const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
+  for (;;) {   // bounded: the shared counter only grows
+    int64_t base = 0;
+    if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr2, (unsigned long long)chunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    const int64_t end = min(base + (int64_t)chunk, n);
+    for (int64_t p = base + lane; p < end; p += 32)
+      adjoint_one<NS, NM, SEG, DUAL>(p, ps, pm, srec, xs, xm, conn_s, conn_m, lambda, rp, gs_out, gm_out, ab_out,
+                                     J_out, ctr);
+  }
+  block_count_add(&st->clip_overflow, ctr.clip_over);
+  block_count_add(&st->newton_fail, ctr.newton_fail);
+}
+
+// Element quadrature point k (same rule as the precomputation).
+template <int NEN>
+__device__ __forceinline__ void elem_point_a(int k, double& xi, double& eta, double& w) {
+  if constexpr (NEN == 4) {
+    const double g = 0.7745966692414834;
+    const double pp[3] = {-g, 0.0, g};
+    const double ww[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    xi = pp[k / 3];
+    eta = pp[k % 3];
+    w = ww[k / 3] * ww[k % 3];
+  } else {
+    tri7_point(k, xi, eta, w);
+    w *= 0.5;
+  }
+}
+
+// Per slave element: sum dJ/dA over its pairs, add the element-domain D term,
+// propagate through A = Dh Me^-1 and the element integrals to the nodes.
+template <int NS, bool DUAL, bool ELEMD>
+__global__ void __launch_bounds__(kThreads) k_adjoint_elems(
+    const double* __restrict__ xs, const int32_t* __restrict__ conn_s, const double* __restrict__ lambda,
+    const double* __restrict__ srec, const double* __restrict__ De, const int64_t* __restrict__ pair_off,
+    const double* __restrict__ ab_pair, int64_t Es, double* __restrict__ ge, const DevStatus* st) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Es) return;
+  double* out = ge + 16 * e;
+  for (int k = 0; k < 16; ++k) out[k] = 0.0;
+  const double* r = srec + (int64_t)SR_STRIDE * e;
+  if (r[SR_EPSIN] < 0.0 || st->over_pairs) return;
+  V3 X[4], lam[4];
+  for (int a = 0; a < NS; ++a) {
+    const int64_t n = conn_s[(int64_t)NS * e + a];
+    X[a] = v3(xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]);
+    lam[a] = v3(lambda[3 * n], lambda[3 * n + 1], lambda[3 * n + 2]);
+  }
+  double A[4][4], Ab[4][4], Meb[4][4], Dhb[4];
+  for (int a = 0; a < 4; ++a) {
+    Dhb[a] = 0.0;
+    for (int b = 0; b < 4; ++b) { A[a][b] = r[SR_A + 4 * a + b]; Ab[a][b] = 0.0; Meb[a][b] = 0.0; }
+  }
+  if (DUAL) {
+    const int64_t p0 = pair_off[e], p1 = pair_off[e + 1];
+    for (int64_t p = p0; p < p1; ++p)
+      for (int a = 0; a < NS; ++a)
+        for (int b = 0; b < NS; ++b) Ab[a][b] += ab_pair[16 * p + 4 * a + b];
+  }
+  V3 Xb[4];
+  for (int a = 0; a < 4; ++a) Xb[a] = v3(0, 0, 0);
+  double Je = 0.0;
+  constexpr int nq = NS == 4 ? 9 : 7;
+  // element integrals Me, Dh (recomputed)
+  double Me[4][4], Dh[4];
+  for (int a = 0; a < 4; ++a) {
+    Dh[a] = 0.0;
+    for (int b = 0; b < 4; ++b) Me[a][b] = 0.0;
+  }
+  for (int q = 0; q < nq; ++q) {
+    double xi, eta, w;
+    elem_point_a<NS>(q, xi, eta, w);
+    double N[4], dN[4][2];
+    shape_fn<NS>(xi, eta, N);
+    shape_grad<NS>(xi, eta, dN);
+    V3 g1 = v3(0, 0, 0), g2 = v3(0, 0, 0);
+    for (int a = 0; a < NS; ++a) { g1 = g1 + dN[a][0] * X[a]; g2 = g2 + dN[a][1] * X[a]; }
+    const V3 nq3 = cross(g1, g2);
+    const double wj = w * sqrt(dot(nq3, nq3));
+    for (int a = 0; a < NS; ++a) {
+      Dh[a] += wj * N[a];
+      for (int b = 0; b < NS; ++b) Me[a][b] += wj * N[a] * N[b];
+    }
+  }
+  if (ELEMD) {
+    // J_e = sum_ab (lam_a . X_b) De_ab with De = A Me
+    for (int a = 0; a < NS; ++a)
+      for (int b = 0; b < NS; ++b) {
+        const double dab = De[16 * e + 4 * a + b];
+        Je += dab * dot(lam[a], X[b]);
+        Xb[b] = Xb[b] + dab * lam[a];
+        const double deb = dot(lam[a], X[b]);
+        for (int c = 0; c < NS; ++c) {
+          Ab[a][c] += deb * Me[c][b];
+          Meb[c][b] += A[a][c] * deb;
+        }
+      }
+  }
+  if (DUAL) {
+    // A = Dh K, K = Me^-1 = Dh^-1 A
+    double K[4][4], Kb[4][4];
+    for (int a = 0; a < NS; ++a)
+      for (int b = 0; b < NS; ++b) {
+        K[a][b] = A[a][b] / Dh[a];
+        Kb[a][b] = Dh[a] * Ab[a][b];
+      }
+    for (int a = 0; a < NS; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < NS; ++b) s += Ab[a][b] * K[a][b];
+      Dhb[a] += s;
+    }
+    // Meb -= K Kb K
+    double T[4][4];
+    for (int a = 0; a < NS; ++a)
+      for (int b = 0; b < NS; ++b) {
+        double s = 0.0;
+        for (int c = 0; c < NS; ++c) s += K[a][c] * Kb[c][b];
+        T[a][b] = s;
+      }
+    for (int a = 0; a < NS; ++a)
+      for (int b = 0; b < NS; ++b) {
+        double s = 0.0;
+        for (int c = 0; c < NS; ++c) s += T[a][c] * K[c][b];
+        Meb[a][b] -= s;
+      }
+  }
+  // element integrals -> nodes
+  for (int q = 0; q < nq; ++q) {
+    double xi, eta, w;
+    elem_point_a<NS>(q, xi, eta, w);
+    double N[4], dN[4][2];
+    shape_fn<NS>(xi, eta, N);
+    shape_grad<NS>(xi, eta, dN);
+    double jb = 0.0;
+    for (int a = 0; a < NS; ++a) {
+      jb += Dhb[a] * w * N[a];
+      for (int b = 0; b < NS; ++b) jb += Meb[a][b] * w * N[a] * N[b];
+    }
+    if (jb == 0.0) continue;
+    V3 g1 = v3(0, 0, 0), g2 = v3(0, 0, 0);
+    for (int a = 0; a < NS; ++a) { g1 = g1 + dN[a][0] * X[a]; g2 = g2 + dN[a][1] * X[a]; }
+    const V3 nq3 = cross(g1, g2);
+    const double J = sqrt(dot(nq3, nq3));
+    const V3 nb = (jb / J) * nq3;
+    const V3 g1b = cross(g2, nb), g2b = cross(nb, g1);
+    for (int a = 0; a < NS; ++a) Xb[a] = Xb[a] + dN[a][0] * g1b + dN[a][1] * g2b;
+  }
+  for (int a = 0; a < NS; ++a) {
+    out[3 * a] = Xb[a].x;
+    out[3 * a + 1] = Xb[a].y;
+    out[3 * a + 2] = Xb[a].z;
+  }
+  out[12] = Je;
+}
+
+// master element -> pairs (non-empty ones), counting sort + per-element sort
+__global__ void k_mp_count(const int32_t* __restrict__ pm, const uint8_t* __restrict__ flag, int64_t pair_cap,
+                           int32_t* __restrict__ cnt, const DevStatus* st) {
+  const int64_t n = st->over_pairs ? 0 : (int64_t)min((unsigned long long)pair_cap, st->n_pairs);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    if (flag[p]) atomicAdd(&cnt[pm[p]], 1);
+}
+
+__global__ void k_mp_fill(const int32_t* __restrict__ pm, const uint8_t* __restrict__ flag, int64_t pair_cap,
+                          const int64_t* __restrict__ off, int32_t* __restrict__ cnt, int32_t* __restrict__ list,
+                          const DevStatus* st) {
+  const int64_t n = st->over_pairs ? 0 : (int64_t)min((unsigned long long)pair_cap, st->n_pairs);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    if (flag[p]) {
+      const int32_t m = pm[p];
+      const int32_t slot = atomicSub(&cnt[m], 1) - 1;
+      list[off[m] + slot] = (int32_t)p;
+    }
+}
+
+__global__ void k_mp_sort(const int64_t* __restrict__ off, int64_t Em, int32_t* __restrict__ list) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= Em) return;
+  const int64_t b0 = off[f], b1 = off[f + 1];
+  for (int64_t a = b0 + 1; a < b1; ++a) {
+    const int32_t v = list[a];
+    int64_t b = a - 1;
+    while (b >= b0 && list[b] > v) { list[b + 1] = list[b]; --b; }
+    list[b + 1] = v;
+  }
+}
+
+__global__ void k_grad_slave(const int64_t* __restrict__ n2e_ptr, const int64_t* __restrict__ n2e_ent,
+                             const int64_t* __restrict__ pair_off, const uint8_t* __restrict__ flag,
+                             const double* __restrict__ gs_pair, const double* __restrict__ ge, int64_t Ns,
+                             double* __restrict__ grad, const DevStatus* st) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Ns) return;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  if (!st->over_pairs)
+    for (int64_t q = n2e_ptr[j]; q < n2e_ptr[j + 1]; ++q) {
+      const int64_t e = n2e_ent[q] >> 2;
+      const int a = (int)(n2e_ent[q] & 3);
+      g0 += ge[16 * e + 3 * a]; g1 += ge[16 * e + 3 * a + 1]; g2 += ge[16 * e + 3 * a + 2];
+      for (int64_t p = pair_off[e]; p < pair_off[e + 1]; ++p) {
+        if (!flag[p]) continue;
+        g0 += gs_pair[12 * p + 3 * a]; g1 += gs_pair[12 * p + 3 * a + 1]; g2 += gs_pair[12 * p + 3 * a + 2];
+      }
+    }
+  grad[3 * j] = g0;
+  grad[3 * j + 1] = g1;
+  grad[3 * j + 2] = g2;
+}
+
+__global__ void k_grad_master(const int64_t* __restrict__ n2e_ptr, const int64_t* __restrict__ n2e_ent,
+                              const int64_t* __restrict__ mp_off, const int32_t* __restrict__ mp_list,
+                              const double* __restrict__ gm_pair, int64_t Nm, double* __restrict__ grad,
+                              const DevStatus* st) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Nm) return;
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  if (!st->over_pairs)
+    for (int64_t q = n2e_ptr[j]; q < n2e_ptr[j + 1]; ++q) {
+      const int64_t f = n2e_ent[q] >> 2;
+      const int l = (int)(n2e_ent[q] & 3);
+      for (int64_t k = mp_off[f]; k < mp_off[f + 1]; ++k) {
+        const int64_t p = mp_list[k];
+        g0 += gm_pair[12 * p + 3 * l]; g1 += gm_pair[12 * p + 3 * l + 1]; g2 += gm_pair[12 * p + 3 * l + 2];
+      }
+    }
+  grad[3 * j] = g0;
+  grad[3 * j + 1] = g1;
+  grad[3 * j + 2] = g2;
+}
+
+constexpr int kJBlocks = 256;
+
+// Fixed-shape reduction of J over pairs and elements (deterministic).
+__global__ void __launch_bounds__(256) k_J_partial(const double* __restrict__ J_pair, int64_t pair_cap,
+                                                   const double* __restrict__ ge, int64_t Es,
+                                                   double* __restrict__ part, const DevStatus* st) {
+  const int64_t np = st->over_pairs ? 0 : (int64_t)min((unsigned long long)pair_cap, st->n_pairs);
+  const int64_t total = np + Es;
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = per * blockIdx.x, b1 = min(total, b0 + per);
+  double s = 0.0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += i < np ? J_pair[i] : ge[16 * (i - np) + 12];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(256) k_J_final(const double* __restrict__ part, DevStatus* st) {
+  __shared__ double sh[256];
+  sh[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->J = sh[0];
+}
+
+template <int NS, int NM, bool SEG, bool DUAL>
+void launch_pairs_t(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk) {
+  k_adjoint_pairs<NS, NM, SEG, DUAL><<<grid, block, 0, c->stream>>>(
+      c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
+      c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->lambda.as<double>(), rp, c->pair_cap,
+      chunk, c->gs_pair.as<double>(), c->gm_pair.as<double>(), c->abar_pair.as<double>(), c->J_pair.as<double>(),
+      c->dstat.as<DevStatus>());
+}
+
+template <int NS, int NM>
+void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk) {
+  const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
+  if (seg && dual) launch_pairs_t<NS, NM, true, true>(c, rp, grid, block, chunk);
+  else if (seg) launch_pairs_t<NS, NM, true, false>(c, rp, grid, block, chunk);
+  else if (dual) launch_pairs_t<NS, NM, false, true>(c, rp, grid, block, chunk);
+  else launch_pairs_t<NS, NM, false, false>(c, rp, grid, block, chunk);
+}
+
+template <int NS>
+void launch_elems_ns(mortar_ctx* c, const RunParams& rp) {
+  const unsigned g = (unsigned)((c->Es + kThreads - 1) / kThreads);
+  if (c->Es == 0) return;
+  const bool elemd = rp.d_domain == 0, dual = rp.lm == 1;
+  auto args = [&](auto kern) {
+    kern<<<g, kThreads, 0, c->stream>>>(c->xs.as<double>(), c->conn_s.as<int32_t>(), c->lambda.as<double>(),
+                                        c->srec.as<double>(), c->De.as<double>(), c->pair_off.as<int64_t>(),
+                                        c->abar_pair.as<double>(), c->Es, c->ge_elem.as<double>(),
+                                        c->dstat.as<DevStatus>());
+  };
+  if (dual && elemd) args(k_adjoint_elems<NS, true, true>);
+  else if (dual) args(k_adjoint_elems<NS, true, false>);
+  else if (elemd) args(k_adjoint_elems<NS, false, true>);
+  else args(k_adjoint_elems<NS, false, false>);
+}
+
+}  // namespace
+
+int prepare_adjoint_buffers(mortar_ctx* c) {
+  const size_t P = (size_t)std::max<int64_t>(c->pair_cap, 1);
+  int r;
+  if ((r = buf_reserve(c->gs_pair, P * 12 * 8)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->gm_pair, P * 12 * 8)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->J_pair, P * 8)) != MORTAR_OK) return r;
+  if (c->opt.lm == MORTAR_LM_DUAL && (r = buf_reserve(c->abar_pair, P * 16 * 8)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->mp_list, P * 4)) != MORTAR_OK) return r;
+  const size_t Es = (size_t)std::max<int64_t>(c->Es, 1), Em = (size_t)std::max<int64_t>(c->Em, 1);
+  if ((r = buf_reserve(c->ge_elem, Es * 16 * 8)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->mp_cnt, Em * 4)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->mp_off, (Em + 1) * 8)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->grad_s, (size_t)std::max<int64_t>(c->Ns, 1) * 24)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->grad_m, (size_t)std::max<int64_t>(c->Nm, 1) * 24)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->J_part, kJBlocks * 8)) != MORTAR_OK) return r;
+  if ((r = buf_reserve(c->lambda, (size_t)std::max<int64_t>(c->Ns, 1) * 24)) != MORTAR_OK) return r;
+  return MORTAR_OK;
+}
+
+void launch_adjoint(mortar_ctx* c, const RunParams& rp) {
+  DevStatus* st = c->dstat.as<DevStatus>();
+  const unsigned block = c->block_size > 0 ? (unsigned)c->block_size : 128u;
+  const int32_t chunk = c->chunk_pairs > 0 ? c->chunk_pairs : 32;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_pairs<4, 4, false, true>, (int)block, 0);
+  if (per_sm < 1) per_sm = 1;
+  const unsigned grid = (unsigned)(c->n_sm * per_sm);
+  if (c->nen_s == 4 && c->nen_m == 4) launch_pairs_nsnm<4, 4>(c, rp, grid, block, chunk);
+  else if (c->nen_s == 4 && c->nen_m == 3) launch_pairs_nsnm<4, 3>(c, rp, grid, block, chunk);
+  else if (c->nen_s == 3 && c->nen_m == 4) launch_pairs_nsnm<3, 4>(c, rp, grid, block, chunk);
+  else launch_pairs_nsnm<3, 3>(c, rp, grid, block, chunk);
+  if (c->nen_s == 4) launch_elems_ns<4>(c, rp); else launch_elems_ns<3>(c, rp);
+  // master element -> pair lists
+  cudaMemsetAsync(c->mp_cnt.p, 0, (size_t)std::max<int64_t>(c->Em, 1) * 4, c->stream);
+  const unsigned pg = (unsigned)(c->n_sm * 8);
+  k_mp_count<<<pg, 256, 0, c->stream>>>(c->pairs_m.as<int32_t>(), c->flag.as<uint8_t>(), c->pair_cap,
+                                        c->mp_cnt.as<int32_t>(), st);
+  launch_exclusive_scan_i32(c->mp_cnt.as<int32_t>(), c->mp_off.as<int64_t>(), nullptr, c->Em,
+                            c->scan_tmp.as<int64_t>(), c->stream);
+  k_mp_fill<<<pg, 256, 0, c->stream>>>(c->pairs_m.as<int32_t>(), c->flag.as<uint8_t>(), c->pair_cap,
+                                       c->mp_off.as<int64_t>(), c->mp_cnt.as<int32_t>(), c->mp_list.as<int32_t>(), st);
+  if (c->Em > 0)
+    k_mp_sort<<<(unsigned)((c->Em + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(
+        c->mp_off.as<int64_t>(), c->Em, c->mp_list.as<int32_t>());
+  if (c->Ns > 0)
+    k_grad_slave<<<(unsigned)((c->Ns + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(
+        c->n2e_s_ptr.as<int64_t>(), c->n2e_s_ent.as<int64_t>(), c->pair_off.as<int64_t>(), c->flag.as<uint8_t>(),
+        c->gs_pair.as<double>(), c->ge_elem.as<double>(), c->Ns, c->grad_s.as<double>(), st);
+  if (c->Nm > 0)
+    k_grad_master<<<(unsigned)((c->Nm + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(
+        c->n2e_m_ptr.as<int64_t>(), c->n2e_m_ent.as<int64_t>(), c->mp_off.as<int64_t>(), c->mp_list.as<int32_t>(),
+        c->gm_pair.as<double>(), c->Nm, c->grad_m.as<double>(), st);
+  k_J_partial<<<kJBlocks, 256, 0, c->stream>>>(c->J_pair.as<double>(), c->pair_cap, c->ge_elem.as<double>(), c->Es,
+                                               c->J_part.as<double>(), st);
+  k_J_final<<<1, 256, 0, c->stream>>>(c->J_part.as<double>(), st);
+}
+
+}  // namespace mortar

@@ -1,0 +1,441 @@
+// Element-level precomputation and the per-interface search grid.
+//
+//  * Slave elements (one thread each): auxiliary plane x0, n0 and in-plane
+//    basis t1, t2 (Sec. 2.3, Fig. 1), projected slave polygon and its bilinear
+//    map, clipping tolerances, LM coefficients A (standard: identity; dual:
+//    A = Dh Me^-1, biorthogonal to N, Sec. 2.2) and the element-domain D
+//    block; inflated bounding box and diameter for the search.
+//  * Master elements: inflated bounding box and diameter.
+//  * Search grid per interface (Sec. 3.3): bounding box of the interface,
+//    minimal bin size beta_min = (1 + 1e-9) max diameter + 2 delta, box
+//    expanded by beta_min, n_d = max(1, floor(L_d / beta_min)) bins per
+//    direction (bins grow by 1.25x while an interface would exceed its bin
+//    capacity).
+#include <cfloat>
+
+#include "context.h"
+
+namespace mortar {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Surface Jacobian |x,xi x x,eta| of an element at (xi, eta).
+template <int NEN>
+__device__ double surface_jac(const V3* X, double xi, double eta) {
+  V3 g1, g2;
+  if constexpr (NEN == 4) {
+    const double em = 0.25 * (1.0 - eta), ep = 0.25 * (1.0 + eta);
+    const double xm = 0.25 * (1.0 - xi), xp = 0.25 * (1.0 + xi);
+    g1 = {-em * X[0].x + em * X[1].x + ep * X[2].x - ep * X[3].x,
+          -em * X[0].y + em * X[1].y + ep * X[2].y - ep * X[3].y,
+          -em * X[0].z + em * X[1].z + ep * X[2].z - ep * X[3].z};
+    g2 = {-xm * X[0].x - xp * X[1].x + xp * X[2].x + xm * X[3].x,
+          -xm * X[0].y - xp * X[1].y + xp * X[2].y + xm * X[3].y,
+          -xm * X[0].z - xp * X[1].z + xp * X[2].z + xm * X[3].z};
+  } else {
+    g1 = sub(X[1], X[0]);
+    g2 = sub(X[2], X[0]);
+  }
+  V3 n = cross(g1, g2);
+  return sqrt(dot(n, n));
+}
+
+// Element rule point k: 3x3 Gauss-Legendre (quad4, weights sum 4) or the
+// 7-point triangle rule (tri3, weights sum 1/2).
+template <int NEN>
+__device__ __forceinline__ void elem_point(int k, double& xi, double& eta, double& w) {
+  if constexpr (NEN == 4) {
+    const double g = 0.7745966692414834;
+    const double p[3] = {-g, 0.0, g};
+    const double ww[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    xi = p[k / 3];
+    eta = p[k % 3];
+    w = ww[k / 3] * ww[k % 3];
+  } else {
+    tri7_point(k, xi, eta, w);
+    w *= 0.5;
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kThreads) k_slave_precompute(
+    const double* __restrict__ xs, const int32_t* __restrict__ conn, int64_t Es, RunParams rp,
+    double* __restrict__ srec, double* __restrict__ De, double* __restrict__ box, DevStatus* st) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool degenerate = false;
+  if (e < Es) {
+    V3 X[4];
+    for (int a = 0; a < NS; ++a) {
+      const int64_t n = conn[NS * e + a];
+      X[a] = {xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]};
+    }
+    // ---- auxiliary plane at the element centre
+    V3 x0, g1, g2;
+    if constexpr (NS == 4) {
+      x0 = {0.25 * ((X[0].x + X[1].x) + (X[2].x + X[3].x)), 0.25 * ((X[0].y + X[1].y) + (X[2].y + X[3].y)),
+            0.25 * ((X[0].z + X[1].z) + (X[2].z + X[3].z))};
+      g1 = {0.25 * ((X[1].x - X[0].x) + (X[2].x - X[3].x)), 0.25 * ((X[1].y - X[0].y) + (X[2].y - X[3].y)),
+            0.25 * ((X[1].z - X[0].z) + (X[2].z - X[3].z))};
+      g2 = {0.25 * ((X[2].x - X[1].x) + (X[3].x - X[0].x)), 0.25 * ((X[2].y - X[1].y) + (X[3].y - X[0].y)),
+            0.25 * ((X[2].z - X[1].z) + (X[3].z - X[0].z))};
+    } else {
+      const double t = 1.0 / 3.0;
+      x0 = {t * (X[0].x + X[1].x + X[2].x), t * (X[0].y + X[1].y + X[2].y), t * (X[0].z + X[1].z + X[2].z)};
+      g1 = sub(X[1], X[0]);
+      g2 = sub(X[2], X[0]);
+    }
+    V3 n = cross(g1, g2);
+    const double ln = sqrt(dot(n, n));
+    const V3 n0 = {n.x / ln, n.y / ln, n.z / ln};
+    const V3 ed = sub(X[1], X[0]);
+    const double en = dot(ed, n0);
+    const V3 ep = {ed.x - en * n0.x, ed.y - en * n0.y, ed.z - en * n0.z};
+    const double le = sqrt(dot(ep, ep));
+    const V3 t1 = {ep.x / le, ep.y / le, ep.z / le};
+    const V3 t2 = cross(n0, t1);
+    double* r = srec + (int64_t)SR_STRIDE * e;
+    r[SR_X0] = x0.x; r[SR_X0 + 1] = x0.y; r[SR_X0 + 2] = x0.z;
+    r[SR_T1] = t1.x; r[SR_T1 + 1] = t1.y; r[SR_T1 + 2] = t1.z;
+    r[SR_T2] = t2.x; r[SR_T2 + 1] = t2.y; r[SR_T2 + 2] = t2.z;
+    r[SR_N0] = n0.x; r[SR_N0 + 1] = n0.y; r[SR_N0 + 2] = n0.z;
+    // ---- projected slave polygon
+    double pu[4] = {0, 0, 0, 0}, pv[4] = {0, 0, 0, 0};
+    for (int a = 0; a < NS; ++a) {
+      const V3 d = sub(X[a], x0);
+      pu[a] = dot(d, t1);
+      pv[a] = dot(d, t2);
+    }
+    const PlaneMap pm = plane_map<NS>(pu, pv);
+    r[SR_C + 0] = pm.c0u; r[SR_C + 1] = pm.c0v; r[SR_C + 2] = pm.c1u; r[SR_C + 3] = pm.c1v;
+    r[SR_C + 4] = pm.c2u; r[SR_C + 5] = pm.c2v; r[SR_C + 6] = pm.c3u; r[SR_C + 7] = pm.c3v;
+    double area2 = 0.0;
+    for (int a = 0; a < NS; ++a) area2 += cross2(pu[a], pv[a], pu[(a + 1) % NS], pv[(a + 1) % NS]);
+    for (int a = 0; a < NS; ++a) {
+      const int src = area2 < 0.0 ? NS - 1 - a : a;
+      r[SR_PS + 2 * a] = pu[src];
+      r[SR_PS + 2 * a + 1] = pv[src];
+    }
+    if (NS == 3) { r[SR_PS + 6] = 0.0; r[SR_PS + 7] = 0.0; }
+    r[SR_REV] = area2 < 0.0 ? 1.0 : 0.0;
+    // ---- tolerances: diameter and projected area
+    double h2 = 0.0;
+    for (int a = 0; a < NS; ++a)
+      for (int b = a + 1; b < NS; ++b) {
+        const V3 d = sub(X[a], X[b]);
+        h2 = fmax(h2, dot(d, d));
+      }
+    const double h = sqrt(h2);
+    const double em = rp.merge_tol_rel * h;
+    r[SR_EPSIN] = rp.clip_tol_rel * h * h;
+    r[SR_EPSM2] = em * em;
+    r[SR_EPSA] = rp.area_tol_rel * (0.5 * fabs(area2));
+    degenerate = !(ln > 0.0) || !(le > 0.0) || !(fabs(area2) > 0.0) || !isfinite(h);
+    if (degenerate) r[SR_EPSIN] = -1.0;   // marks the element; its pairs integrate to nothing
+    // ---- LM coefficients
+    double A[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) A[a][b] = a == b ? 1.0 : 0.0;
+    double Me[4][4], Dh[4];
+    for (int a = 0; a < 4; ++a) {
+      Dh[a] = 0.0;
+      for (int b = 0; b < 4; ++b) Me[a][b] = 0.0;
+    }
+    constexpr int nq = NS == 4 ? 9 : 7;
+    for (int q = 0; q < nq; ++q) {
+      double xi, eta, w;
+      elem_point<NS>(q, xi, eta, w);
+      double N[4];
+      shape_fn<NS>(xi, eta, N);
+      const double wj = w * surface_jac<NS>(X, xi, eta);
+      for (int a = 0; a < NS; ++a) {
+        Dh[a] += wj * N[a];
+        for (int b = 0; b < NS; ++b) Me[a][b] += wj * N[a] * N[b];
+      }
+    }
+    if (rp.lm == 1 && !degenerate) {
+      // solve Me X = diag(Dh) by Gauss-Jordan with partial pivoting; A = X^T
+      double B[4][4];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) B[a][b] = (a == b && a < NS) ? Dh[a] : 0.0;
+      for (int c = 0; c < NS; ++c) {
+        int piv = c;
+        for (int rr = c + 1; rr < NS; ++rr)
+          if (fabs(Me[rr][c]) > fabs(Me[piv][c])) piv = rr;
+        if (piv != c)
+          for (int k = 0; k < 4; ++k) {
+            double t = Me[c][k]; Me[c][k] = Me[piv][k]; Me[piv][k] = t;
+            t = B[c][k]; B[c][k] = B[piv][k]; B[piv][k] = t;
+          }
+        const double inv = 1.0 / Me[c][c];
+        for (int rr = 0; rr < NS; ++rr) {
+          if (rr == c) continue;
+          const double f = Me[rr][c] * inv;
+          for (int k = 0; k < 4; ++k) {
+            Me[rr][k] -= f * Me[c][k];
+            B[rr][k] -= f * B[c][k];
+          }
+        }
+      }
+      for (int a = 0; a < NS; ++a)
+        for (int b = 0; b < NS; ++b) A[a][b] = B[b][a] / Me[b][b];
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) r[SR_A + 4 * a + b] = A[a][b];
+    // ---- element-domain D: De = sum_q w J Phi_a N_b = A Me  (Me rebuilt)
+    double* d = De + 16 * e;
+    double Mq[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) Mq[a][b] = 0.0;
+    for (int q = 0; q < nq; ++q) {
+      double xi, eta, w;
+      elem_point<NS>(q, xi, eta, w);
+      double N[4];
+      shape_fn<NS>(xi, eta, N);
+      const double wj = w * surface_jac<NS>(X, xi, eta);
+      for (int a = 0; a < NS; ++a) {
+        double phi = 0.0;
+        for (int c = 0; c < NS; ++c) phi += A[a][c] * N[c];
+        for (int b = 0; b < NS; ++b) Mq[a][b] += wj * phi * N[b];
+      }
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) d[4 * a + b] = Mq[a][b];
+    // ---- search box (delta-inflated) and diameter
+    double lo[3] = {X[0].x, X[0].y, X[0].z}, hi[3] = {X[0].x, X[0].y, X[0].z};
+    for (int a = 1; a < NS; ++a) {
+      lo[0] = fmin(lo[0], X[a].x); hi[0] = fmax(hi[0], X[a].x);
+      lo[1] = fmin(lo[1], X[a].y); hi[1] = fmax(hi[1], X[a].y);
+      lo[2] = fmin(lo[2], X[a].z); hi[2] = fmax(hi[2], X[a].z);
+    }
+    double* b = box + 8 * e;
+    for (int k = 0; k < 3; ++k) {
+      b[k] = lo[k] - rp.delta;
+      b[3 + k] = hi[k] + rp.delta;
+    }
+    b[6] = h;
+    b[7] = 0.0;
+  }
+  block_count_add(&st->degenerate, degenerate ? 1ull : 0ull);
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads) k_master_boxes(const double* __restrict__ xm,
+                                                            const int32_t* __restrict__ conn, int64_t Em,
+                                                            double delta, double* __restrict__ box) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Em) return;
+  V3 X[4];
+  for (int a = 0; a < NM; ++a) {
+    const int64_t n = conn[NM * e + a];
+    X[a] = {xm[3 * n], xm[3 * n + 1], xm[3 * n + 2]};
+  }
+  double lo[3] = {X[0].x, X[0].y, X[0].z}, hi[3] = {X[0].x, X[0].y, X[0].z};
+  double h2 = 0.0;
+  for (int a = 1; a < NM; ++a) {
+    lo[0] = fmin(lo[0], X[a].x); hi[0] = fmax(hi[0], X[a].x);
+    lo[1] = fmin(lo[1], X[a].y); hi[1] = fmax(hi[1], X[a].y);
+    lo[2] = fmin(lo[2], X[a].z); hi[2] = fmax(hi[2], X[a].z);
+  }
+  for (int a = 0; a < NM; ++a)
+    for (int b = a + 1; b < NM; ++b) {
+      const V3 d = sub(X[a], X[b]);
+      h2 = fmax(h2, dot(d, d));
+    }
+  double* b = box + 8 * e;
+  for (int k = 0; k < 3; ++k) {
+    b[k] = lo[k] - delta;
+    b[3 + k] = hi[k] + delta;
+  }
+  b[6] = sqrt(h2);
+  b[7] = 0.0;
+}
+
+// One block per chunk: min of lo, max of hi, max of h over its elements.
+__global__ void __launch_bounds__(256) k_chunk_reduce(const Chunk* __restrict__ chunks,
+                                                      const double* __restrict__ box_s,
+                                                      const double* __restrict__ box_m,
+                                                      double* __restrict__ red) {
+  const Chunk c = chunks[blockIdx.x];
+  const double* box = c.side == 0 ? box_s : box_m;
+  double v[7] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX, 0.0};
+  for (int64_t e = c.begin + threadIdx.x; e < c.end; e += blockDim.x) {
+    const double* b = box + 8 * e;
+    for (int k = 0; k < 3; ++k) {
+      v[k] = fmin(v[k], b[k]);
+      v[3 + k] = fmax(v[3 + k], b[3 + k]);
+    }
+    v[6] = fmax(v[6], b[6]);
+  }
+  __shared__ double sh[8][7];
+  for (int k = 0; k < 7; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = k < 3 ? fmin(x, y) : fmax(x, y);
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    const int k = threadIdx.x;
+    double x = sh[0][k];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = k < 3 ? fmin(x, sh[w][k]) : fmax(x, sh[w][k]);
+    red[8 * blockIdx.x + k] = x;
+  }
+}
+
+// One block per interface: combine its chunks and set up the bin grid.
+__global__ void __launch_bounds__(256) k_grid_params(const int32_t* __restrict__ chunk_ptr,
+                                                     const double* __restrict__ red,
+                                                     const int64_t* __restrict__ bin_cap_off, double delta,
+                                                     GridParams* __restrict__ grid) {
+  const int i = blockIdx.x;
+  const int32_t c0 = chunk_ptr[i], c1 = chunk_ptr[i + 1];
+  double v[7] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX, 0.0};
+  for (int32_t c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+    for (int k = 0; k < 7; ++k) v[k] = k < 3 ? fmin(v[k], red[8 * c + k]) : fmax(v[k], red[8 * c + k]);
+  __shared__ double sh[8][7];
+  for (int k = 0; k < 7; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = k < 3 ? fmin(x, y) : fmax(x, y);
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < 7; ++k)
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) sh[0][k] = k < 3 ? fmin(sh[0][k], sh[w][k]) : fmax(sh[0][k], sh[w][k]);
+  GridParams g;
+  const int64_t cap = bin_cap_off[i + 1] - bin_cap_off[i];
+  if (c1 <= c0 || !(sh[0][0] <= sh[0][3])) {   // empty interface
+    for (int k = 0; k < 3; ++k) { g.org[k] = 0.0; g.beta[k] = 1.0; g.nb[k] = 1; }
+  } else {
+    double beta_min = (1.0 + 1e-9) * sh[0][6] + 2.0 * delta;
+    if (!(beta_min > 0.0)) beta_min = 1.0;
+    for (int attempt = 0; attempt < 200; ++attempt) {
+      int64_t tot = 1;
+      for (int k = 0; k < 3; ++k) {
+        g.org[k] = sh[0][k] - beta_min;
+        const double L = (sh[0][3 + k] + beta_min) - g.org[k];
+        double nbd = floor(L / beta_min);
+        nbd = fmin(fmax(nbd, 1.0), 1.0e6);
+        g.nb[k] = (int32_t)nbd;
+        g.beta[k] = L / nbd;
+        tot *= g.nb[k];
+      }
+      if (tot <= cap) break;
+      beta_min *= 1.25;
+    }
+  }
+  g.pad = 0;
+  g.n_bins = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+  g.bin_off = 0;
+  grid[i] = g;
+}
+
+// Exclusive scan of n_bins over interfaces (single block); total -> status.
+__global__ void __launch_bounds__(1024) k_bin_offsets(GridParams* __restrict__ grid, int32_t n_if,
+                                                      int64_t bin_cap, DevStatus* st) {
+  __shared__ int64_t warp_tot[32];
+  __shared__ int64_t carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < n_if; b0 += 1024) {
+    const int i = b0 + threadIdx.x;
+    const int64_t v = i < n_if ? grid[i].n_bins : 0;
+    int64_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      const int64_t t = warp_tot[lane];
+      int64_t ti = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, ti, o);
+        if (lane >= o) ti += y;
+      }
+      warp_tot[lane] = ti - t;
+    }
+    __syncthreads();
+    const int64_t excl = inc - v + warp_tot[w] + carry_s;
+    if (i < n_if) grid[i].bin_off = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry_s = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->n_bins = (unsigned long long)carry_s;
+    if (carry_s > bin_cap) st->over_bins = (unsigned long long)carry_s;
+  }
+}
+
+}  // namespace
+
+RunParams run_params(const mortar_ctx* c) {
+  RunParams rp;
+  rp.lm = c->opt.lm;
+  rp.d_domain = c->opt.d_domain;
+  rp.newton_max_iter = c->opt.newton_max_iter;
+  rp.pad = 0;
+  rp.newton_tol = c->opt.newton_tol;
+  rp.clip_tol_rel = c->opt.clip_tol_rel;
+  rp.merge_tol_rel = c->opt.merge_tol_rel;
+  rp.area_tol_rel = c->opt.area_tol_rel;
+  rp.delta = c->opt.search_inflation;
+  return rp;
+}
+
+void launch_slave_precompute(mortar_ctx* c, const RunParams& rp) {
+  if (c->Es == 0) return;
+  const unsigned g = (unsigned)((c->Es + kThreads - 1) / kThreads);
+  DevStatus* st = c->dstat.as<DevStatus>();
+  if (c->nen_s == 4)
+    k_slave_precompute<4><<<g, kThreads, 0, c->stream>>>(c->xs.as<double>(), c->conn_s.as<int32_t>(), c->Es, rp,
+                                                          c->srec.as<double>(), c->De.as<double>(),
+                                                          c->box_s.as<double>(), st);
+  else
+    k_slave_precompute<3><<<g, kThreads, 0, c->stream>>>(c->xs.as<double>(), c->conn_s.as<int32_t>(), c->Es, rp,
+                                                          c->srec.as<double>(), c->De.as<double>(),
+                                                          c->box_s.as<double>(), st);
+}
+
+void launch_master_boxes(mortar_ctx* c, const RunParams& rp) {
+  if (c->Em == 0) return;
+  const unsigned g = (unsigned)((c->Em + kThreads - 1) / kThreads);
+  if (c->nen_m == 4)
+    k_master_boxes<4><<<g, kThreads, 0, c->stream>>>(c->xm.as<double>(), c->conn_m.as<int32_t>(), c->Em, rp.delta,
+                                                     c->box_m.as<double>());
+  else
+    k_master_boxes<3><<<g, kThreads, 0, c->stream>>>(c->xm.as<double>(), c->conn_m.as<int32_t>(), c->Em, rp.delta,
+                                                     c->box_m.as<double>());
+}
+
+void launch_grid_params(mortar_ctx* c, const RunParams& rp) {
+  if (c->n_chunks > 0)
+    k_chunk_reduce<<<(unsigned)c->n_chunks, 256, 0, c->stream>>>(c->chunks.as<Chunk>(), c->box_s.as<double>(),
+                                                                 c->box_m.as<double>(), c->chunk_red.as<double>());
+  k_grid_params<<<(unsigned)c->n_if, 256, 0, c->stream>>>(c->chunk_ptr.as<int32_t>(), c->chunk_red.as<double>(),
+                                                          c->bin_cap_off.as<int64_t>(), rp.delta,
+                                                          c->grid.as<GridParams>());
+  k_bin_offsets<<<1, 1024, 0, c->stream>>>(c->grid.as<GridParams>(), c->n_if, c->bin_cap,
+                                           c->dstat.as<DevStatus>());
+}
+
+}  // namespace mortar

@@ -1,0 +1,261 @@
+"""GPU parity of the forward path (search, integration, assembly) against the oracle.
+
+Everything goes through the C ABI via the Python binding.  Pair sets must be
+identical; CSR patterns identical; values within 1e-12 relative (max abs
+difference over max abs reference value).
+"""
+import numpy as np
+import pytest
+
+from paper_2202_03933_gb300 import inputs
+from gpu_util import blocks_parity, csr_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_03933_gb300 import build, mortar
+    build()
+    return mortar
+
+
+def swap_sides(itf, name):
+    return inputs.Interface(name, itf.xm, itf.conn_m, itf.type_m, itf.xs, itf.conn_s, itf.type_s,
+                            lm=itf.lm, delta=itf.delta)
+
+
+def small_cases():
+    dual_seg = inputs.planar_noisy(9, 8, 1, 41, "dual_seg")
+    tri_slave = swap_sides(inputs.mixed_tri(14, 11, name="m"), "tri_slave")
+    cyl = inputs.cylinder_patch(24, 21, name="cyl_small")
+    return [
+        ("planar_8x7", inputs.planar_8x7(), 0),
+        ("planar_8x7_seg", inputs.planar_8x7(), 1),
+        ("cyl_small_dual", cyl, 0),
+        ("cyl_small_dual_seg", cyl, 1),
+        ("mixed_small", inputs.mixed_tri(30, 40, name="mixed_small"), 0),
+        ("mixed_small_dual", inputs.mixed_tri(30, 40, lm=1, name="mixed_small_dual"), 0),
+        ("tri_slave", tri_slave, 0),
+        ("tri_slave_seg", tri_slave, 1),
+        ("dual_seg", dual_seg, 1),
+        ("matching_std", inputs.matching(7, 0, noise=0.15)[0], 1),
+        ("matching_dual", inputs.matching(7, 1, noise=0.15)[0], 0),
+        ("ragged_33x29", inputs.planar_noisy(33, 29, 0, 43, "ragged"), 0),
+    ]
+
+
+def run_gpu(mt, itf, d_domain, graph=False):
+    m = mt.Mortar(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
+    m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+    if graph:
+        m.run_graph()
+        m.run_graph()
+    else:
+        m.evaluate()
+    return m
+
+
+@pytest.mark.parametrize("name,itf,d_domain", small_cases(), ids=[c[0] for c in small_cases()])
+def test_forward_parity_small(mt, orc, name, itf, d_domain):
+    o = orc.make_opts(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
+    ref = orc.evaluate(itf, o, search="bruteforce")
+    m = run_gpu(mt, itf, d_domain)
+    s, mm = m.pairs()
+    assert np.array_equal(s, ref.s) and np.array_equal(mm, ref.m)
+    Mb, Db, ne = m.pair_blocks(with_D=d_domain == 1)
+    assert np.array_equal(ne, ref.nonempty)
+    blocks_parity(Mb, ref.Mb)
+    if d_domain == 1:
+        blocks_parity(Db, ref.Db)
+    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
+    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    st = m.stats()
+    assert st["n_nonempty"] == ref.stats["nonempty"]
+    assert st["n_gauss_points"] == ref.stats["gauss_points"]
+    assert st["n_newton_fail"] == 0 and st["n_clip_overflow"] == 0
+
+
+def test_deterministic_and_graph_replay(mt):
+    itf = inputs.mixed_tri(40, 55, name="det")
+    a = run_gpu(mt, itf, 0)
+    b = run_gpu(mt, itf, 0, graph=True)
+    for w in (mt.MATRIX_D, mt.MATRIX_M):
+        A, B = a.scipy(w), b.scipy(w)
+        assert np.array_equal(A.indptr, B.indptr) and np.array_equal(A.indices, B.indices)
+        assert np.array_equal(A.data, B.data)   # bitwise
+    Ma, _, _ = a.pair_blocks()
+    Mb, _, _ = b.pair_blocks()
+    assert np.array_equal(Ma, Mb)
+
+
+def test_coordinate_update_reuses_context(mt, orc):
+    itf = inputs.planar_noisy(12, 10, 0, 51, "upd")
+    m = run_gpu(mt, itf, 0)
+    itf2 = inputs.planar_noisy(12, 10, 0, 52, "upd2")
+    m.set_coordinates(itf2.xs, itf2.xm)
+    m.evaluate()
+    ref = orc.evaluate(itf2)
+    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_no_overlap_gives_empty_M(mt):
+    itf = inputs.planar_noisy(4, 3, 0, 1, "far")
+    itf.xm = itf.xm + np.array([5.0, 0.0, 0.0])
+    m = run_gpu(mt, itf, 0)
+    assert m.stats()["n_pairs"] == 0
+    M = m.scipy(mt.MATRIX_M)
+    assert M.nnz == 0 and M.shape == (25, 16)
+    assert abs(m.scipy(mt.MATRIX_D).sum() - 1.0) < 1e-13
+
+
+def test_empty_slave_mesh(mt):
+    xs = np.zeros((0, 3))
+    cs = np.zeros((0, 4), np.int32)
+    itf = inputs.planar_8x7()
+    m = mt.Mortar()
+    m.set_interface(xs, cs, itf.xm, itf.conn_m)
+    m.evaluate()
+    assert m.stats()["n_pairs"] == 0
+    assert m.csr_size(mt.MATRIX_M) == (0, itf.xm.shape[0], 0)
+
+
+def test_single_element_each(mt, orc):
+    xs = inputs.grid_nodes(1, 1)
+    cs = inputs.grid_quad4(1, 1)
+    xm = inputs.grid_nodes(1, 1, 0.3, -0.2, 1.3, 0.8)
+    itf = inputs.Interface("one", xs, cs, 4, xm, cs.copy(), 4)
+    m = run_gpu(mt, itf, 1)
+    ref = orc.evaluate(itf, orc.make_opts(d_domain=1))
+    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    assert abs(m.scipy(mt.MATRIX_M).sum() - 0.7 * 0.8) < 1e-15
+
+
+def test_touching_only_pairs_are_empty(mt, orc):
+    """Neighbouring elements that share only an edge: candidate pair, empty clip."""
+    itf = inputs.matching(3, 0)[0]
+    m = run_gpu(mt, itf, 0)
+    ref = orc.evaluate(itf)
+    _, _, ne = m.pair_blocks()
+    assert np.array_equal(ne, ref.nonempty) and (~ne).sum() > 0
+    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+
+
+def test_bad_connectivity_rejected(mt):
+    itf = inputs.planar_8x7()
+    cs = itf.conn_s.copy()
+    cs[3, 2] = 10_000
+    m = mt.Mortar()
+    with pytest.raises(mt._native.MortarError, match="INVALID_ARG"):
+        m.set_interface(itf.xs, cs, itf.xm, itf.conn_m)
+
+
+def test_degenerate_slave_element_flagged(mt):
+    itf = inputs.planar_noisy(3, 3, 0, 2, "deg")
+    xs = itf.xs.copy()
+    cs = itf.conn_s.copy()
+    cs[4] = [cs[4][0], cs[4][0], cs[4][0], cs[4][0]]   # zero-area element
+    m = mt.Mortar()
+    m.set_interface(xs, cs, itf.xm, itf.conn_m)
+    assert m.evaluate() == -2   # MORTAR_ERR_DEGENERATE, results still written
+    Mb, _, ne = m.pair_blocks()
+    s, _ = m.pairs()
+    assert not ne[s == 4].any()
+
+
+def test_capacity_error_on_small_buffer(mt):
+    import ctypes
+    itf = inputs.planar_8x7()
+    m = run_gpu(mt, itf, 0)
+    nr, nc, nnz = m.csr_size(mt.MATRIX_M)
+    rp = np.empty(nr + 1, np.int64)
+    ci = np.empty(nnz, np.int32)
+    va = np.empty(nnz)
+    r = mt.lib().mortar_csr_copy(m.h, 1, rp.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p),
+                                 va.ctypes.data_as(ctypes.c_void_p), nnz - 1, 0)
+    assert r == -4
+
+
+# ---------------------------------------------------------------- full sizes
+def _sampled_rows(orc, itf, s, m, rows, o):
+    """Oracle CSR rows for the given slave nodes, from only the pairs whose
+    slave element touches one of them."""
+    cs = np.asarray(itf.conn_s)
+    touch = np.isin(cs, rows).any(axis=1)
+    keep = touch[s]
+    Mb, Db, ne, _ = orc.pair_blocks(itf, s[keep], m[keep], o)
+    _, De = orc.element_blocks(itf, o.lm)
+    D, M = orc.assemble(itf, s[keep], m[keep], Mb, Db, ne, De, o.d_domain)
+    return D[rows], M[rows]
+
+
+@pytest.mark.parametrize("cfg", ["cylinder_200x173", "mixed_300x400"])
+def test_full_size_parity(mt, orc, cfg):
+    itf = inputs.by_name(cfg)
+    o = orc.make_opts(lm=itf.lm, delta=itf.delta, n_threads=16)
+    ref = orc.evaluate(itf, o)
+    m = run_gpu(mt, itf, 0, graph=True)
+    s, mm = m.pairs()
+    assert np.array_equal(s, ref.s) and np.array_equal(mm, ref.m)
+    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
+    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    if itf.lm == 1:
+        D = m.scipy(mt.MATRIX_D)
+        off = D - __import__("scipy.sparse", fromlist=["diags"]).diags(D.diagonal())
+        assert abs(off).max() <= 1e-14 * D.diagonal().max()
+
+
+def test_full_size_planar_2000(mt, orc):
+    """The benchmark workload in its benchmark launch (graph replay): exact
+    pair set against the oracle's binned search, sampled pair blocks and
+    sampled CSR rows against the oracle, and closed-form invariants."""
+    itf = inputs.planar_2000x1733()
+    m = run_gpu(mt, itf, 0, graph=True)
+    s, mm = m.pairs()
+    rs, rm = orc.search_binned(itf)
+    assert np.array_equal(s, rs) and np.array_equal(mm, rm)
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(s.size, 20000, replace=False))
+    idx = np.unique(np.concatenate([idx, [0, s.size - 1]]))
+    o = orc.make_opts(lm=itf.lm, delta=itf.delta, n_threads=16)
+    Mb_ref, _, ne_ref, _ = orc.pair_blocks(itf, s[idx], mm[idx], o)
+    Mb, _, ne = m.pair_blocks()
+    assert np.array_equal(ne[idx], ne_ref)
+    blocks_parity(Mb[idx], Mb_ref)
+    rows = np.unique(np.concatenate([rng.choice(itf.xs.shape[0], 300, replace=False), [0, itf.xs.shape[0] - 1]]))
+    Dr, Mr = _sampled_rows(orc, itf, s, mm, rows, o)
+    D = m.scipy(mt.MATRIX_D)
+    M = m.scipy(mt.MATRIX_M)
+    csr_parity(D[rows], Dr)
+    csr_parity(M[rows], Mr)
+    # invariants at full size: unit square fully covered
+    assert abs(D.sum() - 1.0) < 1e-12 and abs(M.sum() - 1.0) < 1e-12
+    for c in (0, 1):
+        assert np.abs(M @ itf.xm[:, c] - D @ itf.xs[:, c]).max() < 1e-15
+    off = D - __import__("scipy.sparse", fromlist=["diags"]).diags(D.diagonal())
+    assert abs(off).max() <= 1e-14 * D.diagonal().max()
+
+
+def test_batched_block_diagonal(mt, orc):
+    itfs = inputs.batched_512()[:40]
+    m = mt.Mortar()
+    m.set_batch(itfs)
+    m.run_graph()
+    m.run_graph()
+    D = m.scipy(mt.MATRIX_D)
+    M = m.scipy(mt.MATRIX_M)
+    sn, mn = m.offsets["slave_nodes"], m.offsets["master_nodes"]
+    for k, itf in enumerate(itfs):
+        ref = orc.evaluate(itf)
+        csr_parity(D[sn[k]:sn[k + 1], sn[k]:sn[k + 1]], ref.D)
+        csr_parity(M[sn[k]:sn[k + 1], mn[k]:mn[k + 1]], ref.M)
+    # nothing outside the diagonal blocks
+    rows = np.repeat(np.arange(M.shape[0]), np.diff(M.indptr))
+    blk_r = np.searchsorted(sn, rows, side="right") - 1
+    blk_c = np.searchsorted(mn, M.indices, side="right") - 1
+    assert np.array_equal(blk_r, blk_c)
