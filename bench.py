@@ -1,0 +1,372 @@
+"""Benchmark: mortar pairs integrated per second (D + M, FP64) with the adjoint,
+on one GB300, against the FP64 roofline.
+
+One step = the whole hot path on one synthetic interface, replayed as one
+CUDA graph: element precompute, binned search, per-pair segment integration,
+CSR assembly of D and M, and the adjoint (gradient of the weighted gap
+lambda.(D Xs - M Xm) w.r.t. all nodal coordinates).  Inputs are resident in
+HBM before the timed region; the working set (~2 GB) is far larger than L2, so
+no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload planar_2000x1733] [--no-cpu-baseline]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of the
+workload (the interface is not sharded, there is no collective on the data
+path); value = all ranks' pairs / max-over-ranks time ("scaling": "weak").
+
+``--impl reference`` times the CPU oracle (the only reference that exists for
+this method: the paper ships no code) on a bounded sample of the same
+workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mortar pairs integrated/sec (D+M, FP64) and fwd+adjoint time on 1 GB300 vs FP64 roofline"
+UNIT = "pairs/s"
+
+# Algorithmic FP64 flops of the per-pair integration, counted by the oracle's
+# flop-counting scalar over the workload's full pair set
+# (`python -m oracle.count_flops <workload>`; + - * / sqrt = 1 flop each).
+ALGO_FLOPS = {
+    "planar_2000x1733": {"pairs": 14936836, "flops": 425035751226},
+    "mixed_300x400": {"pairs": 960724, "flops": 7494813947},
+    "cylinder_200x173": {"pairs": 171739, "flops": 3512674839},
+}
+
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes
+# per SM per clock (4 flop/clk/SM) x 2070 MHz maximum SM clock = 1.259 TFLOP/s,
+# which is the part's nominal 1.25 TFLOP/s FP64 rate.
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_PER_SM = 4
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="planar_2000x1733")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            with open(self.path) as f:
+                for r in csv.reader(f):
+                    if len(r) >= 9:
+                        rows.append([x.strip() for x in r])
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample_step(itf, rows: int, threads: int):
+    """One bounded sample of the workload through the oracle: the slave
+    elements of the first `rows` element rows, all master elements; binned
+    search, per-pair integration, assembly and the forward-mode gradient."""
+    import numpy as np
+    import oracle
+    from paper_2202_03933_gb300 import inputs
+    n = int(round(len(itf.conn_s) ** 0.5))
+    ne = rows * n
+    sub = inputs.Interface("sample", itf.xs, itf.conn_s[:ne], itf.type_s, itf.xm, itf.conn_m, itf.type_m,
+                           lm=itf.lm, delta=itf.delta)
+    lam = np.random.default_rng(0).uniform(-1, 1, itf.xs.shape)
+    o = oracle.make_opts(lm=itf.lm, delta=itf.delta, n_threads=threads)
+    t0 = time.perf_counter()
+    res = oracle.evaluate(sub, o)
+    oracle.weighted_gap_grad(sub, lam, res.s, res.m, o)
+    dt = time.perf_counter() - t0
+    return int(res.s.size), dt, ne
+
+
+def cpu_baseline(itf, target_s: float = 12.0) -> dict:
+    threads = os.cpu_count() or 1
+    pairs, dt, ne = oracle_sample_step(itf, 2, threads)
+    rows = max(2, min(200, int(2 * target_s / max(dt, 1e-3))))
+    pairs, dt, ne = oracle_sample_step(itf, rows, threads)
+    return {"value": pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{ne} of {len(itf.conn_s)} slave elements ({rows} element rows) x all master "
+                      f"elements: {pairs} pairs; oracle search + integration + assembly + "
+                      f"forward-mode gradient, {dt:.1f} s on {threads} host threads"}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle on a bounded sample per step."""
+    if rank != 0:
+        return
+    from paper_2202_03933_gb300 import inputs
+    itf = inputs.by_name(args.workload)
+    threads = os.cpu_count() or 1
+    rows = 4
+    for _ in range(args.warmup):
+        oracle_sample_step(itf, rows, threads)
+    tot_pairs, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        p, dt, ne = oracle_sample_step(itf, rows, threads)
+        tot_pairs += p
+        tot_s += dt
+    value = tot_pairs / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "sample_element_rows": rows},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{ne} slave elements ({rows} element rows) x all master elements "
+                                       "per step, oracle search + integration + assembly + gradient"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2202_03933_gb300 import build, inputs, mortar
+
+    build()
+    itf = inputs.by_name(args.workload)
+    if isinstance(itf, list):
+        raise SystemExit("use a single-interface workload for the headline benchmark")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xs = torch.from_numpy(itf.xs).to(dev)
+    xm = torch.from_numpy(itf.xm).to(dev)
+    cs = torch.from_numpy(itf.conn_s).to(dev)
+    cm = torch.from_numpy(itf.conn_m).to(dev)
+    lam_h = np.random.default_rng(1).uniform(-1, 1, itf.xs.shape)
+    lam = torch.from_numpy(lam_h).to(dev)
+    stream = torch.cuda.current_stream()
+    m = mortar.Mortar(lm=itf.lm, delta=itf.delta, stream=stream.cuda_stream)
+    m.set_interface(xs, cs, xm, cm)
+    m.set_timing(True)
+    for _ in range(max(args.warmup, 3)):
+        m.run_graph(lam)
+    torch.cuda.synchronize()
+    st0 = m.stats()
+    per_step = []
+    t_int, t_adjp, t_adj, t_srch, t_asm = [], [], [], [], []
+    barrier(world)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            m.run_graph(lam)
+            s = m.stats()
+            t_int.append(s["ms_integrate"])
+            t_adjp.append(s["ms_adjoint_pairs"])
+            t_adj.append(s["ms_adjoint"])
+            t_srch.append(s["ms_search"])
+            t_asm.append(s["ms_assemble"])
+            per_step.append(s["ms_total"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(world, ms)
+    st = m.stats()
+    n_pairs = st["n_pairs"]
+    value = world * n_pairs / (ms / 1e3)
+
+    # ---- roofline of the integration kernel (algorithmic flops / kernel time)
+    mean = lambda v: sum(v) / len(v)  # noqa: E731
+    ms_int = mean(t_int)
+    af = ALGO_FLOPS.get(args.workload)
+    roof = None
+    if af and af["pairs"] == n_pairs:
+        achieved = af["flops"] / (ms_int / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_integrate (per-pair segment integration)",
+                "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_kind": "derived FP64: 152 SM x 4 flop/clk x 2070 MHz",
+                "algorithmic_flops_per_launch": af["flops"], "ms_per_launch": round(ms_int, 4)}
+
+    # ---- FP64 probe (measured peak, for context)
+    probe = None
+    try:
+        blocks, threads, iters = SM_COUNT * 8, 256, 20000
+        sink = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+        mortar.probe_dfma(blocks, threads, 100, sink=sink)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mortar.probe_dfma(blocks, threads, iters, sink=sink)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pm = e0.elapsed_time(e1)
+        probe = {"tflops": round(blocks * threads * 8 * 2 * iters / (pm / 1e3) / 1e12, 4), "ms": round(pm, 3)}
+    except Exception as ex:   # measurement context only
+        probe = {"error": str(ex)}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        xs_p = torch.from_numpy(itf.xs).pin_memory()
+        xm_p = torch.from_numpy(itf.xm).pin_memory()
+        lam_p = torch.from_numpy(lam_h).pin_memory()
+        nr, _, nnzD = m.csr_size(mortar.MATRIX_D)
+        _, _, nnzM = m.csr_size(mortar.MATRIX_M)
+        outs = {k: torch.empty(n, dtype=t).pin_memory() for k, n, t in (
+            ("rpD", nr + 1, torch.int64), ("ciD", nnzD, torch.int32), ("vaD", nnzD, torch.float64),
+            ("rpM", nr + 1, torch.int64), ("ciM", nnzM, torch.int32), ("vaM", nnzM, torch.float64),
+            ("gs", itf.xs.size, torch.float64), ("gm", itf.xm.size, torch.float64))}
+        import ctypes
+        L = mortar.lib()
+        P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        Jc = ctypes.c_double()
+
+        def e2e_step():
+            mortar.call("mortar_set_coordinates", m.h, P(xs_p), P(xm_p), 0)
+            mortar.call("mortar_run_graph", m.h, P(lam_p), 0, ok=(0, -3))
+            mortar.call("mortar_get_gradient", m.h, ctypes.byref(Jc), P(outs["gs"]), P(outs["gm"]), 0)
+            mortar.call("mortar_csr_copy", m.h, 0, P(outs["rpD"]), P(outs["ciD"]), P(outs["vaD"]), nnzD, 0)
+            mortar.call("mortar_csr_copy", m.h, 1, P(outs["rpM"]), P(outs["ciM"]), P(outs["vaM"]), nnzM, 0)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(world, (time.perf_counter() - t0) * 1e3 / args.steps)
+        h2d = xs_p.numel() * 8 + xm_p.numel() * 8 + lam_p.numel() * 8
+        d2h = sum(t.numel() * t.element_size() for t in outs.values()) + 8
+        e2e = {"value": world * n_pairs / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e2e_ms, 3),
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        del L
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "slave": "2000x2000 quad4" if args.workload == "planar_2000x1733"
+                   else None, "lm": "dual" if itf.lm == 1 else "standard", "pairs": n_pairs,
+                   "nonempty_pairs": st["n_nonempty"], "gauss_points": st["n_gauss_points"],
+                   "step": "search + integrate + assemble D,M + adjoint, one CUDA graph",
+                   "l2": "inputs and workspaces (~GBs) larger than the 129 MB L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "phases_ms": {"search": round(mean(t_srch), 4), "integrate": round(ms_int, 4),
+                      "assemble": round(mean(t_asm), 4), "adjoint": round(mean(t_adj), 4),
+                      "adjoint_pairs_kernel": round(mean(t_adjp), 4), "graph_total": round(mean(per_step), 4)},
+        "forward_pairs_per_s": world * n_pairs / ((mean(t_srch) + ms_int + mean(t_asm)) / 1e3),
+        "roofline": roof,
+        "fp64_probe": probe,
+        "e2e": e2e,
+        "gpu_launches": int(st0.get("graph_kernels", 0)) * args.steps,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(itf)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_setup()
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

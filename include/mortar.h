@@ -28,9 +28,9 @@
  *  - `on_device` = 1: the pointer is CUDA device memory of the current device;
  *    0: host memory.  Input buffers are only read during the call; the
  *    library keeps its own copies.  Output buffers belong to the caller.
- *  - All device work runs on the stream given to mortar_create() (NULL = the
- *    legacy default stream).  Calls returning host data synchronise that
- *    stream only.
+ *  - All device work runs on the stream given to mortar_create() (NULL = a
+ *    non-blocking stream the context creates and owns).  Calls returning host
+ *    data synchronise that stream only.
  *  - The library owns the context, its device workspaces and any captured
  *    CUDA graph; mortar_destroy() releases them.
  *  - Calls on one context are not thread-safe; distinct contexts are
@@ -91,7 +91,13 @@ typedef struct mortar_stats {
   int64_t nnz_D, nnz_M;
   int64_t n_bins;
   int64_t reruns;           /* capacity-driven re-executions of the last run */
-  float ms_search, ms_integrate, ms_assemble, ms_adjoint, ms_total; /* last run, CUDA events */
+  int64_t graph_kernels;    /* kernel nodes in the captured graph (0 before capture) */
+  /* phase times of the last run (CUDA events on the context's stream, also
+   * inside replayed graphs; 0 unless mortar_set_timing(ctx, 1)):
+   * search = precompute + grid + binning + candidates; integrate = the
+   * per-pair integration kernel; assemble = CSR assembly; adjoint = all
+   * adjoint kernels, of which adjoint_pairs is the per-pair reverse sweep. */
+  float ms_search, ms_integrate, ms_assemble, ms_adjoint, ms_adjoint_pairs, ms_total;
 } mortar_stats;
 
 typedef struct mortar_ctx mortar_ctx;
@@ -99,8 +105,9 @@ typedef struct mortar_ctx mortar_ctx;
 /* Fill `o` with the defaults listed above. */
 int mortar_default_options(mortar_options* o);
 
-/* Create a context.  `stream` is a cudaStream_t (NULL = default stream) that
- * every later call on this context uses.  Uses the current CUDA device. */
+/* Create a context.  `stream` is a cudaStream_t that every later call on this
+ * context uses (NULL: the context creates its own non-blocking stream).  Uses
+ * the current CUDA device. */
 int mortar_create(mortar_ctx** ctx, const mortar_options* o, void* stream);
 
 /* Release the context, its workspaces and graphs.  NULL is ignored. */

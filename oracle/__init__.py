@@ -56,6 +56,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("lm", ctypes.c_int32), ("d_domain", ctypes.c_int32),
                 ("tri_rule", ctypes.c_int32), ("fan", ctypes.c_int32),
                 ("newton_max_iter", ctypes.c_int32), ("n_threads", ctypes.c_int32),
+                ("terms", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("newton_tol", ctypes.c_double),
                 ("clip_tol_rel", ctypes.c_double), ("merge_tol_rel", ctypes.c_double),
                 ("area_tol_rel", ctypes.c_double)]
@@ -63,8 +64,8 @@ class Opts(ctypes.Structure):
 
 def make_opts(lm=0, d_domain=0, delta=1e-9, tri_rule=7, fan=0, newton_tol=1e-14,
               newton_max_iter=20, clip_tol_rel=1e-12, merge_tol_rel=1e-10,
-              area_tol_rel=1e-14, n_threads=1) -> Opts:
-    return Opts(lm, d_domain, tri_rule, fan, newton_max_iter, n_threads, delta,
+              area_tol_rel=1e-14, n_threads=1, terms=3) -> Opts:
+    return Opts(lm, d_domain, tri_rule, fan, newton_max_iter, n_threads, terms, 0, delta,
                 newton_tol, clip_tol_rel, merge_tol_rel, area_tol_rel)
 
 
@@ -275,7 +276,10 @@ def evaluate(itf, opts: Opts | None = None, search: str = "binned", pairs=None) 
 
 
 def weighted_gap_grad(itf, lam, s, m, opts: Opts | None = None):
-    """J = sum_j lam_j.((D Xs)_j - (M Xm)_j) and dJ/dXs, dJ/dXm (forward-mode)."""
+    """J = sum_j lam_j.((D Xs)_j - (M Xm)_j) and dJ/dXs, dJ/dXm (forward-mode).
+
+    ``opts.terms`` selects the terms: 1 = lam.D Xs only, 2 = -lam.M Xm only,
+    3 = both (the functional)."""
     lib = _load()
     o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
     xs, cs, xm, cm = _mesh_arrays(itf)

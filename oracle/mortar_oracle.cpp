@@ -132,6 +132,8 @@ struct Opts {
   int32_t fan;           // 0 = centroid fan, 1 = ear fan from vertex 0
   int32_t newton_max_iter;
   int32_t n_threads;
+  int32_t terms;         // weighted gap terms: bit 0 = lambda.D Xs, bit 1 = lambda.M Xm
+  int32_t pad;
   double delta;          // search inflation
   double newton_tol;
   double clip_tol_rel, merge_tol_rel, area_tol_rel;
@@ -778,8 +780,12 @@ int64_t oracle_count_pair_flops(const double* xs, const int32_t* cs, int32_t nen
                                 const double* xm, const int32_t* cm, int32_t nen_m,
                                 const Opts* o, const int32_t* ps, const int32_t* pm, int64_t P) {
   uint64_t total = 0;
-  Stats st;
+  const int nt = o->n_threads > 0 ? o->n_threads : 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(nt) reduction(+ : total)
+#endif
   for (int64_t p = 0; p < P; ++p) {
+    Stats st;
     SlaveData<double> Sd;
     load_slave<double>(Sd, xs, cs, nen_s, ps[p], o->lm);
     SlaveData<Counted> S;
@@ -807,7 +813,8 @@ int64_t oracle_count_pair_flops(const double* xs, const int32_t* cs, int32_t nen
 }
 
 // Weighted gap functional J = sum_j lambda_j . ((D X_s)_j - (M X_m)_j) and its
-// gradient with respect to every slave and master coordinate, by forward-mode
+// gradient with respect to every slave and master coordinate (or of one of the
+// two terms alone, selected by Opts::terms), by forward-mode
 // dual numbers: Dual<24> over the 8 nodes of each pair, Dual<12> over the
 // slave nodes for the element-domain D.  Contributions are summed in pair
 // order, then element order.
@@ -817,10 +824,15 @@ int oracle_weighted_gap_grad(const double* xs, int64_t Ns, const int32_t* cs, in
                              const double* lambda, double* J_out, double* gs, double* gm) {
   for (int64_t i = 0; i < 3 * Ns; ++i) gs[i] = 0.0;
   for (int64_t i = 0; i < 3 * Nm; ++i) gm[i] = 0.0;
-  double J = 0.0;
   typedef Dual<24> D24;
-  Stats st;
+  const int nt = o->n_threads > 0 ? o->n_threads : 1;
+  // per-pair value and 24 derivatives, computed independently
+  std::vector<double> blk((size_t)P * 25, 0.0);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+#endif
   for (int64_t p = 0; p < P; ++p) {
+    Stats st;
     const int32_t s = ps[p], m = pm[p];
     SlaveData<D24> S;
     S.nen = nen_s;
@@ -843,24 +855,37 @@ int oracle_weighted_gap_grad(const double* xs, int64_t Ns, const int32_t* cs, in
     D24 Jp(0.0);
     for (int a = 0; a < nen_s; ++a) {
       const double* lam = lambda + 3 * (int64_t)cs[(int64_t)nen_s * s + a];
-      for (int l = 0; l < nen_m; ++l) {
-        D24 g = lam[0] * Xm[l].x + lam[1] * Xm[l].y + lam[2] * Xm[l].z;
-        Jp = Jp - r.M[a][l] * g;
-      }
-      if (o->d_domain == 1)
+      if (o->terms & 2)
+        for (int l = 0; l < nen_m; ++l) {
+          D24 g = lam[0] * Xm[l].x + lam[1] * Xm[l].y + lam[2] * Xm[l].z;
+          Jp = Jp - r.M[a][l] * g;
+        }
+      if (o->d_domain == 1 && (o->terms & 1))
         for (int b = 0; b < nen_s; ++b) {
           D24 g = lam[0] * S.X[b].x + lam[1] * S.X[b].y + lam[2] * S.X[b].z;
           Jp = Jp + r.D[a][b] * g;
         }
     }
-    J += Jp.v;
-    for (int a = 0; a < nen_s; ++a)
-      for (int c = 0; c < 3; ++c) gs[3 * (int64_t)cs[(int64_t)nen_s * s + a] + c] += Jp.d[3 * a + c];
-    for (int l = 0; l < nen_m; ++l)
-      for (int c = 0; c < 3; ++c) gm[3 * (int64_t)cm[(int64_t)nen_m * m + l] + c] += Jp.d[12 + 3 * l + c];
+    double* out = blk.data() + 25 * p;
+    out[0] = Jp.v;
+    for (int k = 0; k < 24; ++k) out[1 + k] = Jp.d[k];
   }
-  if (o->d_domain == 0) {
+  double J = 0.0;
+  for (int64_t p = 0; p < P; ++p) {
+    const double* b = blk.data() + 25 * p;
+    const int32_t s = ps[p], m = pm[p];
+    J += b[0];
+    for (int a = 0; a < nen_s; ++a)
+      for (int c = 0; c < 3; ++c) gs[3 * (int64_t)cs[(int64_t)nen_s * s + a] + c] += b[1 + 3 * a + c];
+    for (int l = 0; l < nen_m; ++l)
+      for (int c = 0; c < 3; ++c) gm[3 * (int64_t)cm[(int64_t)nen_m * m + l] + c] += b[13 + 3 * l + c];
+  }
+  if (o->d_domain == 0 && (o->terms & 1)) {
     typedef Dual<12> D12;
+    std::vector<double> eb((size_t)Es * 13, 0.0);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nt)
+#endif
     for (int64_t e = 0; e < Es; ++e) {
       SlaveData<D12> S;
       S.nen = nen_s;
@@ -881,9 +906,15 @@ int oracle_weighted_gap_grad(const double* xs, int64_t Ns, const int32_t* cs, in
           Je = Je + De[a][b] * g;
         }
       }
-      J += Je.v;
+      double* out = eb.data() + 13 * e;
+      out[0] = Je.v;
+      for (int k = 0; k < 12; ++k) out[1 + k] = Je.d[k];
+    }
+    for (int64_t e = 0; e < Es; ++e) {
+      const double* b = eb.data() + 13 * e;
+      J += b[0];
       for (int a = 0; a < nen_s; ++a)
-        for (int c = 0; c < 3; ++c) gs[3 * (int64_t)cs[(int64_t)nen_s * e + a] + c] += Je.d[3 * a + c];
+        for (int c = 0; c < 3; ++c) gs[3 * (int64_t)cs[(int64_t)nen_s * e + a] + c] += b[1 + 3 * a + c];
     }
   }
   *J_out = J;

@@ -128,27 +128,41 @@ struct Phases {
   bool search = true, integrate = true, assemble = true, adjoint = false;
 };
 
+}  // namespace
+
+namespace mortar {
+// Phase event; inside a stream capture it becomes an event-record node of the
+// graph (cudaEventRecordExternal), so replays still time their phases.
+void record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  cudaEventRecordWithFlags(ev, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0);
+}
+}  // namespace mortar
+
+namespace {
+
 // Launch one run (no host synchronisation inside).
 void enqueue_run(mortar_ctx* c, const Phases& ph) {
   const RunParams rp = run_params(c);
   cudaStream_t st = c->stream;
   cudaMemsetAsync(c->dstat.p, 0, sizeof(DevStatus), st);
-  if (c->timing) cudaEventRecord(c->ev[0], st);
+  if (c->timing) record_event(c->ev[0], st);
   launch_slave_precompute(c, rp);
   launch_master_boxes(c, rp);
   launch_grid_params(c, rp);
   launch_bin_masters(c);
   launch_candidates(c);
-  if (c->timing) cudaEventRecord(c->ev[1], st);
+  if (c->timing) record_event(c->ev[1], st);
   if (ph.integrate) launch_integrate(c, rp);
-  if (c->timing) cudaEventRecord(c->ev[2], st);
+  if (c->timing) record_event(c->ev[2], st);
   if (ph.assemble) {
     launch_assemble(c, rp);
     launch_finalize_status(c);
   }
-  if (c->timing) cudaEventRecord(c->ev[3], st);
-  if (ph.adjoint) launch_adjoint(c, rp);
-  if (c->timing) cudaEventRecord(c->ev[4], st);
+  if (c->timing) record_event(c->ev[3], st);
+  if (ph.adjoint) launch_adjoint(c, rp, c->timing ? c->ev[5] : nullptr);
+  if (c->timing) record_event(c->ev[4], st);
   cudaMemcpyAsync(c->hstat, c->dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
 }
 
@@ -200,6 +214,8 @@ int finish_run(mortar_ctx* c, const Phases& ph) {
     cudaEventElapsedTime(&s.ms_assemble, c->ev[2], c->ev[3]);
     cudaEventElapsedTime(&s.ms_adjoint, c->ev[3], c->ev[4]);
     cudaEventElapsedTime(&s.ms_total, c->ev[0], c->ev[4]);
+    s.ms_adjoint_pairs = 0.0f;
+    if (ph.adjoint) cudaEventElapsedTime(&s.ms_adjoint_pairs, c->ev[3], c->ev[5]);
   }
   return MORTAR_OK;
 }
@@ -541,22 +557,28 @@ int mortar_run_graph(mortar_ctx* c, const double* lambda, int32_t on_device) {
     if (ph.adjoint) MORTAR_TRY(prepare_adjoint_buffers(c));
     cudaGraph_t g = nullptr;
     MORTAR_TRY(cuda_status(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)));
-    const bool timing = c->timing;
-    c->timing = false;
-    enqueue_run(c, ph);
-    c->timing = timing;
+    enqueue_run(c, ph);   // phase events (if timing) become event-record nodes
     MORTAR_TRY(cuda_status(cudaStreamEndCapture(c->stream, &g)));
+    c->graph_timing = c->timing;
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes) cudaGraphGetNodes(g, nodes.data(), &n_nodes);
+    int64_t nk = 0;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    c->stats.graph_kernels = nk;
     const int r2 = cuda_status(cudaGraphInstantiate(&c->graph_exec, g, 0));
     cudaGraphDestroy(g);
     MORTAR_TRY(r2);
     c->graph_with_adjoint = ph.adjoint;
     return r;
   }
-  if (c->timing) cudaEventRecord(c->ev[5], c->stream);
   MORTAR_TRY(cuda_status(cudaGraphLaunch(c->graph_exec, c->stream)));
-  if (c->timing) cudaEventRecord(c->ev[6], c->stream);
   const bool timing = c->timing;
-  c->timing = false;
+  c->timing = c->graph_timing;   // the captured graph records the phase events
   int r = finish_run(c, ph);
   c->timing = timing;
   if (r == 1) {   // grown: rerun eagerly, the graph is re-captured on the next call
@@ -566,9 +588,6 @@ int mortar_run_graph(mortar_ctx* c, const double* lambda, int32_t on_device) {
     c->search_valid = true;
     c->eval_valid = true;
     c->grad_valid = ph.adjoint;
-    if (timing) {
-      cudaEventElapsedTime(&c->stats.ms_total, c->ev[5], c->ev[6]);
-    }
     if (c->hstat->newton_fail) r = MORTAR_ERR_NEWTON;
   }
   return r;
@@ -583,6 +602,10 @@ int mortar_get_stats(mortar_ctx* c, mortar_stats* out) {
 int mortar_set_timing(mortar_ctx* c, int32_t enabled) {
   if (!c) return MORTAR_ERR_INVALID_ARG;
   c->timing = enabled != 0;
+  if (c->graph_exec && c->graph_timing != c->timing) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
   return MORTAR_OK;
 }
 

@@ -97,6 +97,7 @@ struct mortar_ctx {
   // ---- graph
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_with_adjoint = false;
+  bool graph_timing = false;
 };
 
 namespace mortar {
@@ -126,8 +127,9 @@ void launch_finalize_status(mortar_ctx* c);
 
 // k_adjoint.cu
 int prepare_adjoint_buffers(mortar_ctx* c);   // sizes per-pair adjoint buffers from n_pairs
-void launch_adjoint(mortar_ctx* c, const RunParams& rp);
+void launch_adjoint(mortar_ctx* c, const RunParams& rp, cudaEvent_t after_pairs);
 
 RunParams run_params(const mortar_ctx* c);
+void record_event(cudaEvent_t ev, cudaStream_t st);   // api.cu
 
 }  // namespace mortar

@@ -795,7 +795,7 @@ int prepare_adjoint_buffers(mortar_ctx* c) {
   return MORTAR_OK;
 }
 
-void launch_adjoint(mortar_ctx* c, const RunParams& rp) {
+void launch_adjoint(mortar_ctx* c, const RunParams& rp, cudaEvent_t after_pairs) {
   DevStatus* st = c->dstat.as<DevStatus>();
   const unsigned block = c->block_size > 0 ? (unsigned)c->block_size : 128u;
   const int32_t chunk = c->chunk_pairs > 0 ? c->chunk_pairs : 32;
@@ -807,6 +807,7 @@ void launch_adjoint(mortar_ctx* c, const RunParams& rp) {
   else if (c->nen_s == 4 && c->nen_m == 3) launch_pairs_nsnm<4, 3>(c, rp, grid, block, chunk);
   else if (c->nen_s == 3 && c->nen_m == 4) launch_pairs_nsnm<3, 4>(c, rp, grid, block, chunk);
   else launch_pairs_nsnm<3, 3>(c, rp, grid, block, chunk);
+  if (after_pairs) record_event(after_pairs, c->stream);
   if (c->nen_s == 4) launch_elems_ns<4>(c, rp); else launch_elems_ns<3>(c, rp);
   // master element -> pair lists
   cudaMemsetAsync(c->mp_cnt.p, 0, (size_t)std::max<int64_t>(c->Em, 1) * 4, c->stream);

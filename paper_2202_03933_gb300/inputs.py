@@ -265,6 +265,8 @@ def matching(n: int, lm: int, seed: int = SEED_BASE + 11, noise: float = 0.0) ->
 def by_name(name: str):
     table = {
         "planar_8x7": planar_8x7,
+        # smaller member of the planar family (profiling captures)
+        "planar_600x520": lambda: planar_noisy(600, 520, LM_DUAL, SEED_BASE + 6, "planar_600x520"),
         "cylinder_200x173": cylinder_patch,
         "mixed_300x400": mixed_tri,
         "batched_512": batched_512,
