@@ -204,6 +204,37 @@ int mortar_set_timing(mortar_ctx* ctx, int32_t enabled);
  * used by the autotuner. */
 int mortar_set_launch(mortar_ctx* ctx, int32_t block_size, int32_t chunk_pairs);
 
+/* Per-pair integration without any device allocation.  The paper has no
+ * counterpart to this call; it exists for callers that cannot call
+ * cudaMalloc -- code running while a host framework captures a CUDA graph or
+ * inside an allocator callback (allocating there is illegal or re-enters the
+ * allocator), and processes held to a device-memory budget fixed up front.
+ *
+ * Computes, for a caller-given pair list, what mortar_evaluate computes per
+ * pair (slave-element precomputation, then Algorithm 1 per pair): M_blocks /
+ * D_blocks (n_pairs x 16 FP64, layout of mortar_get_pair_blocks; D_blocks only
+ * in segment mode, may be NULL otherwise) and nonempty (n_pairs bytes).  All
+ * pointers are device memory of the current device, owned by the caller; ids
+ * are 0-based (pair_s < n_slave_elems, pair_m < n_master_elems).
+ *
+ * Scratch lives in one static device array of this library (room for
+ * 8192 slave elements, 4.7 MB, held on every device that loads the library
+ * until the process exits): n_slave_elems > 8192 returns MORTAR_ERR_CAPACITY
+ * and nothing runs.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array and clears its counters itself; calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it.
+ * Ids out of range return MORTAR_ERR_INVALID_ARG before any geometry kernel
+ * runs (this check synchronises `stream` once); the integration itself is
+ * stream-ordered on `stream` when the call returns MORTAR_OK. */
+int mortar_integrate_pairs_static(const mortar_options* o, void* stream,
+                                  const double* xs, int64_t n_slave_nodes,
+                                  const int32_t* conn_s, int64_t n_slave_elems, int32_t type_s,
+                                  const double* xm, int64_t n_master_nodes,
+                                  const int32_t* conn_m, int64_t n_master_elems, int32_t type_m,
+                                  const int32_t* pair_s, const int32_t* pair_m, int64_t n_pairs,
+                                  double* M_blocks, double* D_blocks, uint8_t* nonempty);
+
 /* Name of a status code. */
 const char* mortar_status_string(int status);
 

@@ -130,6 +130,25 @@ int prepare_adjoint_buffers(mortar_ctx* c);   // sizes per-pair adjoint buffers 
 void launch_adjoint(mortar_ctx* c, const RunParams& rp, cudaEvent_t after_pairs);
 
 RunParams run_params(const mortar_ctx* c);
+
+// Launchers on explicit pointers (no context), used by the no-allocation entry point.
+struct IntegrateArgs {
+  const int32_t* ps;
+  const int32_t* pm;
+  const double* srec;
+  const double* xm;
+  const int32_t* conn_m;
+  double* Mblk;
+  double* Dblk;
+  uint8_t* flag;
+  int64_t pair_cap;
+  DevStatus* st;
+  cudaStream_t stream;
+};
+void launch_slave_precompute_raw(const double* xs, const int32_t* conn_s, int64_t Es, int nen_s,
+                                 const RunParams& rp, double* srec, double* De, double* box, DevStatus* st,
+                                 cudaStream_t stream);
+void launch_integrate_raw(const IntegrateArgs& a, const RunParams& rp, int nen_s, int nen_m, int n_sm);
 void record_event(cudaEvent_t ev, cudaStream_t st);   // api.cu
 
 }  // namespace mortar

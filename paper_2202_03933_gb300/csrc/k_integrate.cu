@@ -263,7 +263,29 @@ void launch_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned blo
         chunk, st);
 }
 
+template <int NS, int NM>
+void launch_raw_nsnm(const IntegrateArgs& a, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk) {
+  if (rp.d_domain == 1)
+    k_integrate<NS, NM, true><<<grid, block, 0, a.stream>>>(a.ps, a.pm, a.srec, a.xm, a.conn_m, rp, a.Mblk, a.Dblk,
+                                                           a.flag, a.pair_cap, chunk, a.st);
+  else
+    k_integrate<NS, NM, false><<<grid, block, 0, a.stream>>>(a.ps, a.pm, a.srec, a.xm, a.conn_m, rp, a.Mblk, a.Dblk,
+                                                            a.flag, a.pair_cap, chunk, a.st);
+}
+
 }  // namespace
+
+void launch_integrate_raw(const IntegrateArgs& a, const RunParams& rp, int nen_s, int nen_m, int n_sm) {
+  const unsigned block = 128u;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<4, 4, false>, (int)block, 0);
+  if (per_sm < 1) per_sm = 1;
+  const unsigned grid = (unsigned)(n_sm * per_sm);
+  if (nen_s == 4 && nen_m == 4) launch_raw_nsnm<4, 4>(a, rp, grid, block, 32);
+  else if (nen_s == 4 && nen_m == 3) launch_raw_nsnm<4, 3>(a, rp, grid, block, 32);
+  else if (nen_s == 3 && nen_m == 4) launch_raw_nsnm<3, 4>(a, rp, grid, block, 32);
+  else launch_raw_nsnm<3, 3>(a, rp, grid, block, 32);
+}
 
 void launch_integrate(mortar_ctx* c, const RunParams& rp) {
   const unsigned block = c->block_size > 0 ? (unsigned)c->block_size : 128u;

@@ -416,6 +416,17 @@ void launch_slave_precompute(mortar_ctx* c, const RunParams& rp) {
                                                           c->box_s.as<double>(), st);
 }
 
+void launch_slave_precompute_raw(const double* xs, const int32_t* conn_s, int64_t Es, int nen_s,
+                                 const RunParams& rp, double* srec, double* De, double* box, DevStatus* st,
+                                 cudaStream_t stream) {
+  if (Es == 0) return;
+  const unsigned g = (unsigned)((Es + kThreads - 1) / kThreads);
+  if (nen_s == 4)
+    k_slave_precompute<4><<<g, kThreads, 0, stream>>>(xs, conn_s, Es, rp, srec, De, box, st);
+  else
+    k_slave_precompute<3><<<g, kThreads, 0, stream>>>(xs, conn_s, Es, rp, srec, De, box, st);
+}
+
 void launch_master_boxes(mortar_ctx* c, const RunParams& rp) {
   if (c->Em == 0) return;
   const unsigned g = (unsigned)((c->Em + kThreads - 1) / kThreads);

@@ -262,6 +262,29 @@ def probe_dfma(blocks: int, threads: int, iters: int, active_lanes: int = 32, st
     return sink
 
 
+def integrate_pairs_static(xs, conn_s, xm, conn_m, pair_s, pair_m, lm: int = LM_STANDARD,
+                           d_domain: int = D_ELEMENT, delta: float = 1e-9, stream=None):
+    """Per-pair M (and segment D) blocks through the no-allocation entry point.
+
+    All arguments are CUDA tensors; returns (M_blocks, D_blocks or None,
+    nonempty) as CUDA tensors.  The output tensors are allocated here, by
+    torch -- a caller that cannot allocate passes its own buffers to the C ABI
+    directly."""
+    torch = _torch()
+    o = default_options()
+    o.lm, o.d_domain, o.search_inflation = lm, d_domain, delta
+    P = int(pair_s.shape[0])
+    Mb = torch.empty((max(P, 1), 4, 4), dtype=torch.float64, device="cuda")
+    Db = torch.empty((max(P, 1), 4, 4), dtype=torch.float64, device="cuda") if d_domain == D_SEGMENT else None
+    ne = torch.empty(max(P, 1), dtype=torch.uint8, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    call("mortar_integrate_pairs_static", ctypes.byref(o), ctypes.c_void_p(st), vp(xs), int(xs.shape[0]),
+         vp(conn_s), int(conn_s.shape[0]), int(conn_s.shape[1]), vp(xm), int(xm.shape[0]), vp(conn_m),
+         int(conn_m.shape[0]), int(conn_m.shape[1]), vp(pair_s), vp(pair_m), P, vp(Mb), vp(Db), vp(ne))
+    return Mb[:P], (Db[:P] if Db is not None else None), ne[:P]
+
+
 def status_string(code: int) -> str:
     return lib().mortar_status_string(code).decode()
 
