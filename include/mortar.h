@@ -200,9 +200,12 @@ int mortar_get_stats(mortar_ctx* ctx, mortar_stats* out);
 /* Enable (1) / disable (0) CUDA-event phase timing (default 0). */
 int mortar_set_timing(mortar_ctx* ctx, int32_t enabled);
 
-/* Set the pair kernels' block size and pairs per work item (0 = defaults);
- * used by the autotuner. */
-int mortar_set_launch(mortar_ctx* ctx, int32_t block_size, int32_t chunk_pairs);
+/* Launch shape of the pair kernels (used by the autotuner; 0 = default):
+ * variant 0 = integration in warp batches of 32 * rounds pairs sorted by
+ * cell count (rounds 1, 2 or 4), variant 1 = one pair per thread;
+ * block_size (multiple of 32) and chunk_pairs (pairs per work-counter fetch)
+ * for the one-pair-per-thread kernels (variant 1 and the adjoint). */
+int mortar_set_launch(mortar_ctx* ctx, int32_t variant, int32_t block_size, int32_t chunk_pairs, int32_t rounds);
 
 /* Per-pair integration without any device allocation.  The paper has no
  * counterpart to this call; it exists for callers that cannot call
@@ -218,7 +221,7 @@ int mortar_set_launch(mortar_ctx* ctx, int32_t block_size, int32_t chunk_pairs);
  * are 0-based (pair_s < n_slave_elems, pair_m < n_master_elems).
  *
  * Scratch lives in one static device array of this library (room for
- * 8192 slave elements, 4.7 MB, held on every device that loads the library
+ * 8192 slave elements, 5.2 MB, held on every device that loads the library
  * until the process exits): n_slave_elems > 8192 returns MORTAR_ERR_CAPACITY
  * and nothing runs.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
@@ -234,6 +237,14 @@ int mortar_integrate_pairs_static(const mortar_options* o, void* stream,
                                   const int32_t* conn_m, int64_t n_master_elems, int32_t type_m,
                                   const int32_t* pair_s, const int32_t* pair_m, int64_t n_pairs,
                                   double* M_blocks, double* D_blocks, uint8_t* nonempty);
+
+/* Autotuner: runs the context's workload once per candidate launch shape
+ * (batched integration with 32, 64 or 128 pairs per warp batch, and one pair
+ * per thread), times the pair kernels (integration, plus the adjoint's
+ * per-pair kernel when lambda != NULL) with CUDA events, and keeps the
+ * fastest shape for later calls.  Writes the choice and its time (ms). */
+int mortar_autotune(mortar_ctx* ctx, const double* lambda, int32_t on_device, int32_t* variant,
+                    int32_t* rounds, float* best_ms);
 
 /* Name of a status code. */
 const char* mortar_status_string(int status);

@@ -25,7 +25,7 @@ EXPORTS = (
     "mortar_evaluate", "mortar_csr_size", "mortar_csr_copy", "mortar_get_pair_blocks",
     "mortar_weighted_gap_grad", "mortar_run_graph", "mortar_get_gradient", "mortar_get_stats",
     "mortar_set_timing", "mortar_set_launch", "mortar_status_string", "mortar_probe_dfma",
-    "mortar_integrate_pairs_static",
+    "mortar_integrate_pairs_static", "mortar_autotune",
 )
 
 
@@ -87,7 +87,9 @@ def lib():
                 "mortar_get_gradient": [P, ctypes.POINTER(f64), P, P, i32],
                 "mortar_get_stats": [P, ctypes.POINTER(Stats)],
                 "mortar_set_timing": [P, i32],
-                "mortar_set_launch": [P, i32, i32],
+                "mortar_set_launch": [P, i32, i32, i32, i32],
+                "mortar_autotune": [P, P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_float)],
                 "mortar_status_string": [ctypes.c_int],
                 "mortar_probe_dfma": [P, i32, i32, i64, i32, P],
                 "mortar_integrate_pairs_static": [ctypes.POINTER(Options), P, P, i64, P, i64, i32,

@@ -609,16 +609,65 @@ int mortar_set_timing(mortar_ctx* c, int32_t enabled) {
   return MORTAR_OK;
 }
 
-int mortar_set_launch(mortar_ctx* c, int32_t block_size, int32_t chunk_pairs) {
-  if (!c || block_size < 0 || block_size > 1024 || (block_size % 32) != 0 || chunk_pairs < 0)
+int mortar_set_launch(mortar_ctx* c, int32_t variant, int32_t block_size, int32_t chunk_pairs, int32_t rounds) {
+  if (!c || variant < 0 || variant > 1 || block_size < 0 || block_size > 1024 || (block_size % 32) != 0 ||
+      chunk_pairs < 0 || (rounds != 0 && rounds != 1 && rounds != 2 && rounds != 4))
     return MORTAR_ERR_INVALID_ARG;
+  c->variant = variant;
   c->block_size = block_size;
   c->chunk_pairs = chunk_pairs;
+  c->rounds = rounds;
   if (c->graph_exec) {
     cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
   }
   return MORTAR_OK;
+}
+
+int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int32_t* variant, int32_t* rounds,
+                    float* best_ms) {
+  if (!c) return MORTAR_ERR_INVALID_ARG;
+  if (!c->have_interface) return MORTAR_ERR_STATE;
+  Phases ph;
+  ph.adjoint = lambda != nullptr;
+  if (lambda) {
+    MORTAR_TRY(buf_reserve(c->lambda, (size_t)std::max<int64_t>(c->Ns, 1) * 24));
+    MORTAR_TRY(copy_in(c->lambda.p, lambda, (size_t)c->Ns * 24, on_device, c->stream));
+  }
+  struct Cand { int32_t variant, rounds; };
+  const Cand cands[] = {{0, 1}, {0, 2}, {0, 4}, {1, 0}};
+  const bool timing = c->timing;
+  c->timing = true;
+  float best = 1e30f;
+  Cand pick = {0, 2};
+  int r = MORTAR_OK;
+  for (const Cand& k : cands) {
+    c->variant = k.variant;
+    c->rounds = k.rounds;
+    float t_best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {   // first run sizes buffers and warms up
+      r = run(c, ph);
+      if (r != MORTAR_OK && r != MORTAR_ERR_NEWTON && r != MORTAR_ERR_DEGENERATE) break;
+      const float t = c->stats.ms_integrate + (ph.adjoint ? c->stats.ms_adjoint_pairs : 0.0f);
+      if (rep > 0) t_best = std::min(t_best, t);
+    }
+    if (r != MORTAR_OK && r != MORTAR_ERR_NEWTON && r != MORTAR_ERR_DEGENERATE) break;
+    if (t_best < best) {
+      best = t_best;
+      pick = k;
+    }
+  }
+  c->timing = timing;
+  c->variant = pick.variant;
+  c->rounds = pick.rounds;
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  if (variant) *variant = pick.variant;
+  if (rounds) *rounds = pick.rounds;
+  if (best_ms) *best_ms = best;
+  return (r == MORTAR_ERR_NEWTON || r == MORTAR_ERR_DEGENERATE) ? MORTAR_OK : r;
 }
 
 const char* mortar_status_string(int s) {

@@ -1,0 +1,191 @@
+// Per-pair geometry shared by the integration and adjoint kernels, so that
+// both take identical decisions: projection and clipping of one slave/master
+// pair (Sec. 2.3, Algorithm 1: project the master element onto the slave
+// element's auxiliary plane, find the intersection by clipping) and the
+// inverse of an element map in that plane (chi_h).
+#pragma once
+
+#include "common.cuh"
+
+namespace mortar {
+
+constexpr int kPolyS = 10;   // stored clip-polygon vertices (convex quad vs quad: <= 8)
+
+// Projection of the master element, its map, and the clipped, merged polygon
+// (Pu, Pv, nr vertices; nr = 0 when the pair contributes nothing).
+template <int NS, int NM, int CAP>
+__device__ __forceinline__ int clip_polygon(const double* __restrict__ r, const double* __restrict__ xm,
+                                            const int32_t* __restrict__ conn_m, int32_t m, PlaneMap& mmap,
+                                            double* Pu, double* Pv,
+                                            unsigned long long& clip_over) {
+  const double eps_in = r[SR_EPSIN];
+  if (!(eps_in >= 0.0)) return 0;
+  const double x0x = r[SR_X0], x0y = r[SR_X0 + 1], x0z = r[SR_X0 + 2];
+  const double t1x = r[SR_T1], t1y = r[SR_T1 + 1], t1z = r[SR_T1 + 2];
+  const double t2x = r[SR_T2], t2y = r[SR_T2 + 1], t2z = r[SR_T2 + 2];
+  double mu[4], mv[4];
+#pragma unroll
+  for (int l = 0; l < NM; ++l) {
+    const int64_t n = conn_m[(int64_t)NM * m + l];
+    const double dx = xm[3 * n] - x0x, dy = xm[3 * n + 1] - x0y, dz = xm[3 * n + 2] - x0z;
+    mu[l] = dx * t1x + dy * t1y + dz * t1z;
+    mv[l] = dx * t2x + dy * t2y + dz * t2z;
+  }
+  mmap = plane_map<NM>(mu, mv);
+  double ma2 = 0.0;
+#pragma unroll
+  for (int l = 0; l < NM; ++l) ma2 += cross2(mu[l], mv[l], mu[(l + 1) % NM], mv[(l + 1) % NM]);
+  double Qu[kMaxPoly], Qv[kMaxPoly], d[kMaxPoly];
+  double Wu[kMaxPoly], Wv[kMaxPoly];   // working polygon
+#pragma unroll
+  for (int l = 0; l < NM; ++l) {
+    const int src = ma2 < 0.0 ? NM - 1 - l : l;
+    Wu[l] = mu[src];
+    Wv[l] = mv[src];
+  }
+  int n = NM;
+  for (int i = 0; i < NS && n > 0; ++i) {
+    const int i1 = i + 1 == NS ? 0 : i + 1;
+    const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
+    const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
+    for (int k = 0; k < n; ++k) d[k] = cross2(eu, ev, Wu[k] - au, Wv[k] - av);
+    int o = 0;
+    for (int k = 0; k < n; ++k) {
+      const int k1 = k + 1 == n ? 0 : k + 1;
+      const double dp = d[k], dq = d[k1];
+      if ((dp > eps_in && dq < -eps_in) || (dp < -eps_in && dq > eps_in)) {
+        const double t = dp / (dp - dq);
+        if (o < kMaxPoly) {
+          Qu[o] = Wu[k] + t * (Wu[k1] - Wu[k]);
+          Qv[o] = Wv[k] + t * (Wv[k1] - Wv[k]);
+        }
+        ++o;
+      }
+      if (dq >= -eps_in) {
+        if (o < kMaxPoly) { Qu[o] = Wu[k1]; Qv[o] = Wv[k1]; }
+        ++o;
+      }
+    }
+    if (o > kMaxPoly) { clip_over++; o = kMaxPoly; }
+    for (int k = 0; k < o; ++k) { Wu[k] = Qu[k]; Wv[k] = Qv[k]; }
+    n = o;
+  }
+  // merge consecutive (cyclic) vertices closer than eps_merge
+  const double em2 = r[SR_EPSM2];
+  int nr = 0;
+  for (int k = 0; k < n; ++k) {
+    if (nr > 0) {
+      const double du = Wu[k] - Wu[nr - 1], dv = Wv[k] - Wv[nr - 1];
+      if (du * du + dv * dv < em2) continue;
+    }
+    Wu[nr] = Wu[k];
+    Wv[nr] = Wv[k];
+    ++nr;
+  }
+  while (nr > 1) {
+    const double du = Wu[nr - 1] - Wu[0], dv = Wv[nr - 1] - Wv[0];
+    if (du * du + dv * dv < em2) --nr; else break;
+  }
+  double pa2 = 0.0;
+  for (int k = 0; k < nr; ++k) {
+    const int k1 = k + 1 == nr ? 0 : k + 1;
+    pa2 += cross2(Wu[k], Wv[k], Wu[k1], Wv[k1]);
+  }
+  if (nr < 3 || 0.5 * fabs(pa2) < r[SR_EPSA]) return 0;
+  if (nr > CAP) {   // cannot happen for convex elements; reported, pair dropped
+    clip_over++;
+    return 0;
+  }
+  for (int k = 0; k < nr; ++k) { Pu[k] = Wu[k]; Pv[k] = Wv[k]; }
+  return nr;
+}
+
+// Inverse of an element map in the plane for many query points: affine maps
+// by a 2x2 inverse, bilinear ones by FP32 Newton on coordinates scaled by a
+// power of two, then two FP64 polishing steps x -= J^-1 r(x) with the FP64
+// residual r and J taken at the FP32 solution (FP32-accurate inverse).  Each
+// polishing step shrinks the error by ~1e-7, so FP32 accuracy (~1e-7) becomes
+// rounding level after the second.
+struct MapInverse {
+  PlaneMap m;
+  bool affine;
+  double i00, i01, i10, i11;        // affine: exact inverse of [c1 c2]
+  double sc, sc2;                   // power-of-two scale and its square
+  float f1u, f1v, f2u, f2v, f3u, f3v;
+  float b00, b01, b10, b11;         // FP32 inverse of the scaled [c1 c2]
+
+  __device__ __forceinline__ void setup(const PlaneMap& mp, bool is_affine) {
+    m = mp;
+    affine = is_affine;
+    if (affine) {
+      const double id = 1.0 / (m.c1u * m.c2v - m.c2u * m.c1v);
+      i00 = m.c2v * id; i01 = -m.c2u * id; i10 = -m.c1v * id; i11 = m.c1u * id;
+      return;
+    }
+    const double L = fmax(fmax(fabs(m.c1u), fabs(m.c1v)), fmax(fabs(m.c2u), fabs(m.c2v)));
+    int e = 0;
+    frexp(L, &e);
+    sc = ldexp(1.0, -e);   // exact power of two, L * sc in [0.5, 1)
+    sc2 = sc * sc;
+    f1u = (float)(m.c1u * sc); f1v = (float)(m.c1v * sc);
+    f2u = (float)(m.c2u * sc); f2v = (float)(m.c2v * sc);
+    f3u = (float)(m.c3u * sc); f3v = (float)(m.c3v * sc);
+    const float fd = 1.0f / (f1u * f2v - f2u * f1v);
+    b00 = f2v * fd; b01 = -f2u * fd; b10 = -f1v * fd; b11 = f1u * fd;
+  }
+
+  // FP64 inverse of the Jacobian at (xi, eta) (reverse sweeps need it exact)
+  __device__ __forceinline__ void jinv(double xi, double eta, double& a00, double& a01, double& a10,
+                                       double& a11) const {
+    if (affine) {
+      a00 = i00; a01 = i01; a10 = i10; a11 = i11;
+      return;
+    }
+    const double j00 = m.c1u + m.c3u * eta, j01 = m.c2u + m.c3u * xi;
+    const double j10 = m.c1v + m.c3v * eta, j11 = m.c2v + m.c3v * xi;
+    const double id = 1.0 / (j00 * j11 - j01 * j10);
+    a00 = j11 * id; a01 = -j01 * id; a10 = -j10 * id; a11 = j00 * id;
+  }
+
+  // returns false if the FP32 iteration did not settle (xi then is the best found)
+  __device__ __forceinline__ bool solve(double xu, double xv, double& xi, double& eta) const {
+    const double du = xu - m.c0u, dv = xv - m.c0v;
+    if (affine) {
+      xi = i00 * du + i01 * dv;
+      eta = i10 * du + i11 * dv;
+      return true;
+    }
+    const float tu = (float)(du * sc), tv = (float)(dv * sc);
+    float x = b00 * tu + b01 * tv, y = b10 * tu + b11 * tv;
+    bool conv = false;
+#pragma unroll 1
+    for (int it = 0; it < 16; ++it) {
+      const float ru = fmaf(f3u * x, y, fmaf(f1u, x, fmaf(f2u, y, -tu)));
+      const float rv = fmaf(f3v * x, y, fmaf(f1v, x, fmaf(f2v, y, -tv)));
+      const float j00 = fmaf(f3u, y, f1u), j01 = fmaf(f3u, x, f2u);
+      const float j10 = fmaf(f3v, y, f1v), j11 = fmaf(f3v, x, f2v);
+      const float id = __frcp_rn(j00 * j11 - j01 * j10);
+      const float d0 = (j11 * ru - j01 * rv) * id, d1 = (j00 * rv - j10 * ru) * id;
+      x -= d0;
+      y -= d1;
+      if (fabsf(d0) + fabsf(d1) <= 3e-7f) { conv = true; break; }
+    }
+    xi = (double)x;
+    eta = (double)y;
+    const double j00 = m.c1u + m.c3u * eta, j01 = m.c2u + m.c3u * xi;
+    const double j10 = m.c1v + m.c3v * eta, j11 = m.c2v + m.c3v * xi;
+    const double det = (j00 * j11 - j01 * j10) * sc2;
+    const double id = (double)__frcp_rn((float)det) * sc2;
+    const double k00 = j11 * id, k01 = -j01 * id, k10 = -j10 * id, k11 = j00 * id;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double ru = fma(fma(m.c3u, eta, m.c1u), xi, fma(m.c2u, eta, -du));
+      const double rv = fma(fma(m.c3v, eta, m.c1v), xi, fma(m.c2v, eta, -dv));
+      xi -= fma(k00, ru, k01 * rv);
+      eta -= fma(k10, ru, k11 * rv);
+    }
+    return conv;
+  }
+};
+
+}  // namespace mortar

@@ -43,7 +43,9 @@ enum SlaveRec : int {
   SR_EPSA = 30,   // area threshold
   SR_REV = 31,    // 1 if the window order is the reverse of the node order
   SR_A = 32,      // LM coefficients A[a][b] (16)
-  SR_STRIDE = 48
+  SR_BINV = 48,   // inverse of [c1 c2] (row-major 2x2): xi = Binv (x - c0) for affine maps
+  SR_AFF = 52,    // 1 if the projected slave map is affine (c3 negligible)
+  SR_STRIDE = 56
 };
 
 // Device-side counters and sizes of one run (read back once per run).
@@ -166,6 +168,13 @@ __device__ __forceinline__ bool invert_plane_map(const PlaneMap& m, double xu, d
     }
     return false;
   }
+}
+
+// A projected quad4 map is treated as affine when its bilinear coefficient is
+// below 1e-15 of the linear ones (rounding level for parallelograms): the
+// affine solve then differs from the bilinear one by less than 1e-15 in xi.
+__device__ __forceinline__ bool map_is_affine(const PlaneMap& m) {
+  return fabs(m.c3u) + fabs(m.c3v) <= 1e-15 * (fabs(m.c1u) + fabs(m.c1v) + fabs(m.c2u) + fabs(m.c2v));
 }
 
 template <int NEN>

@@ -38,8 +38,10 @@ struct mortar_ctx {
   int device = 0;
   int n_sm = 0;
   bool timing = false;
+  int32_t variant = 0;        // integration kernel: 0 batched + sorted (default), 1 one pair per thread
   int32_t block_size = 0;     // pair kernels (0 = default)
-  int32_t chunk_pairs = 0;    // pairs per work item (0 = default)
+  int32_t chunk_pairs = 0;    // pairs per work item of the one-pair-per-thread kernels (0 = default)
+  int32_t rounds = 0;         // batched kernel: 32 * rounds pairs per warp batch (0 = default)
 
   // ---- interface definition
   bool have_interface = false;

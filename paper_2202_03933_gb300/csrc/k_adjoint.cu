@@ -25,6 +25,7 @@
 // reproducible.
 #include <algorithm>
 
+#include "clip.cuh"
 #include "context.h"
 
 namespace mortar {
@@ -489,6 +490,515 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_pairs(
   block_count_add(&st->newton_fail, ctr.newton_fail);
 }
 
+// ---------------------------------------------------------------- variant 0
+// Same functional, reorganised for the FP64 pipe:
+//  * the per-point reverse sweep only carries what depends on xi: with
+//    PX[c][b] = Lambda_c . X_b and PY[c][l] = Lambda_c . Y_l (per pair),
+//      t_c      = Lambda_c . q        = [seg] sum_b N_b PX[c][b] - sum_l Nm_l PY[c][l]
+//      f        = Lh . q              = sum_c N_c t_c
+//      dJ/dN_c  = W (t_c + [seg] sum_d N_d PX[d][c]),  dJ/dNm_l = -W sum_d N_d PY[d][l];
+//  * the terms that hold the shape functions fixed come from the forward
+//    accumulators G = sum W N Nm^T and H = sum W N N^T at the end:
+//      dJ/dY_l |direct = -sum_c G[c][l] Lambda_c,  dJ/dX_b |direct = sum_c H[c][b] Lambda_c,
+//      dJ/dLambda_c = sum_b H[c][b] X_b - sum_l G[c][l] Y_l,  J = sum_c Lambda_c . dJ/dLambda_c;
+//  * element maps are inverted as in the batched integration kernel (affine
+//    2x2 inverse, or FP32 Newton + two FP64 polishing steps), and the
+//    implicit-function step uses the exact FP64 inverse Jacobian;
+//  * a warp sorts its batch of pairs by cell count before the sweep.
+template <int NS, int NM, bool SEG, bool DUAL>
+__device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, const int32_t* __restrict__ pm,
+                                  const double* __restrict__ srec, const double* __restrict__ xs,
+                                  const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
+                                  const int32_t* __restrict__ conn_m, const double* __restrict__ lambda,
+                                  double* __restrict__ gs_out, double* __restrict__ gm_out,
+                                  double* __restrict__ ab_out, double* __restrict__ J_out, AdjCounters& ctr) {
+  const int32_t s = ps[p], m = pm[p];
+  const double* r = srec + (int64_t)SR_STRIDE * s;
+  double gX[4][3], gY[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) { gX[a][k] = 0.0; gY[a][k] = 0.0; }
+  V3 X[4], Y[4], lam[4], Lam[4], Lb[4];
+  for (int a = 0; a < 4; ++a) Lb[a] = v3(0, 0, 0);
+  double Jp = 0.0;
+  const double eps_in = r[SR_EPSIN];
+  for (int a = 0; a < NS; ++a) {
+    const int64_t n = conn_s[(int64_t)NS * s + a];
+    X[a] = v3(xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]);
+    lam[a] = v3(lambda[3 * n], lambda[3 * n + 1], lambda[3 * n + 2]);
+  }
+  for (int l = 0; l < NM; ++l) {
+    const int64_t n = conn_m[(int64_t)NM * m + l];
+    Y[l] = v3(xm[3 * n], xm[3 * n + 1], xm[3 * n + 2]);
+  }
+  const V3 x0 = v3(r[SR_X0], r[SR_X0 + 1], r[SR_X0 + 2]);
+  const V3 t1 = v3(r[SR_T1], r[SR_T1 + 1], r[SR_T1 + 2]);
+  const V3 t2 = v3(r[SR_T2], r[SR_T2 + 1], r[SR_T2 + 2]);
+  double mu[4], mv[4];
+  for (int l = 0; l < NM; ++l) {
+    const double dx = Y[l].x - x0.x, dy = Y[l].y - x0.y, dz = Y[l].z - x0.z;
+    mu[l] = dx * t1.x + dy * t1.y + dz * t1.z;
+    mv[l] = dx * t2.x + dy * t2.y + dz * t2.z;
+  }
+  const PlaneMap mmap = plane_map<NM>(mu, mv);
+  PlaneMap smap;
+  smap.c0u = r[SR_C + 0]; smap.c0v = r[SR_C + 1]; smap.c1u = r[SR_C + 2]; smap.c1v = r[SR_C + 3];
+  smap.c2u = r[SR_C + 4]; smap.c2v = r[SR_C + 5]; smap.c3u = r[SR_C + 6]; smap.c3v = r[SR_C + 7];
+  double ma2 = 0.0;
+  for (int l = 0; l < NM; ++l) ma2 += cross2(mu[l], mv[l], mu[(l + 1) % NM], mv[(l + 1) % NM]);
+  const bool mrev = ma2 < 0.0;
+  const bool srev = r[SR_REV] != 0.0;
+  // ---- forward clip with recorded stages (same decisions as clip_polygon)
+  double Vu[NS + 1][kPolyA], Vv[NS + 1][kPolyA], tt[NS][kPolyA];
+  int8_t src[NS][kPolyA];
+  int nv[NS + 1];
+  for (int k = 0; k < NM; ++k) {
+    const int l = mrev ? NM - 1 - k : k;
+    Vu[0][k] = mu[l];
+    Vv[0][k] = mv[l];
+  }
+  nv[0] = NM;
+  int last = 0;
+  for (int i = 0; i < NS; ++i) {
+    const int n = nv[i];
+    if (n == 0) break;
+    const int i1 = i + 1 == NS ? 0 : i + 1;
+    const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
+    const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
+    double d[kPolyA];
+    for (int k = 0; k < n; ++k) d[k] = cross2(eu, ev, Vu[i][k] - au, Vv[i][k] - av);
+    int o = 0;
+    for (int k = 0; k < n; ++k) {
+      const int k1 = k + 1 == n ? 0 : k + 1;
+      const double dp = d[k], dq = d[k1];
+      if ((dp > eps_in && dq < -eps_in) || (dp < -eps_in && dq > eps_in)) {
+        const double t = dp / (dp - dq);
+        if (o < kPolyA) {
+          Vu[i + 1][o] = Vu[i][k] + t * (Vu[i][k1] - Vu[i][k]);
+          Vv[i + 1][o] = Vv[i][k] + t * (Vv[i][k1] - Vv[i][k]);
+          tt[i][o] = t;
+          src[i][o] = (int8_t)(k + 64);
+        }
+        ++o;
+      }
+      if (dq >= -eps_in) {
+        if (o < kPolyA) {
+          Vu[i + 1][o] = Vu[i][k1];
+          Vv[i + 1][o] = Vv[i][k1];
+          src[i][o] = (int8_t)k;
+        }
+        ++o;
+      }
+    }
+    if (o > kPolyA) { ctr.clip_over++; o = kPolyA; }
+    nv[i + 1] = o;
+    last = i + 1;
+  }
+  const double em2 = r[SR_EPSM2];
+  int sel[kPolyA];
+  int nr = 0;
+  const int nl = nv[last];
+  const bool clipped = last == NS;
+  for (int k = 0; clipped && k < nl; ++k) {
+    if (nr > 0) {
+      const double du = Vu[last][k] - Vu[last][sel[nr - 1]], dv = Vv[last][k] - Vv[last][sel[nr - 1]];
+      if (du * du + dv * dv < em2) continue;
+    }
+    sel[nr++] = k;
+  }
+  while (nr > 1) {
+    const double du = Vu[last][sel[nr - 1]] - Vu[last][sel[0]], dv = Vv[last][sel[nr - 1]] - Vv[last][sel[0]];
+    if (du * du + dv * dv < em2) --nr; else break;
+  }
+  double pa2 = 0.0;
+  for (int k = 0; k < nr; ++k) {
+    const int k1 = k + 1 == nr ? 0 : k + 1;
+    pa2 += cross2(Vu[last][sel[k]], Vv[last][sel[k]], Vu[last][sel[k1]], Vv[last][sel[k1]]);
+  }
+  const bool nonempty = eps_in >= 0.0 && clipped && nr >= 3 && !(0.5 * fabs(pa2) < r[SR_EPSA]);
+  if (nonempty) {
+    for (int c = 0; c < NS; ++c) {
+      if (DUAL) {
+        V3 acc = v3(0, 0, 0);
+        for (int a = 0; a < NS; ++a) acc = acc + r[SR_A + 4 * a + c] * lam[a];
+        Lam[c] = acc;
+      } else {
+        Lam[c] = lam[c];
+      }
+    }
+    double PX[4][4], PY[4][4];
+    for (int c = 0; c < 4; ++c)
+      for (int b = 0; b < 4; ++b) {
+        PX[c][b] = (SEG && c < NS && b < NS) ? dot(Lam[c], X[b]) : 0.0;
+        PY[c][b] = (c < NS && b < NM) ? dot(Lam[c], Y[b]) : 0.0;
+      }
+    MapInverse mi;
+    mi.setup(mmap, NM == 3 || map_is_affine(mmap));
+    MapInverse si;
+    if (r[SR_AFF] != 0.0) {
+      si.m = smap;
+      si.affine = true;
+      si.i00 = r[SR_BINV]; si.i01 = r[SR_BINV + 1]; si.i10 = r[SR_BINV + 2]; si.i11 = r[SR_BINV + 3];
+    } else {
+      si.setup(smap, false);
+    }
+    double Ru[kPolyA], Rv[kPolyA], Rbu[kPolyA], Rbv[kPolyA];
+    for (int k = 0; k < nr; ++k) {
+      Ru[k] = Vu[last][sel[k]];
+      Rv[k] = Vv[last][sel[k]];
+      Rbu[k] = 0.0;
+      Rbv[k] = 0.0;
+    }
+    double cu = 0.0, cv = 0.0, cbu = 0.0, cbv = 0.0;
+    int ncell = 1;
+    if (nr > 3) {
+      double su = 0.0, sv = 0.0;
+      for (int k = 0; k < nr; ++k) { su += Ru[k]; sv += Rv[k]; }
+      cu = su / (double)nr;
+      cv = sv / (double)nr;
+      ncell = nr;
+    }
+    double G[4][4], H[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) { G[a][b] = 0.0; H[a][b] = 0.0; }
+    double smb[8] = {0, 0, 0, 0, 0, 0, 0, 0}, mmb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int cI = 0; cI < ncell; ++cI) {
+      int ib, iw;
+      double au, av;
+      if (nr == 3) {
+        au = Ru[0]; av = Rv[0]; ib = 1; iw = 2;
+      } else {
+        au = cu; av = cv; ib = cI; iw = cI + 1 == nr ? 0 : cI + 1;
+      }
+      const double e1u = Ru[ib] - au, e1v = Rv[ib] - av, e2u = Ru[iw] - au, e2v = Rv[iw] - av;
+      const double cr = cross2(e1u, e1v, e2u, e2v);
+      const double area = 0.5 * fabs(cr);
+      double area_b = 0.0, e1bu = 0.0, e1bv = 0.0, e2bu = 0.0, e2bv = 0.0, abu = 0.0, abv = 0.0;
+#pragma unroll 1
+      for (int q = 0; q < 7; ++q) {
+        double l1, l2, w;
+        tri7_point(q, l1, l2, w);
+        const double xu = au + l1 * e1u + l2 * e2u;
+        const double xv = av + l1 * e1v + l2 * e2v;
+        const double W = w * area;
+        double xs1, xs2, xm1, xm2;
+        if (!si.solve(xu, xv, xs1, xs2)) ctr.newton_fail++;
+        if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
+        double Ns[4], Nm[4];
+        shape_fn<NS>(xs1, xs2, Ns);
+        shape_fn<NM>(xm1, xm2, Nm);
+        double t[4], f = 0.0;
+#pragma unroll
+        for (int c = 0; c < NS; ++c) {
+          double v = 0.0;
+          if (SEG)
+#pragma unroll
+            for (int b = 0; b < NS; ++b) v = fma(Ns[b], PX[c][b], v);
+#pragma unroll
+          for (int l = 0; l < NM; ++l) v = fma(-Nm[l], PY[c][l], v);
+          t[c] = v;
+          f = fma(Ns[c], v, f);
+        }
+        area_b = fma(w, f, area_b);
+        double Nsb[4], Nmb[4];
+#pragma unroll
+        for (int c = 0; c < NS; ++c) {
+          double v = t[c];
+          if (SEG)
+#pragma unroll
+            for (int d = 0; d < NS; ++d) v = fma(Ns[d], PX[d][c], v);
+          Nsb[c] = W * v;
+        }
+#pragma unroll
+        for (int l = 0; l < NM; ++l) {
+          double v = 0.0;
+#pragma unroll
+          for (int d = 0; d < NS; ++d) v = fma(Ns[d], PY[d][l], v);
+          Nmb[l] = -W * v;
+        }
+        // forward accumulators for the direct terms
+#pragma unroll
+        for (int c = 0; c < NS; ++c) {
+          const double wn = W * Ns[c];
+#pragma unroll
+          for (int l = 0; l < NM; ++l) G[c][l] = fma(wn, Nm[l], G[c][l]);
+          if (SEG)
+#pragma unroll
+            for (int b = 0; b < NS; ++b) H[c][b] = fma(wn, Ns[b], H[c][b]);
+        }
+        double dNs[4][2], dNm[4][2];
+        shape_grad<NS>(xs1, xs2, dNs);
+        shape_grad<NM>(xm1, xm2, dNm);
+        double xsb0 = 0.0, xsb1 = 0.0, xmb0 = 0.0, xmb1 = 0.0;
+#pragma unroll
+        for (int c = 0; c < NS; ++c) { xsb0 = fma(Nsb[c], dNs[c][0], xsb0); xsb1 = fma(Nsb[c], dNs[c][1], xsb1); }
+#pragma unroll
+        for (int l = 0; l < NM; ++l) { xmb0 = fma(Nmb[l], dNm[l][0], xmb0); xmb1 = fma(Nmb[l], dNm[l][1], xmb1); }
+        double a00, a01, a10, a11;
+        si.jinv(xs1, xs2, a00, a01, a10, a11);
+        const double msu = a00 * xsb0 + a10 * xsb1, msv = a01 * xsb0 + a11 * xsb1;   // J^-T xib
+        mi.jinv(xm1, xm2, a00, a01, a10, a11);
+        const double mmu = a00 * xmb0 + a10 * xmb1, mmv = a01 * xmb0 + a11 * xmb1;
+        const double xs12 = xs1 * xs2, xm12 = xm1 * xm2;
+        smb[0] -= msu; smb[1] -= msv;
+        smb[2] = fma(-xs1, msu, smb[2]); smb[3] = fma(-xs1, msv, smb[3]);
+        smb[4] = fma(-xs2, msu, smb[4]); smb[5] = fma(-xs2, msv, smb[5]);
+        smb[6] = fma(-xs12, msu, smb[6]); smb[7] = fma(-xs12, msv, smb[7]);
+        mmb[0] -= mmu; mmb[1] -= mmv;
+        mmb[2] = fma(-xm1, mmu, mmb[2]); mmb[3] = fma(-xm1, mmv, mmb[3]);
+        mmb[4] = fma(-xm2, mmu, mmb[4]); mmb[5] = fma(-xm2, mmv, mmb[5]);
+        mmb[6] = fma(-xm12, mmu, mmb[6]); mmb[7] = fma(-xm12, mmv, mmb[7]);
+        const double xbu = msu + mmu, xbv = msv + mmv;
+        abu += xbu; abv += xbv;
+        e1bu = fma(l1, xbu, e1bu); e1bv = fma(l1, xbv, e1bv);
+        e2bu = fma(l2, xbu, e2bu); e2bv = fma(l2, xbv, e2bv);
+      }
+      const double crb = 0.5 * (cr < 0.0 ? -area_b : area_b);
+      e1bu += crb * e2v; e1bv -= crb * e2u;
+      e2bu -= crb * e1v; e2bv += crb * e1u;
+      Rbu[ib] += e1bu; Rbv[ib] += e1bv;
+      Rbu[iw] += e2bu; Rbv[iw] += e2bv;
+      abu -= e1bu + e2bu;
+      abv -= e1bv + e2bv;
+      if (nr == 3) { Rbu[0] += abu; Rbv[0] += abv; } else { cbu += abu; cbv += abv; }
+    }
+    if (nr > 3) {
+      const double inv = 1.0 / (double)nr;
+      for (int k = 0; k < nr; ++k) { Rbu[k] += cbu * inv; Rbv[k] += cbv * inv; }
+    }
+    // ---- direct terms and J from the forward accumulators
+    for (int c = 0; c < NS; ++c) {
+      V3 acc = v3(0, 0, 0);
+      if (SEG)
+        for (int b = 0; b < NS; ++b) acc = acc + H[c][b] * X[b];
+      for (int l = 0; l < NM; ++l) acc = acc - G[c][l] * Y[l];
+      Lb[c] = acc;
+      Jp += dot(Lam[c], acc);
+    }
+    for (int l = 0; l < NM; ++l) {
+      V3 acc = v3(0, 0, 0);
+      for (int c = 0; c < NS; ++c) acc = acc + G[c][l] * Lam[c];
+      gY[l][0] -= acc.x; gY[l][1] -= acc.y; gY[l][2] -= acc.z;
+    }
+    if (SEG)
+      for (int b = 0; b < NS; ++b) {
+        V3 acc = v3(0, 0, 0);
+        for (int c = 0; c < NS; ++c) acc = acc + H[c][b] * Lam[c];
+        gX[b][0] += acc.x; gX[b][1] += acc.y; gX[b][2] += acc.z;
+      }
+    // ---- reverse merge and clipping stages
+    double Bu[NS + 1][kPolyA], Bv[NS + 1][kPolyA];
+    for (int k = 0; k < nl; ++k) { Bu[last][k] = 0.0; Bv[last][k] = 0.0; }
+    for (int k = 0; k < nr; ++k) { Bu[last][sel[k]] += Rbu[k]; Bv[last][sel[k]] += Rbv[k]; }
+    double Wbu[4] = {0, 0, 0, 0}, Wbv[4] = {0, 0, 0, 0};
+    for (int i = NS - 1; i >= 0; --i) {
+      const int n = nv[i];
+      const int i1 = i + 1 == NS ? 0 : i + 1;
+      const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
+      const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
+      for (int k = 0; k < n; ++k) { Bu[i][k] = 0.0; Bv[i][k] = 0.0; }
+      double abu2 = 0.0, abv2 = 0.0, ebu = 0.0, ebv = 0.0;
+      for (int o = 0; o < nv[i + 1]; ++o) {
+        const double gbu = Bu[i + 1][o], gbv = Bv[i + 1][o];
+        const int code = src[i][o];
+        const int k = code & 63;
+        const int k1 = k + 1 == n ? 0 : k + 1;
+        if (code < 64) {
+          Bu[i][k1] += gbu;
+          Bv[i][k1] += gbv;
+          continue;
+        }
+        const double tk = tt[i][o];
+        const double pu = Vu[i][k], pv = Vv[i][k], qu = Vu[i][k1], qv = Vv[i][k1];
+        Bu[i][k] += (1.0 - tk) * gbu; Bv[i][k] += (1.0 - tk) * gbv;
+        Bu[i][k1] += tk * gbu;        Bv[i][k1] += tk * gbv;
+        const double tb = gbu * (qu - pu) + gbv * (qv - pv);
+        const double dp = cross2(eu, ev, pu - au, pv - av);
+        const double dq = cross2(eu, ev, qu - au, qv - av);
+        const double den = dp - dq;
+        const double i2 = 1.0 / (den * den);
+        const double dpb = -tb * dq * i2, dqb = tb * dp * i2;
+        Bu[i][k] += -ev * dpb;  Bv[i][k] += eu * dpb;
+        Bu[i][k1] += -ev * dqb; Bv[i][k1] += eu * dqb;
+        abu2 += ev * (dpb + dqb);
+        abv2 += -eu * (dpb + dqb);
+        ebu += (pv - av) * dpb + (qv - av) * dqb;
+        ebv += -(pu - au) * dpb - (qu - au) * dqb;
+      }
+      Wbu[i] += abu2 - ebu; Wbv[i] += abv2 - ebv;
+      Wbu[i1] += ebu;       Wbv[i1] += ebv;
+    }
+    double sbu[4] = {0, 0, 0, 0}, sbv[4] = {0, 0, 0, 0}, mbu[4] = {0, 0, 0, 0}, mbv[4] = {0, 0, 0, 0};
+    for (int k = 0; k < NS; ++k) {
+      const int a = srev ? NS - 1 - k : k;
+      sbu[a] += Wbu[k];
+      sbv[a] += Wbv[k];
+    }
+    for (int k = 0; k < NM; ++k) {
+      const int l = mrev ? NM - 1 - k : k;
+      mbu[l] += Bu[0][k];
+      mbv[l] += Bv[0][k];
+    }
+    map_coeff_reverse<NS>(smb, sbu, sbv);
+    map_coeff_reverse<NM>(mmb, mbu, mbv);
+    // ---- projection and auxiliary plane
+    V3 x0b = v3(0, 0, 0), t1b = v3(0, 0, 0), t2b = v3(0, 0, 0);
+    for (int a = 0; a < NS; ++a) {
+      const V3 dd = X[a] - x0;
+      const V3 db = sbu[a] * t1 + sbv[a] * t2;
+      gX[a][0] += db.x; gX[a][1] += db.y; gX[a][2] += db.z;
+      x0b = x0b - db;
+      t1b = t1b + sbu[a] * dd;
+      t2b = t2b + sbv[a] * dd;
+    }
+    for (int l = 0; l < NM; ++l) {
+      const V3 dd = Y[l] - x0;
+      const V3 db = mbu[l] * t1 + mbv[l] * t2;
+      gY[l][0] += db.x; gY[l][1] += db.y; gY[l][2] += db.z;
+      x0b = x0b - db;
+      t1b = t1b + mbu[l] * dd;
+      t2b = t2b + mbv[l] * dd;
+    }
+    const V3 n0 = v3(r[SR_N0], r[SR_N0 + 1], r[SR_N0 + 2]);
+    V3 g1, g2;
+    if constexpr (NS == 4) {
+      g1 = 0.25 * ((X[1] - X[0]) + (X[2] - X[3]));
+      g2 = 0.25 * ((X[2] - X[1]) + (X[3] - X[0]));
+    } else {
+      g1 = X[1] - X[0];
+      g2 = X[2] - X[0];
+    }
+    const V3 nn = cross(g1, g2);
+    const double ln = sqrt(dot(nn, nn));
+    const V3 ed = X[1] - X[0];
+    const double en = dot(ed, n0);
+    const V3 ep = ed - en * n0;
+    const double le = sqrt(dot(ep, ep));
+    V3 n0b = cross(t1, t2b);
+    t1b = t1b + cross(t2b, n0);
+    const V3 epb = (1.0 / le) * (t1b - dot(t1, t1b) * t1);
+    V3 edb = epb;
+    const double enb = -dot(epb, n0);
+    n0b = n0b - en * epb;
+    edb = edb + enb * n0;
+    n0b = n0b + enb * ed;
+    const V3 nb = (1.0 / ln) * (n0b - dot(n0, n0b) * n0);
+    const V3 g1b = cross(g2, nb), g2b = cross(nb, g1);
+    V3 Xb[4];
+    for (int a = 0; a < 4; ++a) Xb[a] = v3(0, 0, 0);
+    Xb[1] = Xb[1] + edb;
+    Xb[0] = Xb[0] - edb;
+    if constexpr (NS == 4) {
+      const V3 a1 = 0.25 * g1b, a2 = 0.25 * g2b, ax = 0.25 * x0b;
+      Xb[0] = Xb[0] - a1 - a2 + ax;
+      Xb[1] = Xb[1] + a1 - a2 + ax;
+      Xb[2] = Xb[2] + a1 + a2 + ax;
+      Xb[3] = Xb[3] - a1 + a2 + ax;
+    } else {
+      const V3 ax = (1.0 / 3.0) * x0b;
+      Xb[0] = Xb[0] - g1b - g2b + ax;
+      Xb[1] = Xb[1] + g1b + ax;
+      Xb[2] = Xb[2] + g2b + ax;
+    }
+    for (int a = 0; a < NS; ++a) {
+      gX[a][0] += Xb[a].x; gX[a][1] += Xb[a].y; gX[a][2] += Xb[a].z;
+    }
+  }
+  double* go = gs_out + 12 * p;
+  double* gmo = gm_out + 12 * p;
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) {
+      go[3 * a + k] = gX[a][k];
+      gmo[3 * a + k] = gY[a][k];
+    }
+  if (DUAL) {
+    double* ab = ab_out + 16 * p;
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c)
+        ab[4 * a + c] = (nonempty && a < NS && c < NS) ? dot(lam[a], Lb[c]) : 0.0;
+  }
+  J_out[p] = Jp;
+}
+
+constexpr int kAdjWarps = 4;
+
+template <int NS, int NM, bool SEG, bool DUAL, int R>
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_batched(
+    const int32_t* __restrict__ ps, const int32_t* __restrict__ pm, const double* __restrict__ srec,
+    const double* __restrict__ xs, const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
+    const int32_t* __restrict__ conn_m, const double* __restrict__ lambda, int64_t pair_cap,
+    double* __restrict__ gs_out, double* __restrict__ gm_out, double* __restrict__ ab_out,
+    double* __restrict__ J_out, DevStatus* st) {
+  constexpr int B = 32 * R;
+  __shared__ uint8_t perm_s[kAdjWarps][B];
+  uint8_t* perm = perm_s[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  AdjCounters ctr;
+  const bool ok = st->over_pairs == 0 && st->over_bins == 0;
+  const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
+  for (;;) {   // bounded: the shared counter only grows
+    int64_t base = 0;
+    if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr2, (unsigned long long)B);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    // phase A: cell count of each pair (clip without recording); empty pairs done here
+    int key[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int64_t p = base + rr * 32 + lane;
+      int nr = 0;
+      if (p < n) {
+        const double* r = srec + (int64_t)SR_STRIDE * ps[p];
+        PlaneMap mm;
+        double Pu[kPolyS], Pv[kPolyS];
+        unsigned long long dummy = 0;
+        nr = clip_polygon<NS, NM, kPolyS>(r, xm, conn_m, pm[p], mm, Pu, Pv, dummy);
+        if (nr == 0) {
+          double2* g1 = reinterpret_cast<double2*>(gs_out + 12 * p);
+          double2* g2 = reinterpret_cast<double2*>(gm_out + 12 * p);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) { g1[k] = make_double2(0.0, 0.0); g2[k] = make_double2(0.0, 0.0); }
+          if (DUAL) {
+            double2* a2 = reinterpret_cast<double2*>(ab_out + 16 * p);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a2[k] = make_double2(0.0, 0.0);
+          }
+          J_out[p] = 0.0;
+        }
+      }
+      key[rr] = nr == 0 ? 0 : (nr == 3 ? 1 : nr);
+    }
+    int pos[R];
+    int basecnt = 0;
+#pragma unroll 1
+    for (int v = kPolyS; v >= 1; --v) {
+      int before = 0;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const unsigned mk = __ballot_sync(0xffffffffu, key[rr] == v);
+        if (key[rr] == v) pos[rr] = basecnt + before + __popc(mk & lt_mask);
+        before += __popc(mk);
+      }
+      basecnt += before;
+    }
+    const int n_live = basecnt;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (key[rr] > 0) perm[pos[rr]] = (uint8_t)(rr * 32 + lane);
+    __syncwarp();
+    // phase B: full adjoint of each non-empty pair, rounds of similar cell counts
+    for (int i0 = 0; i0 < n_live; i0 += 32) {
+      const int i = i0 + lane;
+      if (i < n_live)
+        adjoint_pair_fast<NS, NM, SEG, DUAL>(base + perm[i], ps, pm, srec, xs, xm, conn_s, conn_m, lambda, gs_out,
+                                             gm_out, ab_out, J_out, ctr);
+    }
+    __syncwarp();
+  }
+  block_count_add(&st->clip_overflow, ctr.clip_over);
+  block_count_add(&st->newton_fail, ctr.newton_fail);
+}
+
 // Element quadrature point k (same rule as the precomputation).
 template <int NEN>
 __device__ __forceinline__ void elem_point_a(int k, double& xi, double& eta, double& w) {
@@ -748,13 +1258,38 @@ void launch_pairs_t(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned 
       c->dstat.as<DevStatus>());
 }
 
+template <int NS, int NM, bool SEG, bool DUAL>
+void launch_batched_t(mortar_ctx* c, int rounds) {
+  auto go = [&](auto kern) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjWarps * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    kern<<<(unsigned)(c->n_sm * per_sm), kAdjWarps * 32, 0, c->stream>>>(
+        c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
+        c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->lambda.as<double>(), c->pair_cap,
+        c->gs_pair.as<double>(), c->gm_pair.as<double>(), c->abar_pair.as<double>(), c->J_pair.as<double>(),
+        c->dstat.as<DevStatus>());
+  };
+  if (rounds <= 1) go(k_adjoint_batched<NS, NM, SEG, DUAL, 1>);
+  else if (rounds == 2) go(k_adjoint_batched<NS, NM, SEG, DUAL, 2>);
+  else go(k_adjoint_batched<NS, NM, SEG, DUAL, 4>);
+}
+
 template <int NS, int NM>
 void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk) {
   const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
-  if (seg && dual) launch_pairs_t<NS, NM, true, true>(c, rp, grid, block, chunk);
-  else if (seg) launch_pairs_t<NS, NM, true, false>(c, rp, grid, block, chunk);
-  else if (dual) launch_pairs_t<NS, NM, false, true>(c, rp, grid, block, chunk);
-  else launch_pairs_t<NS, NM, false, false>(c, rp, grid, block, chunk);
+  if (c->variant == 1) {
+    if (seg && dual) launch_pairs_t<NS, NM, true, true>(c, rp, grid, block, chunk);
+    else if (seg) launch_pairs_t<NS, NM, true, false>(c, rp, grid, block, chunk);
+    else if (dual) launch_pairs_t<NS, NM, false, true>(c, rp, grid, block, chunk);
+    else launch_pairs_t<NS, NM, false, false>(c, rp, grid, block, chunk);
+    return;
+  }
+  const int rounds = c->rounds > 0 ? c->rounds : 2;
+  if (seg && dual) launch_batched_t<NS, NM, true, true>(c, rounds);
+  else if (seg) launch_batched_t<NS, NM, true, false>(c, rounds);
+  else if (dual) launch_batched_t<NS, NM, false, true>(c, rounds);
+  else launch_batched_t<NS, NM, false, false>(c, rounds);
 }
 
 template <int NS>

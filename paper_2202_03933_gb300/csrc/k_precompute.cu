@@ -128,6 +128,16 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     }
     if (NS == 3) { r[SR_PS + 6] = 0.0; r[SR_PS + 7] = 0.0; }
     r[SR_REV] = area2 < 0.0 ? 1.0 : 0.0;
+    {
+      const double det = pm.c1u * pm.c2v - pm.c2u * pm.c1v;
+      const double id = 1.0 / det;
+      r[SR_BINV + 0] = pm.c2v * id;
+      r[SR_BINV + 1] = -pm.c2u * id;
+      r[SR_BINV + 2] = -pm.c1v * id;
+      r[SR_BINV + 3] = pm.c1u * id;
+      r[SR_AFF] = (NS == 3 || map_is_affine(pm)) ? 1.0 : 0.0;
+      r[SR_AFF + 1] = 0.0; r[SR_AFF + 2] = 0.0; r[SR_AFF + 3] = 0.0;
+    }
     // ---- tolerances: diameter and projected area
     double h2 = 0.0;
     for (int a = 0; a < NS; ++a)

@@ -188,3 +188,26 @@ def test_full_size_planar_2000_adjoint_sampled(mt, orc):
     Jr, rs, rm = orc.weighted_gap_grad(itf, lam, s[keep], mm[keep], o)
     _grad_parity(gs, gm, rs, rm)
     assert abs(J - Jr) <= 1e-12 * np.abs(rs).max()
+
+
+@pytest.mark.parametrize("variant,rounds", [(1, 0), (0, 1), (0, 4)])
+def test_adjoint_launch_variants(mt, orc, variant, rounds):
+    """Both adjoint schedules give the oracle's gradient (bilinear and tri3
+    masters, dual segment mode, warped slave)."""
+    warped = inputs.planar_noisy(13, 11, 1, 46, "w")
+    warped.xs = warped.xs.copy()
+    warped.xs[:, 2] = 0.02 * np.sin(5 * warped.xs[:, 0]) * np.cos(3 * warped.xs[:, 1])
+    warped.xm = warped.xm.copy()
+    warped.xm[:, 2] = 0.02 * np.sin(5 * warped.xm[:, 0]) * np.cos(3 * warped.xm[:, 1]) + 1e-3
+    warped.delta = 5e-3
+    for itf, d_domain in ((inputs.planar_noisy(15, 13, 1, 47, "v"), 1), (inputs.mixed_tri(16, 21, name="t"), 0),
+                          (warped, 0)):
+        lam = np.random.default_rng(9).uniform(-1, 1, itf.xs.shape)
+        m = mt.Mortar(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
+        m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+        m.set_launch(variant=variant, rounds=rounds)
+        J, gs, gm = m.weighted_gap_grad(lam)
+        s, mm = m.pairs()
+        o = orc.make_opts(lm=itf.lm, d_domain=d_domain, delta=itf.delta, n_threads=8)
+        Jr, rs, rm = orc.weighted_gap_grad(itf, lam, s, mm, o)
+        _grad_parity(gs, gm, rs, rm, scale=grad_term_scale(orc, itf, lam, s, mm, o))

@@ -259,3 +259,28 @@ def test_batched_block_diagonal(mt, orc):
     blk_r = np.searchsorted(sn, rows, side="right") - 1
     blk_c = np.searchsorted(mn, M.indices, side="right") - 1
     assert np.array_equal(blk_r, blk_c)
+
+
+@pytest.mark.parametrize("variant,rounds", [(1, 0), (0, 1), (0, 2), (0, 4)])
+def test_launch_variants_agree(mt, orc, variant, rounds):
+    """Every integration schedule gives the oracle's blocks (bilinear masters,
+    tri3 masters, a non-affine warped slave, segment mode)."""
+    cases = [(inputs.planar_noisy(41, 37, 1, 44, "v"), 1), (inputs.mixed_tri(33, 41, name="vt"), 0)]
+    warped = inputs.planar_noisy(21, 17, 0, 45, "w")
+    warped.xs = warped.xs.copy()
+    warped.xs[:, 0] += 0.2 / 21 * np.sin(7 * warped.xs[:, 1]) * (warped.xs[:, 0] * (1 - warped.xs[:, 0]))
+    cases.append((warped, 0))
+    for itf, d_domain in cases:
+        o = orc.make_opts(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
+        ref = orc.evaluate(itf, o)
+        m = mt.Mortar(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
+        m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+        m.set_launch(variant=variant, rounds=rounds)
+        m.evaluate()
+        Mb, Db, ne = m.pair_blocks(with_D=d_domain == 1)
+        assert np.array_equal(ne, ref.nonempty)
+        blocks_parity(Mb, ref.Mb)
+        if d_domain == 1:
+            blocks_parity(Db, ref.Db)
+        csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+        assert m.stats()["n_newton_fail"] == 0
