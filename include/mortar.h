@@ -92,12 +92,19 @@ typedef struct mortar_stats {
   int64_t n_bins;
   int64_t reruns;           /* capacity-driven re-executions of the last run */
   int64_t graph_kernels;    /* kernel nodes in the captured graph (0 before capture) */
+  int64_t fused;            /* 1: one pair kernel produced both the forward blocks and the adjoint */
   /* phase times of the last run (CUDA events on the context's stream, also
    * inside replayed graphs; 0 unless mortar_set_timing(ctx, 1)):
    * search = precompute + grid + binning + candidates; integrate = the
-   * per-pair integration kernel; assemble = CSR assembly; adjoint = all
-   * adjoint kernels, of which adjoint_pairs is the per-pair reverse sweep. */
+   * per-pair kernel producing the forward blocks (when fused = 1 that kernel
+   * also runs the adjoint's per-pair reverse sweep); assemble = CSR assembly;
+   * adjoint = the remaining adjoint kernels, of which adjoint_pairs is the
+   * separate per-pair reverse sweep (0 when fused). */
   float ms_search, ms_integrate, ms_assemble, ms_adjoint, ms_adjoint_pairs, ms_total;
+  /* CTA busy-time imbalance max/min of the batched pair kernel in the last run
+   * (timing on; the measure eta_t of the paper's load-balancing trigger,
+   * Sec. 4.3, taken over CTAs instead of processes); 0 if not measured */
+  float eta_t;
 } mortar_stats;
 
 typedef struct mortar_ctx mortar_ctx;

@@ -46,9 +46,9 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_interfaces", "n_pairs", "n_nonempty", "n_gauss_points", "n_cells", "n_newton_fail",
-        "n_xi_out_of_range", "n_clip_overflow", "nnz_D", "nnz_M", "n_bins", "reruns", "graph_kernels")] + \
+        "n_xi_out_of_range", "n_clip_overflow", "nnz_D", "nnz_M", "n_bins", "reruns", "graph_kernels", "fused")] + \
         [(n, ctypes.c_float) for n in ("ms_search", "ms_integrate", "ms_assemble", "ms_adjoint",
-                                       "ms_adjoint_pairs", "ms_total")]
+                                       "ms_adjoint_pairs", "ms_total", "eta_t")]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -147,6 +147,7 @@ void enqueue_run(mortar_ctx* c, const Phases& ph) {
   const RunParams rp = run_params(c);
   cudaStream_t st = c->stream;
   cudaMemsetAsync(c->dstat.p, 0, sizeof(DevStatus), st);
+  c->pair_grid = 0;
   if (c->timing) record_event(c->ev[0], st);
   launch_slave_precompute(c, rp);
   launch_master_boxes(c, rp);
@@ -154,15 +155,24 @@ void enqueue_run(mortar_ctx* c, const Phases& ph) {
   launch_bin_masters(c);
   launch_candidates(c);
   if (c->timing) record_event(c->ev[1], st);
-  if (ph.integrate) launch_integrate(c, rp);
+  // with the adjoint, the batched adjoint pair kernel also produces the
+  // forward blocks (one pass over the pairs instead of two)
+  const bool fused = ph.adjoint && ph.integrate && adjoint_fuses_forward(c);
+  if (fused) launch_adjoint_pairs(c, rp, true);
+  else if (ph.integrate) launch_integrate(c, rp);
   if (c->timing) record_event(c->ev[2], st);
   if (ph.assemble) {
     launch_assemble(c, rp);
     launch_finalize_status(c);
   }
   if (c->timing) record_event(c->ev[3], st);
-  if (ph.adjoint) launch_adjoint(c, rp, c->timing ? c->ev[5] : nullptr);
+  if (ph.adjoint) {
+    if (!fused) launch_adjoint_pairs(c, rp, false);
+    if (c->timing) record_event(c->ev[5], st);
+    launch_adjoint_rest(c, rp);
+  }
   if (c->timing) record_event(c->ev[4], st);
+  c->stats.fused = fused ? 1 : 0;
   cudaMemcpyAsync(c->hstat, c->dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
 }
 
@@ -216,6 +226,21 @@ int finish_run(mortar_ctx* c, const Phases& ph) {
     cudaEventElapsedTime(&s.ms_total, c->ev[0], c->ev[4]);
     s.ms_adjoint_pairs = 0.0f;
     if (ph.adjoint) cudaEventElapsedTime(&s.ms_adjoint_pairs, c->ev[3], c->ev[5]);
+    s.eta_t = 0.0f;
+    const int g = c->pair_grid;
+    if (g > 0 && (size_t)g * 16 <= c->cta_t.bytes) {   // CTA busy-time imbalance of the pair kernel
+      c->h_cta_t.resize(2 * (size_t)g);
+      if (cudaMemcpy(c->h_cta_t.data(), c->cta_t.p, 16 * (size_t)g, cudaMemcpyDeviceToHost) == cudaSuccess) {
+        unsigned long long lo = ~0ull, hi = 0;
+        for (int b = 0; b < g; ++b) {
+          const unsigned long long d = c->h_cta_t[2 * b + 1] - c->h_cta_t[2 * b];
+          lo = std::min(lo, d);
+          hi = std::max(hi, d);
+        }
+        if (lo > 0) s.eta_t = (float)((double)hi / (double)lo);
+      }
+      cudaGetLastError();
+    }
   }
   return MORTAR_OK;
 }
@@ -325,6 +350,7 @@ int set_common(mortar_ctx* c, int32_t n_if, const int64_t* sn_off, const int64_t
   MORTAR_TRY(buf_reserve(c->cand_cnt, Es * 4));
   MORTAR_TRY(buf_reserve(c->pair_off, (Es + 1) * 8));
   MORTAR_TRY(buf_reserve(c->row_cnt, std::max(Ns, Nm) * 4));
+  MORTAR_TRY(buf_reserve(c->row_cnt2, std::max<size_t>(Ns, 1) * 4));
   MORTAR_TRY(buf_reserve(c->rowptr_D, (Ns + 1) * 8));
   MORTAR_TRY(buf_reserve(c->rowptr_M, (Ns + 1) * 8));
   MORTAR_TRY(buf_reserve(c->n2e_s_ptr, (Ns + 1) * 8));
@@ -396,6 +422,7 @@ int mortar_create(mortar_ctx** out, const mortar_options* o, void* stream) {
     else r = cuda_status(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)), c->owns_stream = true;
   }
   if (r == MORTAR_OK) r = buf_reserve(c->dstat, sizeof(DevStatus));
+  if (r == MORTAR_OK) r = buf_reserve(c->cta_t, (size_t)c->n_sm * 64 * 2 * sizeof(unsigned long long));
   if (r == MORTAR_OK) r = cuda_status(cudaMallocHost((void**)&c->hstat, sizeof(DevStatus)));
   for (int i = 0; i < 8 && r == MORTAR_OK; ++i) r = cuda_status(cudaEventCreate(&c->ev[i]));
   if (r != MORTAR_OK) {
@@ -415,10 +442,10 @@ void mortar_destroy(mortar_ctx* c) {
                     &c->chunk_ptr, &c->bin_cap_off, &c->n2e_s_ptr, &c->n2e_s_ent, &c->n2e_m_ptr, &c->n2e_m_ent,
                     &c->srec, &c->De, &c->box_s, &c->box_m, &c->chunk_red, &c->grid, &c->mkey, &c->bin_cnt,
                     &c->bin_start, &c->bin_elems, &c->cand_cnt, &c->pair_off, &c->pairs_s, &c->pairs_m, &c->Mblk,
-                    &c->Dblk, &c->flag, &c->row_cnt, &c->rowptr_D, &c->col_D, &c->val_D, &c->rowptr_M,
+                    &c->Dblk, &c->flag, &c->row_cnt, &c->row_cnt2, &c->rowptr_D, &c->col_D, &c->val_D, &c->rowptr_M,
                     &c->col_M, &c->val_M, &c->scan_tmp, &c->lambda, &c->gs_pair, &c->gm_pair, &c->abar_pair,
                     &c->J_pair, &c->ge_elem, &c->mp_cnt, &c->mp_off, &c->mp_list, &c->grad_s, &c->grad_m,
-                    &c->J_part, &c->dstat};
+                    &c->J_part, &c->dstat, &c->cta_t};
   for (DevBuf* b : bufs) buf_free(*b);
   if (c->hstat) cudaFreeHost(c->hstat);
   for (int i = 0; i < 8; ++i)

@@ -102,10 +102,10 @@ __device__ __forceinline__ int clip_polygon(const double* __restrict__ r, const 
 
 // Inverse of an element map in the plane for many query points: affine maps
 // by a 2x2 inverse, bilinear ones by FP32 Newton on coordinates scaled by a
-// power of two, then two FP64 polishing steps x -= J^-1 r(x) with the FP64
-// residual r and J taken at the FP32 solution (FP32-accurate inverse).  Each
-// polishing step shrinks the error by ~1e-7, so FP32 accuracy (~1e-7) becomes
-// rounding level after the second.
+// power of two (error e0 ~ 1e-7 in xi), then one FP64 Newton step with the
+// FP64 residual and the FP64 Jacobian at the FP32 solution, whose inverse uses
+// an FP32 reciprocal refined once in FP64 (relative error ~1e-14): the step
+// leaves ~1e-14 e0 + |c3|/|J| e0^2 ~ 1e-15 in xi, i.e. rounding level.
 struct MapInverse {
   PlaneMap m;
   bool affine;
@@ -134,16 +134,25 @@ struct MapInverse {
     b00 = f2v * fd; b01 = -f2u * fd; b10 = -f1v * fd; b11 = f1u * fd;
   }
 
-  // FP64 inverse of the Jacobian at (xi, eta) (reverse sweeps need it exact)
+  // FP64 reciprocal of a Jacobian determinant: FP32 seed on the scaled value,
+  // one FP64 Newton refinement (relative error ~1e-14).
+  __device__ __forceinline__ double inv_det(double det) const {
+    double id = (double)__frcp_rn((float)(det * sc2)) * sc2;
+    const double e = fma(-det, id, 1.0);
+    return fma(id, e, id);
+  }
+
+  // Inverse of the Jacobian at (xi, eta) to ~1e-14 (the reverse sweep's
+  // implicit-function step)
   __device__ __forceinline__ void jinv(double xi, double eta, double& a00, double& a01, double& a10,
                                        double& a11) const {
     if (affine) {
       a00 = i00; a01 = i01; a10 = i10; a11 = i11;
       return;
     }
-    const double j00 = m.c1u + m.c3u * eta, j01 = m.c2u + m.c3u * xi;
-    const double j10 = m.c1v + m.c3v * eta, j11 = m.c2v + m.c3v * xi;
-    const double id = 1.0 / (j00 * j11 - j01 * j10);
+    const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
+    const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
+    const double id = inv_det(fma(j00, j11, -j01 * j10));
     a00 = j11 * id; a01 = -j01 * id; a10 = -j10 * id; a11 = j00 * id;
   }
 
@@ -172,19 +181,42 @@ struct MapInverse {
     }
     xi = (double)x;
     eta = (double)y;
-    const double j00 = m.c1u + m.c3u * eta, j01 = m.c2u + m.c3u * xi;
-    const double j10 = m.c1v + m.c3v * eta, j11 = m.c2v + m.c3v * xi;
-    const double det = (j00 * j11 - j01 * j10) * sc2;
-    const double id = (double)__frcp_rn((float)det) * sc2;
-    const double k00 = j11 * id, k01 = -j01 * id, k10 = -j10 * id, k11 = j00 * id;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const double ru = fma(fma(m.c3u, eta, m.c1u), xi, fma(m.c2u, eta, -du));
-      const double rv = fma(fma(m.c3v, eta, m.c1v), xi, fma(m.c2v, eta, -dv));
-      xi -= fma(k00, ru, k01 * rv);
-      eta -= fma(k10, ru, k11 * rv);
-    }
+    double k00, k01, k10, k11;
+    jinv(xi, eta, k00, k01, k10, k11);
+    const double ru = fma(fma(m.c3u, eta, m.c1u), xi, fma(m.c2u, eta, -du));
+    const double rv = fma(fma(m.c3v, eta, m.c1v), xi, fma(m.c2v, eta, -dv));
+    xi -= fma(k00, ru, k01 * rv);
+    eta -= fma(k10, ru, k11 * rv);
     return conv;
+  }
+};
+
+// Shape functions and the pull-back of a shape-function adjoint to xi:
+// quad4 with a = 1 - xi, b = 1 + xi, c = 1 - eta, d = 1 + eta:
+//   N = (a c, b c, b d, a d) / 4,  dN/dxi = (-c, c, d, -d) / 4,  dN/deta = (-a, -b, b, a) / 4.
+template <int NEN>
+struct ShapeAD {
+  double N[4];
+  double qa, qb, qc, qd;
+  __device__ __forceinline__ void eval(double xi, double eta) {
+    if constexpr (NEN == 4) {
+      qa = 0.25 * (1.0 - xi); qb = 0.25 * (1.0 + xi);
+      const double c = 1.0 - eta, d = 1.0 + eta;
+      qc = 0.25 * c; qd = 0.25 * d;
+      N[0] = qa * c; N[1] = qb * c; N[2] = qb * d; N[3] = qa * d;
+    } else {
+      N[0] = 1.0 - xi - eta; N[1] = xi; N[2] = eta; N[3] = 0.0;
+    }
+  }
+  // (dxi, deta) += sum_k Nb[k] grad N_k
+  __device__ __forceinline__ void pull(const double* Nb, double& g0, double& g1) const {
+    if constexpr (NEN == 4) {
+      g0 = fma(qc, Nb[1] - Nb[0], qd * (Nb[2] - Nb[3]));
+      g1 = fma(qa, Nb[3] - Nb[0], qb * (Nb[2] - Nb[1]));
+    } else {
+      g0 = Nb[1] - Nb[0];
+      g1 = Nb[2] - Nb[0];
+    }
   }
 };
 

@@ -209,6 +209,18 @@ __device__ __forceinline__ void tri7_point(int q, double& l1, double& l2, double
   }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Busy interval of this CTA of a persistent kernel (first / last thread
+// activity), recorded only when cta_t is non-null.
+__device__ __forceinline__ void cta_mark(unsigned long long* cta_t, int which) {
+  if (cta_t && threadIdx.x == 0) cta_t[2 * blockIdx.x + which] = global_ns();
+}
+
 // Block-wide sum of an unsigned counter, one atomic per block.
 __device__ __forceinline__ void block_count_add(unsigned long long* dst, unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -72,11 +72,14 @@ struct mortar_ctx {
   mortar::DevBuf pairs_s, pairs_m;          // int32 (pair_cap)
   int64_t pair_cap = 0;
   mortar::DevBuf Mblk, Dblk, flag;          // FP64 16/pair, uint8/pair
-  mortar::DevBuf row_cnt;                   // int32 (max(Ns, Nm))
+  mortar::DevBuf row_cnt, row_cnt2;         // int32 (max(Ns, Nm)), int32 (Ns)
   mortar::DevBuf rowptr_D, col_D, val_D;
   mortar::DevBuf rowptr_M, col_M, val_M;
   int64_t nnz_cap_D = 0, nnz_cap_M = 0;
   mortar::DevBuf scan_tmp;                  // block partials of the scans
+  mortar::DevBuf cta_t;                     // per-CTA busy intervals of the pair kernel (timing)
+  int pair_grid = 0;                        // CTAs of the last batched pair kernel (timing)
+  std::vector<unsigned long long> h_cta_t;
 
   // ---- adjoint workspaces
   mortar::DevBuf lambda;                    // Ns x 3
@@ -129,7 +132,9 @@ void launch_finalize_status(mortar_ctx* c);
 
 // k_adjoint.cu
 int prepare_adjoint_buffers(mortar_ctx* c);   // sizes per-pair adjoint buffers from n_pairs
-void launch_adjoint(mortar_ctx* c, const RunParams& rp, cudaEvent_t after_pairs);
+bool adjoint_fuses_forward(const mortar_ctx* c);   // the adjoint pair kernel also writes M/D blocks
+void launch_adjoint_pairs(mortar_ctx* c, const RunParams& rp, bool fused);
+void launch_adjoint_rest(mortar_ctx* c, const RunParams& rp);   // element adjoint, gathers, J
 
 RunParams run_params(const mortar_ctx* c);
 
@@ -146,6 +151,8 @@ struct IntegrateArgs {
   int64_t pair_cap;
   DevStatus* st;
   cudaStream_t stream;
+  unsigned long long* cta_t = nullptr;   // per-CTA busy interval (timing only)
+  int* grid_out = nullptr;               // receives the grid size used
 };
 void launch_slave_precompute_raw(const double* xs, const int32_t* conn_s, int64_t Es, int nen_s,
                                  const RunParams& rp, double* srec, double* De, double* box, DevStatus* st,

@@ -98,7 +98,14 @@ __device__ __forceinline__ void map_coeff_reverse(const double* cb, double* pbu,
 }
 
 struct AdjCounters {
-  unsigned long long clip_over = 0, newton_fail = 0;
+  unsigned long long clip_over = 0, newton_fail = 0, nonempty = 0, cells = 0, gp = 0;
+};
+
+// Forward outputs written by the fused kernel (M, D blocks and flags).
+struct FwdOut {
+  double* Mblk;
+  double* Dblk;
+  uint8_t* flag;
 };
 
 template <int NS, int NM, bool SEG, bool DUAL>
@@ -505,13 +512,14 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_pairs(
 //    2x2 inverse, or FP32 Newton + two FP64 polishing steps), and the
 //    implicit-function step uses the exact FP64 inverse Jacobian;
 //  * a warp sorts its batch of pairs by cell count before the sweep.
-template <int NS, int NM, bool SEG, bool DUAL>
+template <int NS, int NM, bool SEG, bool DUAL, bool FWD>
 __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, const int32_t* __restrict__ pm,
                                   const double* __restrict__ srec, const double* __restrict__ xs,
                                   const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
                                   const int32_t* __restrict__ conn_m, const double* __restrict__ lambda,
                                   double* __restrict__ gs_out, double* __restrict__ gm_out,
-                                  double* __restrict__ ab_out, double* __restrict__ J_out, AdjCounters& ctr) {
+                                  double* __restrict__ ab_out, double* __restrict__ J_out,
+                                  const FwdOut& fo, AdjCounters& ctr) {
   const int32_t s = ps[p], m = pm[p];
   const double* r = srec + (int64_t)SR_STRIDE * s;
   double gX[4][3], gY[4][3];
@@ -673,6 +681,7 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
       const double cr = cross2(e1u, e1v, e2u, e2v);
       const double area = 0.5 * fabs(cr);
       double area_b = 0.0, e1bu = 0.0, e1bv = 0.0, e2bu = 0.0, e2bv = 0.0, abu = 0.0, abv = 0.0;
+      if (FWD) { ctr.cells++; ctr.gp += 7; }
 #pragma unroll 1
       for (int q = 0; q < 7; ++q) {
         double l1, l2, w;
@@ -683,9 +692,12 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
         double xs1, xs2, xm1, xm2;
         if (!si.solve(xu, xv, xs1, xs2)) ctr.newton_fail++;
         if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
-        double Ns[4], Nm[4];
-        shape_fn<NS>(xs1, xs2, Ns);
-        shape_fn<NM>(xm1, xm2, Nm);
+        ShapeAD<NS> SA;
+        ShapeAD<NM> MA;
+        SA.eval(xs1, xs2);
+        MA.eval(xm1, xm2);
+        const double* Ns = SA.N;
+        const double* Nm = MA.N;
         double t[4], f = 0.0;
 #pragma unroll
         for (int c = 0; c < NS; ++c) {
@@ -725,14 +737,9 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
 #pragma unroll
             for (int b = 0; b < NS; ++b) H[c][b] = fma(wn, Ns[b], H[c][b]);
         }
-        double dNs[4][2], dNm[4][2];
-        shape_grad<NS>(xs1, xs2, dNs);
-        shape_grad<NM>(xm1, xm2, dNm);
-        double xsb0 = 0.0, xsb1 = 0.0, xmb0 = 0.0, xmb1 = 0.0;
-#pragma unroll
-        for (int c = 0; c < NS; ++c) { xsb0 = fma(Nsb[c], dNs[c][0], xsb0); xsb1 = fma(Nsb[c], dNs[c][1], xsb1); }
-#pragma unroll
-        for (int l = 0; l < NM; ++l) { xmb0 = fma(Nmb[l], dNm[l][0], xmb0); xmb1 = fma(Nmb[l], dNm[l][1], xmb1); }
+        double xsb0, xsb1, xmb0, xmb1;
+        SA.pull(Nsb, xsb0, xsb1);
+        MA.pull(Nmb, xmb0, xmb1);
         double a00, a01, a10, a11;
         si.jinv(xs1, xs2, a00, a01, a10, a11);
         const double msu = a00 * xsb0 + a10 * xsb1, msv = a01 * xsb0 + a11 * xsb1;   // J^-T xib
@@ -785,6 +792,36 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
         for (int c = 0; c < NS; ++c) acc = acc + H[c][b] * Lam[c];
         gX[b][0] += acc.x; gX[b][1] += acc.y; gX[b][2] += acc.z;
       }
+    if (FWD) {   // fused forward: M = A G, D = A H of this pair
+      ctr.nonempty++;
+      double* mo = fo.Mblk + 16 * p;
+      for (int a = 0; a < 4; ++a)
+        for (int l = 0; l < 4; ++l) {
+          double v = 0.0;
+          if (a < NS && l < NM) {
+            if (DUAL)
+              for (int c = 0; c < NS; ++c) v += r[SR_A + 4 * a + c] * G[c][l];
+            else
+              v = G[a][l];
+          }
+          mo[4 * a + l] = v;
+        }
+      if (SEG) {
+        double* dout = fo.Dblk + 16 * p;
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            double v = 0.0;
+            if (a < NS && b < NS) {
+              if (DUAL)
+                for (int c = 0; c < NS; ++c) v += r[SR_A + 4 * a + c] * H[c][b];
+              else
+                v = H[a][b];
+            }
+            dout[4 * a + b] = v;
+          }
+      }
+      fo.flag[p] = 1;
+    }
     // ---- reverse merge and clipping stages
     double Bu[NS + 1][kPolyA], Bv[NS + 1][kPolyA];
     for (int k = 0; k < nl; ++k) { Bu[last][k] = 0.0; Bv[last][k] = 0.0; }
@@ -921,13 +958,14 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
 
 constexpr int kAdjWarps = 4;
 
-template <int NS, int NM, bool SEG, bool DUAL, int R>
+template <int NS, int NM, bool SEG, bool DUAL, bool FWD, int R>
 __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_batched(
     const int32_t* __restrict__ ps, const int32_t* __restrict__ pm, const double* __restrict__ srec,
     const double* __restrict__ xs, const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
     const int32_t* __restrict__ conn_m, const double* __restrict__ lambda, int64_t pair_cap,
     double* __restrict__ gs_out, double* __restrict__ gm_out, double* __restrict__ ab_out,
-    double* __restrict__ J_out, DevStatus* st) {
+    double* __restrict__ J_out, FwdOut fo, DevStatus* st, unsigned long long* cta_t) {
+  cta_mark(cta_t, 0);
   constexpr int B = 32 * R;
   __shared__ uint8_t perm_s[kAdjWarps][B];
   uint8_t* perm = perm_s[threadIdx.x >> 5];
@@ -964,6 +1002,17 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_batched(
             for (int k = 0; k < 8; ++k) a2[k] = make_double2(0.0, 0.0);
           }
           J_out[p] = 0.0;
+          if (FWD) {
+            double2* mo = reinterpret_cast<double2*>(fo.Mblk + 16 * p);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) mo[k] = make_double2(0.0, 0.0);
+            if (SEG) {
+              double2* dd = reinterpret_cast<double2*>(fo.Dblk + 16 * p);
+#pragma unroll
+              for (int k = 0; k < 8; ++k) dd[k] = make_double2(0.0, 0.0);
+            }
+            fo.flag[p] = 0;
+          }
         }
       }
       key[rr] = nr == 0 ? 0 : (nr == 3 ? 1 : nr);
@@ -990,13 +1039,20 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_batched(
     for (int i0 = 0; i0 < n_live; i0 += 32) {
       const int i = i0 + lane;
       if (i < n_live)
-        adjoint_pair_fast<NS, NM, SEG, DUAL>(base + perm[i], ps, pm, srec, xs, xm, conn_s, conn_m, lambda, gs_out,
-                                             gm_out, ab_out, J_out, ctr);
+        adjoint_pair_fast<NS, NM, SEG, DUAL, FWD>(base + perm[i], ps, pm, srec, xs, xm, conn_s, conn_m, lambda,
+                                                  gs_out, gm_out, ab_out, J_out, fo, ctr);
     }
     __syncwarp();
   }
   block_count_add(&st->clip_overflow, ctr.clip_over);
   block_count_add(&st->newton_fail, ctr.newton_fail);
+  if (FWD) {
+    block_count_add(&st->nonempty, ctr.nonempty);
+    block_count_add(&st->cells, ctr.cells);
+    block_count_add(&st->gauss_points, ctr.gp);
+  }
+  __syncthreads();
+  cta_mark(cta_t, 1);
 }
 
 // Element quadrature point k (same rule as the precomputation).
@@ -1258,25 +1314,36 @@ void launch_pairs_t(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned 
       c->dstat.as<DevStatus>());
 }
 
-template <int NS, int NM, bool SEG, bool DUAL>
-void launch_batched_t(mortar_ctx* c, int rounds) {
+template <int NS, int NM, bool SEG, bool DUAL, bool FWD>
+void launch_batched_f(mortar_ctx* c, int rounds) {
+  const FwdOut fo{c->Mblk.as<double>(), c->Dblk.as<double>(), c->flag.as<uint8_t>()};
+  unsigned long long* cta_t = (FWD && c->timing && c->cta_t.p) ? c->cta_t.as<unsigned long long>() : nullptr;
   auto go = [&](auto kern) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjWarps * 32, 0);
     if (per_sm < 1) per_sm = 1;
-    kern<<<(unsigned)(c->n_sm * per_sm), kAdjWarps * 32, 0, c->stream>>>(
+    const unsigned grid = (unsigned)(c->n_sm * per_sm);
+    if (cta_t) c->pair_grid = (int)grid;
+    kern<<<grid, kAdjWarps * 32, 0, c->stream>>>(
         c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
         c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->lambda.as<double>(), c->pair_cap,
-        c->gs_pair.as<double>(), c->gm_pair.as<double>(), c->abar_pair.as<double>(), c->J_pair.as<double>(),
-        c->dstat.as<DevStatus>());
+        c->gs_pair.as<double>(), c->gm_pair.as<double>(), c->abar_pair.as<double>(), c->J_pair.as<double>(), fo,
+        c->dstat.as<DevStatus>(), cta_t);
   };
-  if (rounds <= 1) go(k_adjoint_batched<NS, NM, SEG, DUAL, 1>);
-  else if (rounds == 2) go(k_adjoint_batched<NS, NM, SEG, DUAL, 2>);
-  else go(k_adjoint_batched<NS, NM, SEG, DUAL, 4>);
+  if (rounds <= 1) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 1>);
+  else if (rounds == 2) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 2>);
+  else go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 4>);
+}
+
+template <int NS, int NM, bool SEG, bool DUAL>
+void launch_batched_t(mortar_ctx* c, int rounds, bool fused) {
+  if (fused) launch_batched_f<NS, NM, SEG, DUAL, true>(c, rounds);
+  else launch_batched_f<NS, NM, SEG, DUAL, false>(c, rounds);
 }
 
 template <int NS, int NM>
-void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk) {
+void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk,
+                       bool fused) {
   const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
   if (c->variant == 1) {
     if (seg && dual) launch_pairs_t<NS, NM, true, true>(c, rp, grid, block, chunk);
@@ -1286,10 +1353,10 @@ void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsign
     return;
   }
   const int rounds = c->rounds > 0 ? c->rounds : 2;
-  if (seg && dual) launch_batched_t<NS, NM, true, true>(c, rounds);
-  else if (seg) launch_batched_t<NS, NM, true, false>(c, rounds);
-  else if (dual) launch_batched_t<NS, NM, false, true>(c, rounds);
-  else launch_batched_t<NS, NM, false, false>(c, rounds);
+  if (seg && dual) launch_batched_t<NS, NM, true, true>(c, rounds, fused);
+  else if (seg) launch_batched_t<NS, NM, true, false>(c, rounds, fused);
+  else if (dual) launch_batched_t<NS, NM, false, true>(c, rounds, fused);
+  else launch_batched_t<NS, NM, false, false>(c, rounds, fused);
 }
 
 template <int NS>
@@ -1330,19 +1397,23 @@ int prepare_adjoint_buffers(mortar_ctx* c) {
   return MORTAR_OK;
 }
 
-void launch_adjoint(mortar_ctx* c, const RunParams& rp, cudaEvent_t after_pairs) {
-  DevStatus* st = c->dstat.as<DevStatus>();
+bool adjoint_fuses_forward(const mortar_ctx* c) { return c->variant == 0; }
+
+void launch_adjoint_pairs(mortar_ctx* c, const RunParams& rp, bool fused) {
   const unsigned block = c->block_size > 0 ? (unsigned)c->block_size : 128u;
   const int32_t chunk = c->chunk_pairs > 0 ? c->chunk_pairs : 32;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_pairs<4, 4, false, true>, (int)block, 0);
   if (per_sm < 1) per_sm = 1;
   const unsigned grid = (unsigned)(c->n_sm * per_sm);
-  if (c->nen_s == 4 && c->nen_m == 4) launch_pairs_nsnm<4, 4>(c, rp, grid, block, chunk);
-  else if (c->nen_s == 4 && c->nen_m == 3) launch_pairs_nsnm<4, 3>(c, rp, grid, block, chunk);
-  else if (c->nen_s == 3 && c->nen_m == 4) launch_pairs_nsnm<3, 4>(c, rp, grid, block, chunk);
-  else launch_pairs_nsnm<3, 3>(c, rp, grid, block, chunk);
-  if (after_pairs) record_event(after_pairs, c->stream);
+  if (c->nen_s == 4 && c->nen_m == 4) launch_pairs_nsnm<4, 4>(c, rp, grid, block, chunk, fused);
+  else if (c->nen_s == 4 && c->nen_m == 3) launch_pairs_nsnm<4, 3>(c, rp, grid, block, chunk, fused);
+  else if (c->nen_s == 3 && c->nen_m == 4) launch_pairs_nsnm<3, 4>(c, rp, grid, block, chunk, fused);
+  else launch_pairs_nsnm<3, 3>(c, rp, grid, block, chunk, fused);
+}
+
+void launch_adjoint_rest(mortar_ctx* c, const RunParams& rp) {
+  DevStatus* st = c->dstat.as<DevStatus>();
   if (c->nen_s == 4) launch_elems_ns<4>(c, rp); else launch_elems_ns<3>(c, rp);
   // master element -> pair lists
   cudaMemsetAsync(c->mp_cnt.p, 0, (size_t)std::max<int64_t>(c->Em, 1) * 4, c->stream);

@@ -87,62 +87,108 @@ struct RowSource {
   }
 };
 
-// MODE 0: count unique columns of each row; MODE 1: write the row.
+// Sorted list of unique columns with running sums: inserting (c, v) adds v to
+// column c's sum (sums in insertion order, i.e. gather order) or opens c.
+template <int CAP>
+struct RowAcc {
+  int32_t col[CAP];
+  double val[CAP];
+  int u = 0;
+  bool over = false;
+  __device__ __forceinline__ void add(int32_t c, double v) {
+    int lo = 0, hi = u;   // first index with col >= c
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (col[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    if (lo < u && col[lo] == c) {
+      val[lo] += v;
+      return;
+    }
+    if (u == CAP) {
+      over = true;
+      return;
+    }
+    for (int k = u; k > lo; --k) { col[k] = col[k - 1]; val[k] = val[k - 1]; }
+    col[lo] = c;
+    val[lo] = v;
+    ++u;
+  }
+};
+
+// Long row (more unique columns than the accumulator holds): repeated
+// selection of the next column, sums in gather order.  Returns the count.
 template <int MODE, class Src>
-__global__ void __launch_bounds__(kThreads) k_rows(Src src, int64_t N, int32_t* __restrict__ row_cnt,
-                                                   const int64_t* __restrict__ rowptr, int64_t nnz_cap,
-                                                   int32_t* __restrict__ col_out, double* __restrict__ val_out,
-                                                   DevStatus* st, int which_over) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  if (st->over_pairs) {   // pair buffers incomplete: the run is repeated with larger ones
-    if (MODE == 0) row_cnt[j] = 0;
-    return;
-  }
-  if (MODE == 1 && rowptr[N] > nnz_cap) {
-    if (j == 0) atomicMax(&st->over_nnz, (unsigned long long)rowptr[N]);
-    return;
-  }
-  int32_t col[kMaxRow];
-  double val[kMaxRow];
-  int k = 0;
-  src.visit(j, [&](int32_t c, double v) {
-    if (k < kMaxRow) {   // stable insertion by column
-      int b = k - 1;
-      while (b >= 0 && col[b] > c) { col[b + 1] = col[b]; val[b + 1] = val[b]; --b; }
-      col[b + 1] = c;
-      val[b + 1] = v;
-    }
-    ++k;
-  });
-  int64_t out = MODE == 1 ? rowptr[j] : 0;
-  if (k <= kMaxRow) {
-    int u = 0;
-    for (int a = 0; a < k;) {
-      const int32_t c = col[a];
-      double s = 0.0;
-      while (a < k && col[a] == c) s += val[a++];
-      if (MODE == 1) { col_out[out + u] = c; val_out[out + u] = s; }
-      ++u;
-    }
-    if (MODE == 0) row_cnt[j] = u;
-    return;
-  }
-  // long row: repeated selection of the next column, sums in gather order
-  if (MODE == 0 && which_over == 0) atomicAdd(&st->row_slow, 1ull);
+__device__ int row_slow(const Src& src, int64_t j, int64_t out, int32_t* __restrict__ col_out,
+                        double* __restrict__ val_out) {
   int u = 0;
   int32_t last = -1;
   for (;;) {
     int32_t next = 0x7fffffff;
     src.visit(j, [&](int32_t c, double) { if (c > last && c < next) next = c; });
     if (next == 0x7fffffff) break;
+    bool first = true;
     double s = 0.0;
-    src.visit(j, [&](int32_t c, double v) { if (c == next) s += v; });
+    src.visit(j, [&](int32_t c, double v) {
+      if (c == next) {
+        s = first ? v : s + v;
+        first = false;
+      }
+    });
     if (MODE == 1) { col_out[out + u] = next; val_out[out + u] = s; }
     ++u;
     last = next;
   }
-  if (MODE == 0) row_cnt[j] = u;
+  return u;
+}
+
+// One thread per slave node (row): both D and M.  MODE 0 counts the unique
+// columns of each row, MODE 1 writes the rows.
+template <int MODE, class SrcD, class SrcM>
+__global__ void __launch_bounds__(kThreads) k_rows(SrcD srcD, SrcM srcM, int64_t N, int32_t* __restrict__ cntD,
+                                                   int32_t* __restrict__ cntM, const int64_t* __restrict__ rpD,
+                                                   const int64_t* __restrict__ rpM, int64_t capD, int64_t capM,
+                                                   int32_t* __restrict__ colD, double* __restrict__ valD,
+                                                   int32_t* __restrict__ colM, double* __restrict__ valM,
+                                                   DevStatus* st) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  if (st->over_pairs) {   // pair buffers incomplete: the run is repeated with larger ones
+    if (MODE == 0) { cntD[j] = 0; cntM[j] = 0; }
+    return;
+  }
+  if (MODE == 1 && (rpD[N] > capD || rpM[N] > capM)) {
+    if (j == 0) atomicMax(&st->over_nnz, 1ull);
+    return;
+  }
+  {
+    RowAcc<32> acc;
+    srcD.visit(j, [&](int32_t c, double v) { acc.add(c, v); });
+    int u = acc.u;
+    const int64_t out = MODE == 1 ? rpD[j] : 0;
+    if (!acc.over) {
+      if (MODE == 1)
+        for (int k = 0; k < u; ++k) { colD[out + k] = acc.col[k]; valD[out + k] = acc.val[k]; }
+    } else {
+      if (MODE == 0) atomicAdd(&st->row_slow, 1ull);
+      u = row_slow<MODE>(srcD, j, out, colD, valD);
+    }
+    if (MODE == 0) cntD[j] = u;
+  }
+  {
+    RowAcc<64> acc;
+    srcM.visit(j, [&](int32_t c, double v) { acc.add(c, v); });
+    int u = acc.u;
+    const int64_t out = MODE == 1 ? rpM[j] : 0;
+    if (!acc.over) {
+      if (MODE == 1)
+        for (int k = 0; k < u; ++k) { colM[out + k] = acc.col[k]; valM[out + k] = acc.val[k]; }
+    } else {
+      if (MODE == 0) atomicAdd(&st->row_slow, 1ull);
+      u = row_slow<MODE>(srcM, j, out, colM, valM);
+    }
+    if (MODE == 0) cntM[j] = u;
+  }
 }
 
 __global__ void k_finalize(const int64_t* __restrict__ rpD, const int64_t* __restrict__ rpM, int64_t N,
@@ -153,32 +199,35 @@ __global__ void k_finalize(const int64_t* __restrict__ rpD, const int64_t* __res
   }
 }
 
-template <int WHICH, int NS, int NM>
-void assemble_one(mortar_ctx* c, const double* blk, mortar::DevBuf& rowptr, mortar::DevBuf& col,
-                  mortar::DevBuf& val, int64_t cap, int which_over) {
-  RowSource<WHICH, NS, NM> src{c->n2e_s_ptr.as<int64_t>(), c->n2e_s_ent.as<int64_t>(), c->pair_off.as<int64_t>(),
-                               c->pairs_m.as<int32_t>(), c->flag.as<uint8_t>(), blk, c->conn_s.as<int32_t>(),
-                               c->conn_m.as<int32_t>()};
+template <int WHICHD, int NS, int NM>
+void assemble_t(mortar_ctx* c, const double* blkD) {
+  RowSource<WHICHD, NS, NM> srcD{c->n2e_s_ptr.as<int64_t>(), c->n2e_s_ent.as<int64_t>(), c->pair_off.as<int64_t>(),
+                                 c->pairs_m.as<int32_t>(), c->flag.as<uint8_t>(), blkD, c->conn_s.as<int32_t>(),
+                                 c->conn_m.as<int32_t>()};
+  RowSource<2, NS, NM> srcM{c->n2e_s_ptr.as<int64_t>(), c->n2e_s_ent.as<int64_t>(), c->pair_off.as<int64_t>(),
+                            c->pairs_m.as<int32_t>(), c->flag.as<uint8_t>(), c->Mblk.as<double>(),
+                            c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>()};
   DevStatus* st = c->dstat.as<DevStatus>();
   const int64_t N = c->Ns;
   const unsigned g = (unsigned)((N + kThreads - 1) / kThreads);
+  int32_t* cntD = c->row_cnt.as<int32_t>();
+  int32_t* cntM = c->row_cnt2.as<int32_t>();
   if (N > 0)
-    k_rows<0><<<g, kThreads, 0, c->stream>>>(src, N, c->row_cnt.as<int32_t>(), nullptr, 0, nullptr, nullptr, st,
-                                              which_over);
-  launch_exclusive_scan_i32(c->row_cnt.as<int32_t>(), rowptr.as<int64_t>(), nullptr, N, c->scan_tmp.as<int64_t>(),
-                            c->stream);
+    k_rows<0><<<g, kThreads, 0, c->stream>>>(srcD, srcM, N, cntD, cntM, nullptr, nullptr, 0, 0, nullptr, nullptr,
+                                              nullptr, nullptr, st);
+  launch_exclusive_scan_i32(cntD, c->rowptr_D.as<int64_t>(), nullptr, N, c->scan_tmp.as<int64_t>(), c->stream);
+  launch_exclusive_scan_i32(cntM, c->rowptr_M.as<int64_t>(), nullptr, N, c->scan_tmp.as<int64_t>(), c->stream);
   if (N > 0)
-    k_rows<1><<<g, kThreads, 0, c->stream>>>(src, N, nullptr, rowptr.as<int64_t>(), cap, col.as<int32_t>(),
-                                              val.as<double>(), st, which_over);
+    k_rows<1><<<g, kThreads, 0, c->stream>>>(srcD, srcM, N, nullptr, nullptr, c->rowptr_D.as<int64_t>(),
+                                              c->rowptr_M.as<int64_t>(), c->nnz_cap_D, c->nnz_cap_M,
+                                              c->col_D.as<int32_t>(), c->val_D.as<double>(), c->col_M.as<int32_t>(),
+                                              c->val_M.as<double>(), st);
 }
 
 template <int NS, int NM>
 void assemble_nsnm(mortar_ctx* c, const RunParams& rp) {
-  if (rp.d_domain == 1)
-    assemble_one<1, NS, NM>(c, c->Dblk.as<double>(), c->rowptr_D, c->col_D, c->val_D, c->nnz_cap_D, 0);
-  else
-    assemble_one<0, NS, NM>(c, c->De.as<double>(), c->rowptr_D, c->col_D, c->val_D, c->nnz_cap_D, 0);
-  assemble_one<2, NS, NM>(c, c->Mblk.as<double>(), c->rowptr_M, c->col_M, c->val_M, c->nnz_cap_M, 1);
+  if (rp.d_domain == 1) assemble_t<1, NS, NM>(c, c->Dblk.as<double>());
+  else assemble_t<0, NS, NM>(c, c->De.as<double>());
 }
 
 }  // namespace

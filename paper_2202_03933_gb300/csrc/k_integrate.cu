@@ -220,7 +220,9 @@ template <int NS, int NM, bool SEG, int R>
 __global__ void __launch_bounds__(128) k_integrate_batched(
     const int32_t* __restrict__ ps, const int32_t* __restrict__ pm, const double* __restrict__ srec,
     const double* __restrict__ xm, const int32_t* __restrict__ conn_m, RunParams rp, double* __restrict__ Mblk,
-    double* __restrict__ Dblk, uint8_t* __restrict__ flag, int64_t pair_cap, DevStatus* st) {
+    double* __restrict__ Dblk, uint8_t* __restrict__ flag, int64_t pair_cap, DevStatus* st,
+    unsigned long long* cta_t) {
+  cta_mark(cta_t, 0);
   using L = BatchSmem<R>;
   constexpr int B = L::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -387,6 +389,8 @@ __global__ void __launch_bounds__(128) k_integrate_batched(
   block_count_add(&st->newton_fail, ctr.newton_fail);
   block_count_add(&st->xi_oor, ctr.xi_oor);
   block_count_add(&st->clip_overflow, ctr.clip_over);
+  __syncthreads();
+  cta_mark(cta_t, 1);
 }
 
 template <int NS, int NM, bool SEG, int R>
@@ -398,8 +402,10 @@ void launch_batched_t(const IntegrateArgs& a, const RunParams& rp, int n_sm) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, shm);
   if (per_sm < 1) per_sm = 1;
-  kern<<<(unsigned)(n_sm * per_sm), kWarps * 32, shm, a.stream>>>(a.ps, a.pm, a.srec, a.xm, a.conn_m, rp, a.Mblk,
-                                                                  a.Dblk, a.flag, a.pair_cap, a.st);
+  const unsigned grid = (unsigned)(n_sm * per_sm);
+  if (a.grid_out) *a.grid_out = (int)grid;
+  kern<<<grid, kWarps * 32, shm, a.stream>>>(a.ps, a.pm, a.srec, a.xm, a.conn_m, rp, a.Mblk, a.Dblk, a.flag,
+                                             a.pair_cap, a.st, a.cta_t);
 }
 
 template <int NS, int NM, bool SEG>
@@ -448,6 +454,11 @@ void launch_integrate(mortar_ctx* c, const RunParams& rp) {
   IntegrateArgs a{c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xm.as<double>(),
                   c->conn_m.as<int32_t>(), c->Mblk.as<double>(), c->Dblk.as<double>(), c->flag.as<uint8_t>(),
                   c->pair_cap, c->dstat.as<DevStatus>(), c->stream};
+  c->pair_grid = 0;
+  if (c->timing && c->cta_t.p) {
+    a.cta_t = c->cta_t.as<unsigned long long>();
+    a.grid_out = &c->pair_grid;
+  }
   const int block = c->block_size > 0 ? c->block_size : 128;
   const int chunk = c->chunk_pairs > 0 ? c->chunk_pairs : 32;
   const int rounds = c->rounds > 0 ? c->rounds : 2;

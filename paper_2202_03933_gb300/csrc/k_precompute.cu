@@ -152,75 +152,99 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     r[SR_EPSA] = rp.area_tol_rel * (0.5 * fabs(area2));
     degenerate = !(ln > 0.0) || !(le > 0.0) || !(fabs(area2) > 0.0) || !isfinite(h);
     if (degenerate) r[SR_EPSIN] = -1.0;   // marks the element; its pairs integrate to nothing
-    // ---- LM coefficients
-    double A[4][4];
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) A[a][b] = a == b ? 1.0 : 0.0;
+    // ---- element integrals Me[a][b] = int N_a N_b, Dh[a] = int N_a (surface measure)
+    // An element whose bilinear term is negligible (parallelogram, any tri3) has a
+    // constant surface Jacobian J0, and then Me = J0 Mref, Dh = J0 dref exactly.
     double Me[4][4], Dh[4];
     for (int a = 0; a < 4; ++a) {
       Dh[a] = 0.0;
       for (int b = 0; b < 4; ++b) Me[a][b] = 0.0;
     }
-    constexpr int nq = NS == 4 ? 9 : 7;
-    for (int q = 0; q < nq; ++q) {
-      double xi, eta, w;
-      elem_point<NS>(q, xi, eta, w);
-      double N[4];
-      shape_fn<NS>(xi, eta, N);
-      const double wj = w * surface_jac<NS>(X, xi, eta);
-      for (int a = 0; a < NS; ++a) {
-        Dh[a] += wj * N[a];
-        for (int b = 0; b < NS; ++b) Me[a][b] += wj * N[a] * N[b];
+    bool flat_jac = NS == 3;
+    if constexpr (NS == 4) {
+      const V3 d3 = {0.25 * ((X[0].x - X[1].x) + (X[2].x - X[3].x)), 0.25 * ((X[0].y - X[1].y) + (X[2].y - X[3].y)),
+                     0.25 * ((X[0].z - X[1].z) + (X[2].z - X[3].z))};
+      const double s3 = fabs(d3.x) + fabs(d3.y) + fabs(d3.z);
+      const double s12 = fabs(g1.x) + fabs(g1.y) + fabs(g1.z) + fabs(g2.x) + fabs(g2.y) + fabs(g2.z);
+      flat_jac = s3 <= 1e-15 * s12;
+    }
+    if (flat_jac) {
+      if constexpr (NS == 4) {
+        const double J0 = ln;   // |g1 x g2| at the centre = the constant Jacobian
+        const double m4 = J0 * (4.0 / 9.0), m2 = J0 * (2.0 / 9.0), m1 = J0 * (1.0 / 9.0);
+        for (int a = 0; a < 4; ++a) {
+          Dh[a] = J0;
+          for (int b = 0; b < 4; ++b) {
+            const int dd = (a - b + 4) % 4;
+            Me[a][b] = dd == 0 ? m4 : (dd == 2 ? m1 : m2);
+          }
+        }
+      } else {
+        const double J0 = ln;   // twice the triangle area
+        for (int a = 0; a < 3; ++a) {
+          Dh[a] = J0 * (1.0 / 6.0);
+          for (int b = 0; b < 3; ++b) Me[a][b] = J0 * (a == b ? 1.0 / 12.0 : 1.0 / 24.0);
+        }
+      }
+    } else {
+      constexpr int nq = NS == 4 ? 9 : 7;
+      for (int q = 0; q < nq; ++q) {
+        double xi, eta, w;
+        elem_point<NS>(q, xi, eta, w);
+        double N[4];
+        shape_fn<NS>(xi, eta, N);
+        const double wj = w * surface_jac<NS>(X, xi, eta);
+        for (int a = 0; a < NS; ++a) {
+          const double wn = wj * N[a];
+          Dh[a] += wn;
+          for (int b = 0; b < NS; ++b) Me[a][b] += wn * N[b];
+        }
       }
     }
+    // ---- LM coefficients: standard A = I; dual A = Dh Me^-1 (Me A^T = diag(Dh))
+    double A[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) A[a][b] = a == b ? 1.0 : 0.0;
     if (rp.lm == 1 && !degenerate) {
-      // solve Me X = diag(Dh) by Gauss-Jordan with partial pivoting; A = X^T
-      double B[4][4];
+      double K[4][4], B[4][4];
       for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) B[a][b] = (a == b && a < NS) ? Dh[a] : 0.0;
-      for (int c = 0; c < NS; ++c) {
+        for (int b = 0; b < 4; ++b) {
+          K[a][b] = Me[a][b];
+          B[a][b] = (a == b && a < NS) ? Dh[a] : 0.0;
+        }
+      for (int c = 0; c < NS; ++c) {   // Gauss-Jordan with partial pivoting
         int piv = c;
         for (int rr = c + 1; rr < NS; ++rr)
-          if (fabs(Me[rr][c]) > fabs(Me[piv][c])) piv = rr;
+          if (fabs(K[rr][c]) > fabs(K[piv][c])) piv = rr;
         if (piv != c)
           for (int k = 0; k < 4; ++k) {
-            double t = Me[c][k]; Me[c][k] = Me[piv][k]; Me[piv][k] = t;
+            double t = K[c][k]; K[c][k] = K[piv][k]; K[piv][k] = t;
             t = B[c][k]; B[c][k] = B[piv][k]; B[piv][k] = t;
           }
-        const double inv = 1.0 / Me[c][c];
+        const double inv = 1.0 / K[c][c];
+        for (int k = 0; k < 4; ++k) { K[c][k] *= inv; B[c][k] *= inv; }
         for (int rr = 0; rr < NS; ++rr) {
           if (rr == c) continue;
-          const double f = Me[rr][c] * inv;
+          const double f = K[rr][c];
           for (int k = 0; k < 4; ++k) {
-            Me[rr][k] -= f * Me[c][k];
+            K[rr][k] -= f * K[c][k];
             B[rr][k] -= f * B[c][k];
           }
         }
       }
       for (int a = 0; a < NS; ++a)
-        for (int b = 0; b < NS; ++b) A[a][b] = B[b][a] / Me[b][b];
+        for (int b = 0; b < NS; ++b) A[a][b] = B[b][a];
     }
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) r[SR_A + 4 * a + b] = A[a][b];
-    // ---- element-domain D: De = sum_q w J Phi_a N_b = A Me  (Me rebuilt)
+    // ---- element-domain D: De = sum_q w J Phi_a N_b = A Me
     double* d = De + 16 * e;
-    double Mq[4][4];
     for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) Mq[a][b] = 0.0;
-    for (int q = 0; q < nq; ++q) {
-      double xi, eta, w;
-      elem_point<NS>(q, xi, eta, w);
-      double N[4];
-      shape_fn<NS>(xi, eta, N);
-      const double wj = w * surface_jac<NS>(X, xi, eta);
-      for (int a = 0; a < NS; ++a) {
-        double phi = 0.0;
-        for (int c = 0; c < NS; ++c) phi += A[a][c] * N[c];
-        for (int b = 0; b < NS; ++b) Mq[a][b] += wj * phi * N[b];
+      for (int b = 0; b < 4; ++b) {
+        double v = 0.0;
+        for (int c = 0; c < NS; ++c) v += A[a][c] * Me[c][b];
+        d[4 * a + b] = (a < NS && b < NS) ? v : 0.0;
       }
-    }
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) d[4 * a + b] = Mq[a][b];
     // ---- search box (delta-inflated) and diameter
     double lo[3] = {X[0].x, X[0].y, X[0].z}, hi[3] = {X[0].x, X[0].y, X[0].z};
     for (int a = 1; a < NS; ++a) {

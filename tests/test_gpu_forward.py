@@ -284,3 +284,17 @@ def test_launch_variants_agree(mt, orc, variant, rounds):
             blocks_parity(Db, ref.Db)
         csr_parity(m.scipy(mt.MATRIX_M), ref.M)
         assert m.stats()["n_newton_fail"] == 0
+
+
+def test_autotune_keeps_results(mt, orc):
+    itf = inputs.mixed_tri(36, 45, name="at")
+    m = mt.Mortar(lm=0, delta=itf.delta)
+    m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+    lam = np.random.default_rng(3).uniform(-1, 1, itf.xs.shape)
+    pick = m.autotune(lam)
+    assert pick["variant"] in (0, 1) and pick["rounds"] in (0, 1, 2, 4) and pick["ms"] > 0
+    m.run_graph(lam)
+    m.run_graph(lam)
+    ref = orc.evaluate(itf)
+    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
