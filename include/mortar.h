@@ -77,6 +77,8 @@ typedef struct mortar_options {
   double clip_tol_rel;      /* inside tolerance eps_in = clip_tol_rel * h_s^2 (1e-12) */
   double merge_tol_rel;     /* vertex merge distance = merge_tol_rel * h_s (1e-10) */
   double area_tol_rel;      /* discard polygons below area_tol_rel * slave area (1e-14) */
+  double bin_margin;        /* added to the minimal bin size: the 2 dt |mean interface velocity| term
+                               of Sec. 3.3 for moving interfaces (0); bins are rebuilt every run */
 } mortar_options;
 
 typedef struct mortar_stats {

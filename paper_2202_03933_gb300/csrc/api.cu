@@ -401,6 +401,7 @@ int mortar_default_options(mortar_options* o) {
   o->clip_tol_rel = 1e-12;
   o->merge_tol_rel = 1e-10;
   o->area_tol_rel = 1e-14;
+  o->bin_margin = 0.0;
   return MORTAR_OK;
 }
 
@@ -410,7 +411,7 @@ int mortar_create(mortar_ctx** out, const mortar_options* o, void* stream) {
   mortar_ctx* c = new mortar_ctx();
   if (o) c->opt = *o; else mortar_default_options(&c->opt);
   if ((c->opt.lm != 0 && c->opt.lm != 1) || (c->opt.d_domain != 0 && c->opt.d_domain != 1) ||
-      c->opt.newton_max_iter < 1 || !(c->opt.search_inflation >= 0.0)) {
+      c->opt.newton_max_iter < 1 || !(c->opt.search_inflation >= 0.0) || !(c->opt.bin_margin >= 0.0)) {
     delete c;
     return MORTAR_ERR_INVALID_ARG;
   }

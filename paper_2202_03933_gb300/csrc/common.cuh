@@ -27,6 +27,7 @@ struct RunParams {
   double merge_tol_rel;
   double area_tol_rel;
   double delta;
+  double bin_margin;
 };
 
 // Slave element record (FP64 words).  Written once per evaluation by the

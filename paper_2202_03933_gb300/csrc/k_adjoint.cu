@@ -1105,13 +1105,50 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
   for (int a = 0; a < 4; ++a) Xb[a] = v3(0, 0, 0);
   double Je = 0.0;
   constexpr int nq = NS == 4 ? 9 : 7;
-  // element integrals Me, Dh (recomputed)
+  // element integrals Me, Dh (recomputed).  A flat element (negligible
+  // bilinear term: parallelograms, every tri3) has constant tangents g1, g2
+  // and Jacobian J0, so Me = J0 Mref and Dh = J0 dref, and in the reverse
+  // sweep below the Jacobian's gradient directions are the same at every
+  // quadrature point.
   double Me[4][4], Dh[4];
   for (int a = 0; a < 4; ++a) {
     Dh[a] = 0.0;
     for (int b = 0; b < 4; ++b) Me[a][b] = 0.0;
   }
-  for (int q = 0; q < nq; ++q) {
+  V3 g1c, g2c;
+  bool flat;
+  if constexpr (NS == 4) {
+    g1c = 0.25 * ((X[1] - X[0]) + (X[2] - X[3]));
+    g2c = 0.25 * ((X[2] - X[1]) + (X[3] - X[0]));
+    const V3 d3 = 0.25 * ((X[0] - X[1]) + (X[2] - X[3]));
+    const double s3 = fabs(d3.x) + fabs(d3.y) + fabs(d3.z);
+    const double s12 = fabs(g1c.x) + fabs(g1c.y) + fabs(g1c.z) + fabs(g2c.x) + fabs(g2c.y) + fabs(g2c.z);
+    flat = s3 <= 1e-15 * s12;
+  } else {
+    g1c = X[1] - X[0];
+    g2c = X[2] - X[0];
+    flat = true;
+  }
+  const V3 nc = cross(g1c, g2c);
+  const double J0 = sqrt(dot(nc, nc));
+  if (flat) {
+    if constexpr (NS == 4) {
+      const double m4 = J0 * (4.0 / 9.0), m2 = J0 * (2.0 / 9.0), m1 = J0 * (1.0 / 9.0);
+      for (int a = 0; a < 4; ++a) {
+        Dh[a] = J0;
+        for (int b = 0; b < 4; ++b) {
+          const int dd = (a - b + 4) % 4;
+          Me[a][b] = dd == 0 ? m4 : (dd == 2 ? m1 : m2);
+        }
+      }
+    } else {
+      for (int a = 0; a < 3; ++a) {
+        Dh[a] = J0 * (1.0 / 6.0);
+        for (int b = 0; b < 3; ++b) Me[a][b] = J0 * (a == b ? 1.0 / 12.0 : 1.0 / 24.0);
+      }
+    }
+  }
+  for (int q = 0; q < nq && !flat; ++q) {
     double xi, eta, w;
     elem_point_a<NS>(q, xi, eta, w);
     double N[4], dN[4][2];
@@ -1169,6 +1206,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
       }
   }
   // element integrals -> nodes
+  double S1[4] = {0, 0, 0, 0}, S2[4] = {0, 0, 0, 0};   // flat: sum_q jb_q dN_a/dxi, dN_a/deta
   for (int q = 0; q < nq; ++q) {
     double xi, eta, w;
     elem_point_a<NS>(q, xi, eta, w);
@@ -1177,8 +1215,14 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
     shape_grad<NS>(xi, eta, dN);
     double jb = 0.0;
     for (int a = 0; a < NS; ++a) {
-      jb += Dhb[a] * w * N[a];
-      for (int b = 0; b < NS; ++b) jb += Meb[a][b] * w * N[a] * N[b];
+      double v = Dhb[a];
+      for (int b = 0; b < NS; ++b) v = fma(Meb[a][b], N[b], v);
+      jb = fma(v, N[a], jb);
+    }
+    jb *= w;
+    if (flat) {
+      for (int a = 0; a < NS; ++a) { S1[a] = fma(jb, dN[a][0], S1[a]); S2[a] = fma(jb, dN[a][1], S2[a]); }
+      continue;
     }
     if (jb == 0.0) continue;
     V3 g1 = v3(0, 0, 0), g2 = v3(0, 0, 0);
@@ -1188,6 +1232,11 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
     const V3 nb = (jb / J) * nq3;
     const V3 g1b = cross(g2, nb), g2b = cross(nb, g1);
     for (int a = 0; a < NS; ++a) Xb[a] = Xb[a] + dN[a][0] * g1b + dN[a][1] * g2b;
+  }
+  if (flat && J0 > 0.0) {   // d J / d g1 = g2 x n / J, d J / d g2 = n / J x g1 (same at every point)
+    const V3 nu = (1.0 / J0) * nc;
+    const V3 d1 = cross(g2c, nu), d2 = cross(nu, g1c);
+    for (int a = 0; a < NS; ++a) Xb[a] = Xb[a] + S1[a] * d1 + S2[a] * d2;
   }
   for (int a = 0; a < NS; ++a) {
     out[3 * a] = Xb[a].x;

@@ -7,7 +7,8 @@
 //    block; inflated bounding box and diameter for the search.
 //  * Master elements: inflated bounding box and diameter.
 //  * Search grid per interface (Sec. 3.3): bounding box of the interface,
-//    minimal bin size beta_min = (1 + 1e-9) max diameter + 2 delta, box
+//    minimal bin size beta_min = (1 + 1e-9) max diameter + 2 delta (+ the
+//    velocity margin of moving interfaces), box
 //    expanded by beta_min, n_d = max(1, floor(L_d / beta_min)) bins per
 //    direction (bins grow by 1.25x while an interface would exceed its bin
 //    capacity).
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(256) k_chunk_reduce(const Chunk* __restrict__ 
 __global__ void __launch_bounds__(256) k_grid_params(const int32_t* __restrict__ chunk_ptr,
                                                      const double* __restrict__ red,
                                                      const int64_t* __restrict__ bin_cap_off, double delta,
-                                                     GridParams* __restrict__ grid) {
+                                                     double margin, GridParams* __restrict__ grid) {
   const int i = blockIdx.x;
   const int32_t c0 = chunk_ptr[i], c1 = chunk_ptr[i + 1];
   double v[7] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX, 0.0};
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(256) k_grid_params(const int32_t* __restrict__
   if (c1 <= c0 || !(sh[0][0] <= sh[0][3])) {   // empty interface
     for (int k = 0; k < 3; ++k) { g.org[k] = 0.0; g.beta[k] = 1.0; g.nb[k] = 1; }
   } else {
-    double beta_min = (1.0 + 1e-9) * sh[0][6] + 2.0 * delta;
+    double beta_min = (1.0 + 1e-9) * sh[0][6] + 2.0 * delta + margin;
     if (!(beta_min > 0.0)) beta_min = 1.0;
     for (int attempt = 0; attempt < 200; ++attempt) {
       int64_t tot = 1;
@@ -433,6 +434,7 @@ RunParams run_params(const mortar_ctx* c) {
   rp.merge_tol_rel = c->opt.merge_tol_rel;
   rp.area_tol_rel = c->opt.area_tol_rel;
   rp.delta = c->opt.search_inflation;
+  rp.bin_margin = c->opt.bin_margin;
   return rp;
 }
 
@@ -477,7 +479,7 @@ void launch_grid_params(mortar_ctx* c, const RunParams& rp) {
     k_chunk_reduce<<<(unsigned)c->n_chunks, 256, 0, c->stream>>>(c->chunks.as<Chunk>(), c->box_s.as<double>(),
                                                                  c->box_m.as<double>(), c->chunk_red.as<double>());
   k_grid_params<<<(unsigned)c->n_if, 256, 0, c->stream>>>(c->chunk_ptr.as<int32_t>(), c->chunk_red.as<double>(),
-                                                          c->bin_cap_off.as<int64_t>(), rp.delta,
+                                                          c->bin_cap_off.as<int64_t>(), rp.delta, rp.bin_margin,
                                                           c->grid.as<GridParams>());
   k_bin_offsets<<<1, 1024, 0, c->stream>>>(c->grid.as<GridParams>(), c->n_if, c->bin_cap,
                                            c->dstat.as<DevStatus>());

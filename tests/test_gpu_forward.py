@@ -298,3 +298,31 @@ def test_autotune_keeps_results(mt, orc):
     ref = orc.evaluate(itf)
     csr_parity(m.scipy(mt.MATRIX_M), ref.M)
     csr_parity(m.scipy(mt.MATRIX_D), ref.D)
+
+
+def test_moving_interface_reevaluation(mt, orc):
+    """Repeated evaluation of one context while the master slides and turns
+    (coordinates updated on the device between graph replays, bins rebuilt
+    every step, bin size with the velocity margin of Sec. 3.3)."""
+    import math
+    import torch
+    base = inputs.planar_noisy(24, 21, 1, 48, "mov")
+    xm0 = base.xm.copy()
+    m = mt.Mortar(lm=1, delta=1e-9, bin_margin=2 * 0.01)
+    m.set_interface(torch.from_numpy(base.xs).cuda(), torch.from_numpy(base.conn_s).cuda(),
+                    torch.from_numpy(xm0).cuda(), torch.from_numpy(base.conn_m).cuda())
+    lam = np.random.default_rng(6).uniform(-1, 1, base.xs.shape)
+    for step in range(4):
+        a = 0.02 * step
+        xm = xm0.copy()
+        u, v = xm[:, 0] - 0.5, xm[:, 1] - 0.5
+        xm[:, 0] = 0.5 + math.cos(a) * u - math.sin(a) * v + 0.01 * step
+        xm[:, 1] = 0.5 + math.sin(a) * u + math.cos(a) * v
+        m.set_coordinates(None, torch.from_numpy(xm).cuda())
+        m.run_graph(torch.from_numpy(lam).cuda())
+        itf = inputs.Interface("mov", base.xs, base.conn_s, 4, xm, base.conn_m, 4, lm=1, delta=1e-9)
+        ref = orc.evaluate(itf)
+        s, mm = m.pairs()
+        assert np.array_equal(s, ref.s) and np.array_equal(mm, ref.m), step
+        csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+        csr_parity(m.scipy(mt.MATRIX_D), ref.D)
