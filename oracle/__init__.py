@@ -19,6 +19,9 @@ Parity status per function (how each is pinned is in ``tests/test_oracle_*.py``)
       form beyond those invariants
   weighted_gap_grad                  -- pinned (finite differences, Euler
       homogeneity, translation invariance)
+  tangent                            -- pinned (finite differences, Euler
+      homogeneity, translation and rotation invariance, a closed-form
+      overlap-area derivative, consistency with weighted_gap_grad)
 """
 from __future__ import annotations
 
@@ -92,6 +95,9 @@ def _load():
             lib.oracle_weighted_gap_grad.restype = ctypes.c_int
             lib.oracle_weighted_gap_grad.argtypes = [P, i64, P, i64, i32, P, i64, P, i32,
                                                      ctypes.POINTER(Opts), P, P, i64, P, P, P, P]
+            lib.oracle_tangent_blocks.restype = ctypes.c_int
+            lib.oracle_tangent_blocks.argtypes = [P, P, i64, i32, P, P, i32, ctypes.POINTER(Opts),
+                                                  P, P, i64, P, P, P, P, P]
             lib.oracle_slave_frames.restype = ctypes.c_int
             lib.oracle_slave_frames.argtypes = [P, P, i64, i32, P]
             lib.oracle_tri_rule.restype = ctypes.c_int
@@ -294,6 +300,110 @@ def weighted_gap_grad(itf, lam, s, m, opts: Opts | None = None):
                                  _p(s), _p(m), s.shape[0], _p(lam), ctypes.byref(J),
                                  _p(gs), _p(gm))
     return J.value, gs, gm
+
+
+def tangent_blocks(itf, s, m, ys, ym, opts: Opts | None = None):
+    """Dense per-source blocks of K = d/dX[(D (x) I3) ys - (M (x) I3) ym].
+
+    Returns kp (P,4,3,8,3): pair rows (local slave node a, component c) by
+    columns (the pair's 4 slave then 4 master nodes, direction d); ke
+    (Es,4,3,4,3): element-domain D rows by the element's slave nodes (zero in
+    segment mode); flags (P,) of the non-empty pairs."""
+    lib = _load()
+    o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
+    xs, cs, xm, cm = _mesh_arrays(itf)
+    ys = np.ascontiguousarray(ys, np.float64)
+    ym = np.ascontiguousarray(ym, np.float64)
+    s = np.ascontiguousarray(s, np.int32)
+    m = np.ascontiguousarray(m, np.int32)
+    P, E = s.shape[0], cs.shape[0]
+    kp = np.zeros((max(P, 1), 288))
+    ke = np.zeros((max(E, 1), 144))
+    fl = np.zeros(max(P, 1), np.uint8)
+    lib.oracle_tangent_blocks(_p(xs), _p(cs), E, cs.shape[1], _p(xm), _p(cm), cm.shape[1],
+                              ctypes.byref(o), _p(s), _p(m), P, _p(ys), _p(ym), _p(kp),
+                              _p(ke), _p(fl))
+    return (kp[:P].reshape(P, 4, 3, 8, 3), ke[:E].reshape(E, 4, 3, 4, 3),
+            fl[:P].astype(bool))
+
+
+def _bsr_from_blocks(rows, cols, blocks, nrows):
+    """Sum 3x3 blocks with equal (row, col) in order of appearance."""
+    rows = np.asarray(rows, np.int64)
+    cols = np.asarray(cols, np.int64)
+    blocks = np.asarray(blocks, np.float64).reshape(-1, 3, 3)
+    rowptr = np.zeros(nrows + 1, np.int64)
+    if rows.size == 0:
+        return rowptr, np.zeros(0, np.int32), np.zeros((0, 3, 3))
+    order = np.lexsort((cols, rows))          # stable: ties keep appearance order
+    r, c, b = rows[order], cols[order], blocks[order]
+    first = np.ones(r.size, bool)
+    first[1:] = (r[1:] != r[:-1]) | (c[1:] != c[:-1])
+    starts = np.flatnonzero(first)
+    seg = np.cumsum(first) - 1
+    sums = np.zeros((starts.size, 3, 3))
+    np.add.at(sums, seg, b)
+    np.add.at(rowptr, r[starts] + 1, 1)
+    return np.cumsum(rowptr), c[starts].astype(np.int32), sums
+
+
+def tangent(itf, s, m, ys, ym, opts: Opts | None = None, add_direct: bool = False):
+    """Block-sparse K = d/dX[(D (x) I3) ys - (M (x) I3) ym] (3x3 blocks).
+
+    Block rows are slave nodes; block columns are slave nodes [0, Ns) then
+    master nodes [Ns, Ns + Nm); block (j, k)[c][d] = d g_j[c] / d X_k[d].  A
+    block is structural iff a non-empty pair, or (element-domain D) a slave
+    element, has both nodes.  ``add_direct`` adds [D (x) I3 | -M (x) I3],
+    which with ys = Xs, ym = Xm makes K the Jacobian of the weighted gap
+    vector g = (D (x) I3) Xs - (M (x) I3) Xm.  Sums run over pairs in the
+    given order, then elements, then the direct terms.
+    Returns (rowptr int64, colidx int32, vals (nnzb,3,3))."""
+    o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
+    kp, ke, fl = tangent_blocks(itf, s, m, ys, ym, o)
+    cs = np.asarray(itf.conn_s)
+    cm = np.asarray(itf.conn_m)
+    ns, nm = cs.shape[1], cm.shape[1]
+    Ns = itf.n_slave_nodes
+    keep = np.flatnonzero(fl)
+    sk, mk = np.asarray(s)[keep], np.asarray(m)[keep]
+    nodes = np.concatenate([cs[sk], Ns + cm[mk]], axis=1)           # (K, ns + nm)
+    loc = np.concatenate([np.arange(ns), 4 + np.arange(nm)])
+    blk = kp[keep][:, :ns][:, :, :, loc, :]                           # (K, ns, 3, ns+nm, 3)
+    rows = [np.repeat(cs[sk][:, :, None], ns + nm, axis=2).ravel()]
+    cols = [np.repeat(nodes[:, None, :], ns, axis=1).ravel()]
+    blocks = [blk.transpose(0, 1, 3, 2, 4).reshape(-1, 3, 3)]
+    if o.d_domain == 0:
+        rows.append(np.repeat(cs[:, :, None], ns, axis=2).ravel())
+        cols.append(np.repeat(cs[:, None, :], ns, axis=1).ravel())
+        blocks.append(ke[:, :ns, :, :ns, :].transpose(0, 1, 3, 2, 4).reshape(-1, 3, 3))
+    if add_direct:
+        A, De = element_blocks(itf, o.lm)
+        Mb, Db, _, _ = pair_blocks(itf, s, m, o)
+        eye = np.eye(3)
+        rows.append(np.repeat(cs[sk][:, :, None], nm, axis=2).ravel())
+        cols.append(np.repeat(Ns + cm[mk][:, None, :], ns, axis=1).ravel())
+        blocks.append((-Mb[keep][:, :ns, :nm, None, None] * eye).reshape(-1, 3, 3))
+        if o.d_domain == 1:
+            rows.append(np.repeat(cs[sk][:, :, None], ns, axis=2).ravel())
+            cols.append(np.repeat(cs[sk][:, None, :], ns, axis=1).ravel())
+            blocks.append((Db[keep][:, :ns, :ns, None, None] * eye).reshape(-1, 3, 3))
+        else:
+            rows.append(np.repeat(cs[:, :, None], ns, axis=2).ravel())
+            cols.append(np.repeat(cs[:, None, :], ns, axis=1).ravel())
+            blocks.append((De[:, :ns, :ns, None, None] * eye).reshape(-1, 3, 3))
+    return _bsr_from_blocks(np.concatenate(rows), np.concatenate(cols),
+                            np.concatenate(blocks), Ns)
+
+
+def bsr_dense(rowptr, colidx, vals, nrows, ncols):
+    """Dense (3 nrows, 3 ncols) matrix of a 3x3-block BSR triple."""
+    out = np.zeros((3 * nrows, 3 * ncols))
+    rowptr = np.asarray(rowptr)
+    for j in range(nrows):
+        for q in range(rowptr[j], rowptr[j + 1]):
+            k = int(colidx[q])
+            out[3 * j:3 * j + 3, 3 * k:3 * k + 3] += vals[q]
+    return out
 
 
 def tri_rule(which: int = 7) -> np.ndarray:

@@ -921,6 +921,97 @@ int oracle_weighted_gap_grad(const double* xs, int64_t Ns, const int32_t* cs, in
   return 0;
 }
 
+// Linearisation of the mortar coupling terms (Sec. 1: every nonlinear
+// iteration needs the consistent derivatives of D and M), contracted with
+// nodal fields ys (Ns x 3) and ym (Nm x 3) that are held fixed:
+//   K = d/dX [ (D (x) I3) ys - (M (x) I3) ym ].
+// Returned as the dense blocks of its sources, by forward-mode dual numbers
+// (Dual<24> over the 8 nodes of a pair, Dual<12> over the nodes of a slave
+// element), so that the LM coefficients A (dual basis), the auxiliary plane,
+// the clip polygon and the back-projections all carry derivatives:
+//   kp[p][a][c][k][d] = [segment D] sum_b dD_p[a][b]/dX_kd ys_b[c]
+//                       - sum_l dM_p[a][l]/dX_kd ym_l[c]
+//     (a: local slave node = row, c: component, k < 4: slave node k,
+//      k >= 4: master node k - 4, d: coordinate direction);
+//   ke[e][a][c][k][d] = [element D] sum_b dDe[a][b]/dX_kd ys_b[c]  (k < 4).
+// flag[p] = 1 for pairs with a non-empty clip polygon (the structural ones).
+int oracle_tangent_blocks(const double* xs, const int32_t* cs, int64_t Es, int32_t nen_s,
+                          const double* xm, const int32_t* cm, int32_t nen_m, const Opts* o,
+                          const int32_t* ps, const int32_t* pm, int64_t P, const double* ys,
+                          const double* ym, double* kp, double* ke, uint8_t* flag) {
+  typedef Dual<24> D24;
+  const int nt = o->n_threads > 0 ? o->n_threads : 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+#endif
+  for (int64_t p = 0; p < P; ++p) {
+    Stats st;
+    const int32_t s = ps[p], m = pm[p];
+    double* out = kp + 288 * p;
+    for (int k = 0; k < 288; ++k) out[k] = 0.0;
+    SlaveData<D24> S;
+    S.nen = nen_s;
+    V3<D24> Xm[4];
+    for (int a = 0; a < 4; ++a) S.X[a] = {D24(0.0), D24(0.0), D24(0.0)};
+    for (int l = 0; l < 4; ++l) Xm[l] = {D24(0.0), D24(0.0), D24(0.0)};
+    for (int a = 0; a < nen_s; ++a) {
+      const double* q = xs + 3 * (int64_t)cs[(int64_t)nen_s * s + a];
+      S.X[a] = {D24::seed(q[0], 3 * a), D24::seed(q[1], 3 * a + 1), D24::seed(q[2], 3 * a + 2)};
+    }
+    for (int l = 0; l < nen_m; ++l) {
+      const double* q = xm + 3 * (int64_t)cm[(int64_t)nen_m * m + l];
+      Xm[l] = {D24::seed(q[0], 12 + 3 * l), D24::seed(q[1], 12 + 3 * l + 1), D24::seed(q[2], 12 + 3 * l + 2)};
+    }
+    slave_frame<D24>(S);
+    lm_coefficients<D24>(S, o->lm);
+    PairOut<D24> r;
+    integrate_pair<D24>(S, Xm, nen_m, *o, r, st);
+    flag[p] = r.nonempty ? 1 : 0;
+    if (!r.nonempty) continue;
+    for (int a = 0; a < nen_s; ++a)
+      for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 24; ++k) {
+          double v = 0.0;
+          if (o->d_domain == 1)
+            for (int b = 0; b < nen_s; ++b)
+              v += r.D[a][b].d[k] * ys[3 * (int64_t)cs[(int64_t)nen_s * s + b] + c];
+          for (int l = 0; l < nen_m; ++l)
+            v -= r.M[a][l].d[k] * ym[3 * (int64_t)cm[(int64_t)nen_m * m + l] + c];
+          out[72 * a + 24 * c + k] = v;
+        }
+  }
+  if (o->d_domain == 0) {
+    typedef Dual<12> D12;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nt)
+#endif
+    for (int64_t e = 0; e < Es; ++e) {
+      double* out = ke + 144 * e;
+      for (int k = 0; k < 144; ++k) out[k] = 0.0;
+      SlaveData<D12> S;
+      S.nen = nen_s;
+      for (int a = 0; a < 4; ++a) S.X[a] = {D12(0.0), D12(0.0), D12(0.0)};
+      for (int a = 0; a < nen_s; ++a) {
+        const double* q = xs + 3 * (int64_t)cs[(int64_t)nen_s * e + a];
+        S.X[a] = {D12::seed(q[0], 3 * a), D12::seed(q[1], 3 * a + 1), D12::seed(q[2], 3 * a + 2)};
+      }
+      slave_frame<D12>(S);
+      lm_coefficients<D12>(S, o->lm);
+      D12 De[4][4];
+      element_D<D12>(S, De);
+      for (int a = 0; a < nen_s; ++a)
+        for (int c = 0; c < 3; ++c)
+          for (int k = 0; k < 12; ++k) {
+            double v = 0.0;
+            for (int b = 0; b < nen_s; ++b)
+              v += De[a][b].d[k] * ys[3 * (int64_t)cs[(int64_t)nen_s * e + b] + c];
+            out[36 * a + 12 * c + k] = v;
+          }
+    }
+  }
+  return 0;
+}
+
 // Slave auxiliary planes (x0, n0, t1, t2) per element: Es x 12.
 int oracle_slave_frames(const double* xs, const int32_t* cs, int64_t Es, int32_t nen_s, double* out) {
   for (int64_t e = 0; e < Es; ++e) {
