@@ -391,6 +391,24 @@ def run_ours(args, world, rank, local):
     except Exception as ex_:   # reported, not fatal
         fwd = {"error": str(ex_)}
 
+    # ---- linearisation of D and M (Jacobian of the weighted gap vector, BSR):
+    #      separate call, not part of the step; device time of its kernels
+    lin = None
+    try:
+        for _ in range(1):
+            m.tangent(xs, xm, add_direct=True, out_device=True)
+        t_l = []
+        for _ in range(min(args.steps, 3)):
+            m.tangent(xs, xm, add_direct=True, out_device=True)
+            t_l.append(m.stats()["ms_tangent"])
+        sl = m.stats()
+        lin = {"ms": round(mean(t_l), 3), "pairs_per_s": world * n_pairs / (mean(t_l) / 1e3),
+               "blocks_3x3": sl["nnzb_K"],
+               "what": "K = d/dX[(D (x) I3) Xs - (M (x) I3) Xm] + [D (x) I3 | -M (x) I3]: pair blocks, "
+                       "element blocks, BSR assembly"}
+    except Exception as ex_:   # reported, not fatal
+        lin = {"error": str(ex_)}
+
     # ---- FP64 probe (measured peak, for context)
     probe = None
     try:
@@ -463,6 +481,7 @@ def run_ours(args, world, rank, local):
                       "adjoint_pairs_separate": round(mean(t_adjp), 4), "graph_total": round(mean(per_step), 4)},
         "autotune": pick,
         "forward_only": fwd,
+        "linearisation": lin,
         "roofline": roof,
         "fp64_probe": probe,
         "e2e": e2e,

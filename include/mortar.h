@@ -107,6 +107,9 @@ typedef struct mortar_stats {
    * (timing on; the measure eta_t of the paper's load-balancing trigger,
    * Sec. 4.3, taken over CTAs instead of processes); 0 if not measured */
   float eta_t;
+  /* linearisation (mortar_tangent): time of its kernels (timing on) and 3x3 blocks */
+  float ms_tangent;
+  int64_t nnzb_K;
 } mortar_stats;
 
 typedef struct mortar_ctx mortar_ctx;
@@ -192,6 +195,35 @@ int mortar_get_pair_blocks(mortar_ctx* ctx, double* M_blocks, double* D_blocks, 
  * of the last evaluation (evaluates first if needed). */
 int mortar_weighted_gap_grad(mortar_ctx* ctx, const double* lambda, double* J,
                              double* grad_xs, double* grad_xm, int32_t on_device);
+
+/* Consistent linearisation of the mortar coupling terms (Sec. 1: every
+ * nonlinear iteration needs the derivatives of D and M with respect to the
+ * nodal coordinates; Eq. DiscreteWeakFormInterfaceFlux defines D and M):
+ *     K = d/dX [ (D (x) I3) ys - (M (x) I3) ym ]
+ * with the nodal fields ys (n_slave_nodes x 3) and ym (n_master_nodes x 3)
+ * held fixed.  With add_direct != 0 the blocks [D (x) I3 | -M (x) I3] are
+ * added, so that ys = X_s, ym = X_m gives the Jacobian of the weighted gap
+ * vector g = (D (x) I3) X_s - (M (x) I3) X_m.  Derivatives pass through the
+ * auxiliary plane, the clip polygon, the back-projections and the dual basis
+ * A = Dh Me^-1 (and the element-domain D).
+ * K is block sparse with 3x3 blocks: block rows = slave nodes, block columns
+ * = slave nodes [0, n_slave_nodes) then master nodes [n_slave_nodes,
+ * n_slave_nodes + n_master_nodes); block (j, k)[c][d] = d g_j[c] / d X_k[d].
+ * A block is structural iff some non-empty pair has slave node j and node k
+ * among its 8 nodes, or (element-domain D) some slave element has both.
+ * Evaluates first if the last evaluation is stale (its status, e.g.
+ * MORTAR_ERR_NEWTON, is returned).  *nnzb (may be NULL) receives the block
+ * count.  Per-pair workspace: 2.3 KB per candidate pair (device). */
+int mortar_tangent(mortar_ctx* ctx, const double* ys, const double* ym, int32_t add_direct, int32_t on_device,
+                   int64_t* nnzb);
+
+/* Copy the linearisation of the last mortar_tangent call: rowptr
+ * (n_slave_nodes + 1, int64), colidx (nnzb, int32, ascending within a row),
+ * vals (nnzb x 9 FP64, each block row-major).  MORTAR_ERR_CAPACITY if
+ * capacity_nnzb < nnzb (nothing written); MORTAR_ERR_STATE before a
+ * mortar_tangent call or after a coordinate change. */
+int mortar_tangent_copy(mortar_ctx* ctx, int64_t* rowptr, int32_t* colidx, double* vals, int64_t capacity_nnzb,
+                        int32_t on_device);
 
 /* Run search + integration + assembly (+ the adjoint if lambda != NULL) as
  * one stream-ordered sequence with device-side sizes, captured once into a

@@ -25,7 +25,7 @@ EXPORTS = (
     "mortar_evaluate", "mortar_csr_size", "mortar_csr_copy", "mortar_get_pair_blocks",
     "mortar_weighted_gap_grad", "mortar_run_graph", "mortar_get_gradient", "mortar_get_stats",
     "mortar_set_timing", "mortar_set_launch", "mortar_status_string", "mortar_probe_dfma",
-    "mortar_integrate_pairs_static", "mortar_autotune",
+    "mortar_integrate_pairs_static", "mortar_autotune", "mortar_tangent", "mortar_tangent_copy",
 )
 
 
@@ -48,7 +48,8 @@ class Stats(ctypes.Structure):
         "n_interfaces", "n_pairs", "n_nonempty", "n_gauss_points", "n_cells", "n_newton_fail",
         "n_xi_out_of_range", "n_clip_overflow", "nnz_D", "nnz_M", "n_bins", "reruns", "graph_kernels", "fused")] + \
         [(n, ctypes.c_float) for n in ("ms_search", "ms_integrate", "ms_assemble", "ms_adjoint",
-                                       "ms_adjoint_pairs", "ms_total", "eta_t")]
+                                       "ms_adjoint_pairs", "ms_total", "eta_t", "ms_tangent")] + \
+        [("nnzb_K", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -90,6 +91,8 @@ def lib():
                 "mortar_set_launch": [P, i32, i32, i32, i32],
                 "mortar_autotune": [P, P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float)],
+                "mortar_tangent": [P, P, P, i32, i32, ctypes.POINTER(i64)],
+                "mortar_tangent_copy": [P, P, P, P, i64, i32],
                 "mortar_status_string": [ctypes.c_int],
                 "mortar_probe_dfma": [P, i32, i32, i64, i32, P],
                 "mortar_integrate_pairs_static": [ctypes.POINTER(Options), P, P, i64, P, i64, i32,

@@ -117,7 +117,7 @@ int alloc_csr_buffers(mortar_ctx* c, int64_t capD, int64_t capM) {
 }
 
 void invalidate(mortar_ctx* c) {
-  c->search_valid = c->eval_valid = c->grad_valid = false;
+  c->search_valid = c->eval_valid = c->grad_valid = c->tan_valid = false;
   if (c->graph_exec) {
     cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
@@ -254,6 +254,7 @@ int run(mortar_ctx* c, const Phases& ph) {
     const int r = finish_run(c, ph);
     if (r == MORTAR_OK) {
       c->search_valid = true;
+      c->tan_valid = false;
       c->eval_valid = ph.integrate && ph.assemble;
       c->grad_valid = ph.adjoint;
       const DevStatus& h = *c->hstat;
@@ -446,7 +447,8 @@ void mortar_destroy(mortar_ctx* c) {
                     &c->Dblk, &c->flag, &c->row_cnt, &c->row_cnt2, &c->rowptr_D, &c->col_D, &c->val_D, &c->rowptr_M,
                     &c->col_M, &c->val_M, &c->scan_tmp, &c->lambda, &c->gs_pair, &c->gm_pair, &c->abar_pair,
                     &c->J_pair, &c->ge_elem, &c->mp_cnt, &c->mp_off, &c->mp_list, &c->grad_s, &c->grad_m,
-                    &c->J_part, &c->dstat, &c->cta_t};
+                    &c->J_part, &c->dstat, &c->cta_t, &c->tan_ys, &c->tan_ym, &c->tan_Kp, &c->tan_Op,
+                    &c->tan_Ke, &c->tan_rowptr, &c->tan_col, &c->tan_val};
   for (DevBuf* b : bufs) buf_free(*b);
   if (c->hstat) cudaFreeHost(c->hstat);
   for (int i = 0; i < 8; ++i)
@@ -474,7 +476,7 @@ int mortar_set_coordinates(mortar_ctx* c, const double* xs, const double* xm, in
   if (!c || !c->have_interface) return MORTAR_ERR_STATE;
   if (xs) MORTAR_TRY(copy_in(c->xs.p, xs, (size_t)c->Ns * 24, on_device, c->stream));
   if (xm) MORTAR_TRY(copy_in(c->xm.p, xm, (size_t)c->Nm * 24, on_device, c->stream));
-  c->search_valid = c->eval_valid = c->grad_valid = false;   // graph stays valid: same buffers
+  c->search_valid = c->eval_valid = c->grad_valid = c->tan_valid = false;   // graph stays valid: same buffers
   return MORTAR_OK;
 }
 
@@ -554,6 +556,71 @@ int mortar_weighted_gap_grad(mortar_ctx* c, const double* lambda, double* J, dou
   if (r != MORTAR_OK && r != MORTAR_ERR_NEWTON && r != MORTAR_ERR_DEGENERATE) return r;
   MORTAR_TRY(mortar_get_gradient(c, J, grad_xs, grad_xm, on_device));
   return r;
+}
+
+int mortar_tangent(mortar_ctx* c, const double* ys, const double* ym, int32_t add_direct, int32_t on_device,
+                   int64_t* nnzb) {
+  if (!c || !ys || !ym) return MORTAR_ERR_INVALID_ARG;
+  if (!c->have_interface) return MORTAR_ERR_STATE;
+  MORTAR_TRY(buf_reserve(c->tan_ys, (size_t)std::max<int64_t>(c->Ns, 1) * 24));
+  MORTAR_TRY(buf_reserve(c->tan_ym, (size_t)std::max<int64_t>(c->Nm, 1) * 24));
+  MORTAR_TRY(copy_in(c->tan_ys.p, ys, (size_t)c->Ns * 24, on_device, c->stream));
+  MORTAR_TRY(copy_in(c->tan_ym.p, ym, (size_t)c->Nm * 24, on_device, c->stream));
+  int r0 = MORTAR_OK;
+  if (!c->eval_valid) {   // forward blocks, flags and pairs of the current coordinates
+    Phases ph;
+    r0 = run(c, ph);
+    if (r0 != MORTAR_OK && r0 != MORTAR_ERR_NEWTON && r0 != MORTAR_ERR_DEGENERATE) return r0;
+  }
+  c->tan_valid = false;
+  // per-pair and per-element blocks, sized from the pair count of the forward run
+  const size_t P = (size_t)std::max<int64_t>(c->n_pairs, 1);
+  MORTAR_TRY(buf_reserve(c->tan_Kp, P * 288 * 8));
+  if (c->opt.lm == MORTAR_LM_DUAL) MORTAR_TRY(buf_reserve(c->tan_Op, P * 12 * 8));
+  if (tangent_needs_elems(c)) MORTAR_TRY(buf_reserve(c->tan_Ke, (size_t)std::max<int64_t>(c->Es, 1) * 144 * 8));
+  MORTAR_TRY(buf_reserve(c->tan_rowptr, (size_t)(c->Ns + 1) * 8));
+  c->tan_pair_cap = c->n_pairs;
+  c->tan_direct = add_direct ? 1 : 0;
+  const RunParams rp = run_params(c);
+  DevStatus* dst = c->dstat.as<DevStatus>();
+  cudaMemsetAsync(&dst->work_ctr3, 0, 3 * sizeof(unsigned long long), c->stream);   // work_ctr3, nnzb_K, over_K
+  if (c->timing) record_event(c->ev[6], c->stream);
+  launch_tangent_blocks(c, rp);
+  launch_tangent_rows(c, rp, 0);
+  cudaMemcpyAsync(c->hstat, c->dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream);
+  MORTAR_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+  MORTAR_TRY(check_cuda());
+  const int64_t need = (int64_t)c->hstat->nnzb_K;
+  if (need > c->tan_nnzb_cap) {
+    const int64_t cap = need + need / 16 + 64;
+    MORTAR_TRY(buf_reserve(c->tan_col, (size_t)cap * 4));
+    MORTAR_TRY(buf_reserve(c->tan_val, (size_t)cap * 72));
+    c->tan_nnzb_cap = cap;
+  }
+  launch_tangent_rows(c, rp, 1);
+  if (c->timing) record_event(c->ev[7], c->stream);
+  cudaMemcpyAsync(c->hstat, c->dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream);
+  MORTAR_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
+  MORTAR_TRY(check_cuda());
+  if (c->hstat->over_K || c->hstat->over_pairs) return MORTAR_ERR_CAPACITY;
+  c->nnzb_K = need;
+  c->stats.nnzb_K = need;
+  c->stats.ms_tangent = 0.0f;
+  if (c->timing) cudaEventElapsedTime(&c->stats.ms_tangent, c->ev[6], c->ev[7]);
+  c->tan_valid = true;
+  if (nnzb) *nnzb = need;
+  return r0;
+}
+
+int mortar_tangent_copy(mortar_ctx* c, int64_t* rowptr, int32_t* colidx, double* vals, int64_t capacity_nnzb,
+                        int32_t on_device) {
+  if (!c) return MORTAR_ERR_INVALID_ARG;
+  if (!c->tan_valid) return MORTAR_ERR_STATE;
+  if (capacity_nnzb < c->nnzb_K) return MORTAR_ERR_CAPACITY;
+  MORTAR_TRY(copy_out(rowptr, c->tan_rowptr.p, (size_t)(c->Ns + 1) * 8, on_device, c->stream));
+  MORTAR_TRY(copy_out(colidx, c->tan_col.p, (size_t)c->nnzb_K * 4, on_device, c->stream));
+  MORTAR_TRY(copy_out(vals, c->tan_val.p, (size_t)c->nnzb_K * 72, on_device, c->stream));
+  return cuda_status(cudaStreamSynchronize(c->stream));
 }
 
 int mortar_get_gradient(mortar_ctx* c, double* J, double* grad_xs, double* grad_xm, int32_t on_device) {

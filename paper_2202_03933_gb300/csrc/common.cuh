@@ -70,6 +70,9 @@ struct DevStatus {
   unsigned long long over_mlist;   // master pair-list buffer too small
   unsigned long long work_ctr;     // work counter of the persistent integration kernel
   unsigned long long work_ctr2;    // work counter of the persistent adjoint kernel
+  unsigned long long work_ctr3;    // work counter of the linearisation pair kernel
+  unsigned long long nnzb_K;       // 3x3 blocks of the linearisation
+  unsigned long long over_K;       // linearisation block buffer too small
   double J;
 };
 

@@ -89,6 +89,15 @@ struct mortar_ctx {
   mortar::DevBuf grad_s, grad_m;            // Ns x 3, Nm x 3
   mortar::DevBuf J_part;                    // block partial sums of J
 
+  // ---- linearisation workspaces
+  mortar::DevBuf tan_ys, tan_ym;            // contracted fields, Ns x 3 and Nm x 3
+  mortar::DevBuf tan_Kp, tan_Op;            // per pair: 288 block entries, 12 (dual LMs)
+  mortar::DevBuf tan_Ke;                    // per slave element: 144 block entries
+  mortar::DevBuf tan_rowptr, tan_col, tan_val;   // BSR of 3x3 blocks
+  int64_t tan_pair_cap = 0, tan_nnzb_cap = 0, nnzb_K = 0;
+  int32_t tan_direct = 0;
+  bool tan_valid = false;
+
   // ---- status / bookkeeping
   mortar::DevBuf dstat;                     // mortar::DevStatus
   mortar::DevStatus* hstat = nullptr;       // pinned host copy
@@ -135,6 +144,11 @@ int prepare_adjoint_buffers(mortar_ctx* c);   // sizes per-pair adjoint buffers 
 bool adjoint_fuses_forward(const mortar_ctx* c);   // the adjoint pair kernel also writes M/D blocks
 void launch_adjoint_pairs(mortar_ctx* c, const RunParams& rp, bool fused);
 void launch_adjoint_rest(mortar_ctx* c, const RunParams& rp);   // element adjoint, gathers, J
+
+// k_tangent.cu
+bool tangent_needs_elems(const mortar_ctx* c);   // dual LMs or element-domain D: per-element blocks
+void launch_tangent_blocks(mortar_ctx* c, const RunParams& rp);   // per-pair and per-element blocks
+void launch_tangent_rows(mortar_ctx* c, const RunParams& rp, int mode);   // 0: count + rowptr, 1: write
 
 RunParams run_params(const mortar_ctx* c);
 

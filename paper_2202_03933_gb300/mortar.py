@@ -175,6 +175,40 @@ class Mortar:
                  gm.ctypes.data_as(ctypes.c_void_p), 0, ok=(0, -2, -3))
         return J.value, gs, gm
 
+    def tangent(self, ys, ym, add_direct: bool = False, out_device: bool = False):
+        """Linearisation K = d/dX[(D (x) I3) ys - (M (x) I3) ym] (ys, ym fixed), plus
+        [D (x) I3 | -M (x) I3] if add_direct, as a BSR triple (rowptr int64,
+        colidx int32, vals (nnzb, 3, 3)): numpy arrays, or CUDA tensors if out_device.
+        Block rows are slave nodes, block columns slave nodes then Ns + master nodes."""
+        ps, ks, ds = _ptr_in(ys, np.float64)
+        pm, km, dm = _ptr_in(ym, np.float64)
+        if ds != dm:
+            raise ValueError("ys and ym must both be CUDA tensors or both host arrays")
+        nb = ctypes.c_int64()
+        call("mortar_tangent", self.h, ps, pm, int(bool(add_direct)), ds, ctypes.byref(nb), ok=(0, -2, -3))
+        n = int(nb.value)
+        if out_device:
+            torch = _torch()
+            rp = torch.empty(self.Ns + 1, dtype=torch.int64, device="cuda")
+            ci = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+            va = torch.empty((max(n, 1), 3, 3), dtype=torch.float64, device="cuda")
+            call("mortar_tangent_copy", self.h, ctypes.c_void_p(rp.data_ptr()), ctypes.c_void_p(ci.data_ptr()),
+                 ctypes.c_void_p(va.data_ptr()), max(n, 1), 1)
+        else:
+            rp = np.empty(self.Ns + 1, np.int64)
+            ci = np.empty(max(n, 1), np.int32)
+            va = np.empty((max(n, 1), 3, 3))
+            call("mortar_tangent_copy", self.h, rp.ctypes.data_as(ctypes.c_void_p),
+                 ci.ctypes.data_as(ctypes.c_void_p), va.ctypes.data_as(ctypes.c_void_p), max(n, 1), 0)
+        return rp, ci[:n], va[:n]
+
+    def torch_bsr_tangent(self, ys, ym, add_direct: bool = False):
+        """The linearisation as a torch sparse BSR tensor (3x3 blocks) on the CUDA device."""
+        torch = _torch()
+        rp, ci, va = self.tangent(ys, ym, add_direct, out_device=True)
+        return torch.sparse_bsr_tensor(rp, ci.to(torch.int64), va,
+                                       size=(3 * self.Ns, 3 * (self.Ns + self.Nm)))
+
     def gradient(self):
         J = ctypes.c_double()
         gs = np.empty((self.Ns, 3))

@@ -52,3 +52,42 @@ def grad_term_scale(orc, itf, lam, s, m, o):
         scale = max(scale, np.abs(gs).max(), np.abs(gm).max())
     o.terms = 3
     return scale
+
+
+def oracle_ulp_sensitivity(orc, itf, s, m, ys, ym, o, trials=4, seed=0):
+    """Largest block-row-relative change of the oracle's own K when every input
+    coordinate is perturbed by one unit in the last place (random signs): the
+    rounding-level conditioning of K at this configuration."""
+    R = orc.tangent(itf, s, m, ys, ym, o)
+    rng = np.random.default_rng(seed)
+    xs0, xm0 = itf.xs.copy(), itf.xm.copy()
+    worst = 0.0
+    try:
+        for _ in range(trials):
+            itf.xs = xs0 * (1 + 2.2e-16 * rng.choice([-1.0, 1.0], xs0.shape))
+            itf.xm = xm0 * (1 + 2.2e-16 * rng.choice([-1.0, 1.0], xm0.shape))
+            worst = max(worst, bsr_parity(orc.tangent(itf, s, m, ys, ym, o), R, tol=np.inf))
+    finally:
+        itf.xs, itf.xm = xs0, xm0
+    return worst
+
+
+def bsr_parity(G, R, tol=1e-12):
+    """Identical block pattern (rowptr, colidx) of two 3x3-block BSR triples;
+    every block row within tol of its own largest reference entry, floored at
+    1 % of the global largest (as csr_parity).  Returns the max row-relative
+    error."""
+    grp, gci, gva = G
+    rrp, rci, rva = R
+    assert np.array_equal(grp, rrp), "block row pointers differ"
+    assert np.array_equal(gci, rci), "block column indices differ"
+    if rva.shape[0] == 0:
+        return 0.0
+    scale = np.abs(rva).max()
+    rows = np.repeat(np.arange(len(rrp) - 1), np.diff(rrp))
+    rmax = np.zeros(len(rrp) - 1)
+    np.maximum.at(rmax, rows, np.abs(rva).reshape(-1, 9).max(axis=1))
+    dif = np.abs(gva - rva).reshape(-1, 9).max(axis=1)
+    rel = dif / np.maximum(rmax[rows], 1e-2 * scale)
+    assert rel.max() <= tol, f"block-row-relative err {rel.max():.3e} (row {rows[rel.argmax()]})"
+    return float(rel.max())
