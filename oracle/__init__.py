@@ -19,6 +19,10 @@ Parity status per function (how each is pinned is in ``tests/test_oracle_*.py``)
       form beyond those invariants
   weighted_gap_grad                  -- pinned (finite differences, Euler
       homogeneity, translation invariance)
+  element_based_blocks / evaluate_element_based -- pinned (exact slave area
+      and linear-field reproduction on full coverage, matching meshes, a
+      brute-force point location over all master elements, convergence to the
+      segment-based result)
   tangent                            -- pinned (finite differences, Euler
       homogeneity, translation and rotation invariance, a closed-form
       overlap-area derivative, consistency with weighted_gap_grad)
@@ -98,6 +102,9 @@ def _load():
             lib.oracle_tangent_blocks.restype = ctypes.c_int
             lib.oracle_tangent_blocks.argtypes = [P, P, i64, i32, P, P, i32, ctypes.POINTER(Opts),
                                                   P, P, i64, P, P, P, P, P]
+            lib.oracle_element_based_blocks.restype = ctypes.c_int
+            lib.oracle_element_based_blocks.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(Opts),
+                                                        P, P, i64, i32, P, P, P]
             lib.oracle_slave_frames.restype = ctypes.c_int
             lib.oracle_slave_frames.argtypes = [P, P, i64, i32, P]
             lib.oracle_tri_rule.restype = ctypes.c_int
@@ -300,6 +307,36 @@ def weighted_gap_grad(itf, lam, s, m, opts: Opts | None = None):
                                  _p(s), _p(m), s.shape[0], _p(lam), ctypes.byref(J),
                                  _p(gs), _p(gm))
     return J.value, gs, gm
+
+
+def element_based_blocks(itf, s, m, n_rule: int = 8, opts: Opts | None = None):
+    """Per-pair M and D blocks (P,4,4) of element-based integration (n x n
+    rule on each slave element, first covering master in pair order) and the
+    flags of pairs that received a quadrature point."""
+    lib = _load()
+    o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
+    xs, cs, xm, cm = _mesh_arrays(itf)
+    s = np.ascontiguousarray(s, np.int32)
+    m = np.ascontiguousarray(m, np.int32)
+    P = s.shape[0]
+    Mb = np.zeros((max(P, 1), 16))
+    Db = np.zeros((max(P, 1), 16))
+    fl = np.zeros(max(P, 1), np.uint8)
+    lib.oracle_element_based_blocks(_p(xs), _p(cs), cs.shape[1], _p(xm), _p(cm), cm.shape[1],
+                                    ctypes.byref(o), _p(s), _p(m), P, int(n_rule), _p(Mb), _p(Db), _p(fl))
+    return Mb[:P].reshape(P, 4, 4), Db[:P].reshape(P, 4, 4), fl[:P].astype(bool)
+
+
+def evaluate_element_based(itf, n_rule: int = 8, opts: Opts | None = None, pairs=None):
+    """Search + element-based integration + assembly (D from the element
+    integrals in element mode, from the covered quadrature points in segment
+    mode).  Returns (D, M, pairs, flags)."""
+    o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
+    s, m = pairs if pairs is not None else search_binned(itf, o.delta)
+    _, De = element_blocks(itf, o.lm)
+    Mb, Db, fl = element_based_blocks(itf, s, m, n_rule, o)
+    D, M = assemble(itf, s, m, Mb, Db, fl, De, o.d_domain)
+    return D, M, (s, m), fl
 
 
 def tangent_blocks(itf, s, m, ys, ym, opts: Opts | None = None):

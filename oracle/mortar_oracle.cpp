@@ -40,6 +40,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <array>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -770,6 +771,108 @@ int oracle_pair_blocks(const double* xs, const int32_t* cs, int32_t nen_s,
     add_stats(stats, st);
   }
   (void)nt;
+  return 0;
+}
+
+// Element-based integration (Sec. 1 and Sec. 2.3: no clipping or
+// triangulation; a higher-order rule on the slave element copes with the
+// kinks of the integrand at master element edges, at lower accuracy than the
+// segment-based rule).  Per slave element: an n x n Gauss-Legendre rule on
+// quad4 (collapsed n x n rule on tri3) in the element's auxiliary plane; each
+// quadrature point x_q is back-projected onto the master elements of the
+// element's candidate pairs in pair order, and the first whose map inverse
+// converges with the point inside (|xi|, |eta| <= 1 + 1e-10 on quad4,
+// barycentric >= -1e-10 on tri3) receives it:
+//   M_p[a][l] += w_q |det J_s(xi_q)| Phi_a(xi_q) N_l(xi_m),
+//   D_p[a][b] += w_q |det J_s(xi_q)| Phi_a(xi_q) N_b(xi_q)   (segment D).
+// Points no master covers contribute nothing.  Pairs must be sorted by slave
+// element.  flag[p] = 1 if pair p received a point.
+int oracle_element_based_blocks(const double* xs, const int32_t* cs, int32_t nen_s,
+                                const double* xm, const int32_t* cm, int32_t nen_m,
+                                const Opts* o, const int32_t* ps, const int32_t* pm, int64_t P,
+                                int32_t n_rule, double* M_out, double* D_out, uint8_t* flag) {
+  std::vector<double> gx, gw;
+  gauss_legendre(n_rule, gx, gw);
+  struct SP { double xi, eta, w; };   // slave parameter points, weights summing to the parameter area
+  std::vector<SP> rule;
+  if (nen_s == 4) {
+    for (int i = 0; i < n_rule; ++i)
+      for (int j = 0; j < n_rule; ++j) rule.push_back({gx[i], gx[j], gw[i] * gw[j]});
+  } else {
+    for (const TriPoint& q : rule_tri_duffy(n_rule)) rule.push_back({q.l1, q.l2, 0.5 * q.w});
+  }
+  const double tol_in = 1e-10;
+  for (int64_t p = 0; p < P; ++p) {
+    flag[p] = 0;
+    for (int k = 0; k < 16; ++k) { M_out[16 * p + k] = 0.0; if (D_out) D_out[16 * p + k] = 0.0; }
+  }
+  // runs of pairs with the same slave element
+  std::vector<int64_t> starts;
+  for (int64_t p = 0; p < P; ++p)
+    if (p == 0 || ps[p] != ps[p - 1]) starts.push_back(p);
+  starts.push_back(P);
+  const int nt = o->n_threads > 0 ? o->n_threads : 1;
+  const int64_t n_runs = (int64_t)starts.size() - 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+#endif
+  for (int64_t r = 0; r < n_runs; ++r) {
+    const int64_t p0 = starts[r], p1 = starts[r + 1];
+    SlaveData<double> S;
+    load_slave<double>(S, xs, cs, nen_s, ps[p0], o->lm);
+    V2<double> pss[4];
+    for (int a = 0; a < nen_s; ++a) {
+      V3<double> d = sub(S.X[a], S.x0);
+      pss[a] = {dot(d, S.t1), dot(d, S.t2)};
+    }
+    // projected master elements of the candidate pairs
+    std::vector<std::array<V2<double>, 4>> pmm(p1 - p0);
+    for (int64_t p = p0; p < p1; ++p)
+      for (int l = 0; l < nen_m; ++l) {
+        const double* q = xm + 3 * (int64_t)cm[(int64_t)nen_m * pm[p] + l];
+        V3<double> d = sub(V3<double>{q[0], q[1], q[2]}, S.x0);
+        pmm[p - p0][l] = {dot(d, S.t1), dot(d, S.t2)};
+      }
+    for (const SP& g : rule) {
+      double N[4], dN[4][2];
+      shape<double>(nen_s, g.xi, g.eta, N);
+      shape_deriv<double>(nen_s, g.xi, g.eta, dN);
+      V2<double> x{0.0, 0.0};
+      double J00 = 0.0, J01 = 0.0, J10 = 0.0, J11 = 0.0;
+      for (int a = 0; a < nen_s; ++a) {
+        x.u = x.u + N[a] * pss[a].u;
+        x.v = x.v + N[a] * pss[a].v;
+        J00 = J00 + dN[a][0] * pss[a].u; J01 = J01 + dN[a][1] * pss[a].u;
+        J10 = J10 + dN[a][0] * pss[a].v; J11 = J11 + dN[a][1] * pss[a].v;
+      }
+      const double W = g.w * std::fabs(J00 * J11 - J01 * J10);
+      double Phi[4];
+      for (int a = 0; a < nen_s; ++a) {
+        Phi[a] = 0.0;
+        for (int c = 0; c < nen_s; ++c) Phi[a] = Phi[a] + S.A[a][c] * N[c];
+      }
+      for (int64_t p = p0; p < p1; ++p) {
+        Stats st;
+        double xim[2];
+        invert_map<double>(nen_m, pmm[p - p0].data(), x, *o, xim, st);
+        if (st.newton_fail) continue;
+        const bool inside = nen_m == 4
+            ? (std::fabs(xim[0]) <= 1.0 + tol_in && std::fabs(xim[1]) <= 1.0 + tol_in)
+            : (xim[0] >= -tol_in && xim[1] >= -tol_in && xim[0] + xim[1] <= 1.0 + tol_in);
+        if (!inside) continue;
+        double Nm[4];
+        shape<double>(nen_m, xim[0], xim[1], Nm);
+        for (int a = 0; a < nen_s; ++a) {
+          const double wp = W * Phi[a];
+          for (int l = 0; l < nen_m; ++l) M_out[16 * p + 4 * a + l] += wp * Nm[l];
+          if (D_out && o->d_domain == 1)
+            for (int b = 0; b < nen_s; ++b) D_out[16 * p + 4 * a + b] += wp * N[b];
+        }
+        flag[p] = 1;
+        break;
+      }
+    }
+  }
   return 0;
 }
 
