@@ -66,6 +66,15 @@ enum { MORTAR_LM_STANDARD = 0, MORTAR_LM_DUAL = 1 };
  * Algorithm 1 (then sum(D) = sum(M)). */
 enum { MORTAR_D_ELEMENT = 0, MORTAR_D_SEGMENT = 1 };
 enum { MORTAR_MATRIX_D = 0, MORTAR_MATRIX_M = 1 };
+/* Integration of M (and of D in segment mode): SEGMENT = Algorithm 1 (clip,
+ * triangulate, 7-point rule per cell; exact up to the Newton tolerance for
+ * affine masters); ELEMENT = element-based integration (Sec. 1, Sec. 2.3): an
+ * n x n Gauss-Legendre rule on each slave element (collapsed n x n on tri3),
+ * every point assigned to the first master element of its candidate pairs
+ * (pair order) that contains its projection, no clipping; cheaper and less
+ * accurate (kinks of the integrand at master edges, coverage ends inside
+ * elements).  The gradient and the linearisation need SEGMENT. */
+enum { MORTAR_INTEGRATE_SEGMENT = 0, MORTAR_INTEGRATE_ELEMENT = 1 };
 
 typedef struct mortar_options {
   int32_t lm;               /* MORTAR_LM_STANDARD or MORTAR_LM_DUAL */
@@ -79,6 +88,8 @@ typedef struct mortar_options {
   double area_tol_rel;      /* discard polygons below area_tol_rel * slave area (1e-14) */
   double bin_margin;        /* added to the minimal bin size: the 2 dt |mean interface velocity| term
                                of Sec. 3.3 for moving interfaces (0); bins are rebuilt every run */
+  int32_t integration;      /* MORTAR_INTEGRATE_SEGMENT (default) or MORTAR_INTEGRATE_ELEMENT */
+  int32_t element_rule_n;   /* points per direction of the element-based rule, 1..16 (8) */
 } mortar_options;
 
 typedef struct mortar_stats {
@@ -268,7 +279,7 @@ int mortar_set_launch(mortar_ctx* ctx, int32_t variant, int32_t block_size, int3
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call shares the array and clears its counters itself; calls
  * whose work overlaps on the GPU (other streams, other threads) race on it.
- * Ids out of range return MORTAR_ERR_INVALID_ARG before any geometry kernel
+ * Always segment-based (o->integration is ignored).  Ids out of range return MORTAR_ERR_INVALID_ARG before any geometry kernel
  * runs (this check synchronises `stream` once); the integration itself is
  * stream-ordered on `stream` when the call returns MORTAR_OK. */
 int mortar_integrate_pairs_static(const mortar_options* o, void* stream,

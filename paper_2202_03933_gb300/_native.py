@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("newton_max_iter", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("search_inflation", ctypes.c_double), ("newton_tol", ctypes.c_double),
                 ("clip_tol_rel", ctypes.c_double), ("merge_tol_rel", ctypes.c_double),
-                ("area_tol_rel", ctypes.c_double), ("bin_margin", ctypes.c_double)]
+                ("area_tol_rel", ctypes.c_double), ("bin_margin", ctypes.c_double),
+                ("integration", ctypes.c_int32), ("element_rule_n", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

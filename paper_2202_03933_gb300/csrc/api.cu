@@ -247,6 +247,7 @@ int finish_run(mortar_ctx* c, const Phases& ph) {
 
 int run(mortar_ctx* c, const Phases& ph) {
   if (!c->have_interface) return MORTAR_ERR_STATE;
+  if (ph.adjoint && c->opt.integration != MORTAR_INTEGRATE_SEGMENT) return MORTAR_ERR_INVALID_ARG;
   c->stats.reruns = 0;
   for (int attempt = 0; attempt < 4; ++attempt) {
     if (ph.adjoint) MORTAR_TRY(prepare_adjoint_buffers(c));
@@ -403,6 +404,8 @@ int mortar_default_options(mortar_options* o) {
   o->merge_tol_rel = 1e-10;
   o->area_tol_rel = 1e-14;
   o->bin_margin = 0.0;
+  o->integration = MORTAR_INTEGRATE_SEGMENT;
+  o->element_rule_n = 8;
   return MORTAR_OK;
 }
 
@@ -412,7 +415,9 @@ int mortar_create(mortar_ctx** out, const mortar_options* o, void* stream) {
   mortar_ctx* c = new mortar_ctx();
   if (o) c->opt = *o; else mortar_default_options(&c->opt);
   if ((c->opt.lm != 0 && c->opt.lm != 1) || (c->opt.d_domain != 0 && c->opt.d_domain != 1) ||
-      c->opt.newton_max_iter < 1 || !(c->opt.search_inflation >= 0.0) || !(c->opt.bin_margin >= 0.0)) {
+      c->opt.newton_max_iter < 1 || !(c->opt.search_inflation >= 0.0) || !(c->opt.bin_margin >= 0.0) ||
+      (c->opt.integration != MORTAR_INTEGRATE_SEGMENT && c->opt.integration != MORTAR_INTEGRATE_ELEMENT) ||
+      c->opt.element_rule_n < 1 || c->opt.element_rule_n > 16) {
     delete c;
     return MORTAR_ERR_INVALID_ARG;
   }
@@ -424,6 +429,8 @@ int mortar_create(mortar_ctx** out, const mortar_options* o, void* stream) {
     else r = cuda_status(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)), c->owns_stream = true;
   }
   if (r == MORTAR_OK) r = buf_reserve(c->dstat, sizeof(DevStatus));
+  if (r == MORTAR_OK && c->opt.integration == MORTAR_INTEGRATE_ELEMENT)
+    r = upload_gauss_legendre(c, c->opt.element_rule_n);
   if (r == MORTAR_OK) r = buf_reserve(c->cta_t, (size_t)c->n_sm * 64 * 2 * sizeof(unsigned long long));
   if (r == MORTAR_OK) r = cuda_status(cudaMallocHost((void**)&c->hstat, sizeof(DevStatus)));
   for (int i = 0; i < 8 && r == MORTAR_OK; ++i) r = cuda_status(cudaEventCreate(&c->ev[i]));
@@ -448,7 +455,7 @@ void mortar_destroy(mortar_ctx* c) {
                     &c->col_M, &c->val_M, &c->scan_tmp, &c->lambda, &c->gs_pair, &c->gm_pair, &c->abar_pair,
                     &c->J_pair, &c->ge_elem, &c->mp_cnt, &c->mp_off, &c->mp_list, &c->grad_s, &c->grad_m,
                     &c->J_part, &c->dstat, &c->cta_t, &c->tan_ys, &c->tan_ym, &c->tan_Kp, &c->tan_Op,
-                    &c->tan_Ke, &c->tan_rowptr, &c->tan_col, &c->tan_val};
+                    &c->tan_Ke, &c->tan_rowptr, &c->tan_col, &c->tan_val, &c->rule_1d};
   for (DevBuf* b : bufs) buf_free(*b);
   if (c->hstat) cudaFreeHost(c->hstat);
   for (int i = 0; i < 8; ++i)
@@ -561,6 +568,7 @@ int mortar_weighted_gap_grad(mortar_ctx* c, const double* lambda, double* J, dou
 int mortar_tangent(mortar_ctx* c, const double* ys, const double* ym, int32_t add_direct, int32_t on_device,
                    int64_t* nnzb) {
   if (!c || !ys || !ym) return MORTAR_ERR_INVALID_ARG;
+  if (c->opt.integration != MORTAR_INTEGRATE_SEGMENT) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
   MORTAR_TRY(buf_reserve(c->tan_ys, (size_t)std::max<int64_t>(c->Ns, 1) * 24));
   MORTAR_TRY(buf_reserve(c->tan_ym, (size_t)std::max<int64_t>(c->Nm, 1) * 24));

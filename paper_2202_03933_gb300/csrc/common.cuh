@@ -28,6 +28,8 @@ struct RunParams {
   double area_tol_rel;
   double delta;
   double bin_margin;
+  int32_t integration;    // 0 segment-based, 1 element-based
+  int32_t rule_n;         // element-based rule: points per direction
 };
 
 // Slave element record (FP64 words).  Written once per evaluation by the

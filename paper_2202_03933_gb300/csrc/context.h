@@ -99,6 +99,8 @@ struct mortar_ctx {
   bool tan_valid = false;
 
   // ---- status / bookkeeping
+  mortar::DevBuf rule_1d;                   // element-based rule: Gauss-Legendre points and weights
+  int32_t rule_1d_n = 0;
   mortar::DevBuf dstat;                     // mortar::DevStatus
   mortar::DevStatus* hstat = nullptr;       // pinned host copy
   bool search_valid = false;
@@ -133,6 +135,10 @@ void launch_candidates(mortar_ctx* c);
 
 // k_integrate.cu
 void launch_integrate(mortar_ctx* c, const RunParams& rp);
+
+// k_elembased.cu
+int upload_gauss_legendre(mortar_ctx* c, int n);   // element-based rule table (host, at create)
+void launch_integrate_element_based(mortar_ctx* c, const RunParams& rp);
 
 // k_assemble.cu
 void launch_topology(mortar_ctx* c);

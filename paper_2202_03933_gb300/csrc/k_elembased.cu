@@ -1,0 +1,226 @@
+// Element-based integration of the mortar matrices (Sec. 1 and Sec. 2.3 set
+// it against the segment-based Algorithm 1: no clipping or triangulation; a
+// higher-order rule on the slave element copes with the kinks of the
+// integrand at master element edges, at lower accuracy).
+//
+// One thread per slave element.  Rule: n x n Gauss-Legendre points on quad4
+// (collapsed n x n points on tri3), mapped into the element's auxiliary plane
+// by the projected slave map, weights w |det J_s|.  The element's candidate
+// pairs are visited in pair order; each takes the points not taken yet whose
+// back-projection onto its projected master element converges inside it
+// (|xi|, |eta| <= 1 + 1e-10 on quad4, barycentric >= -1e-10 on tri3) and adds
+//     M_p[a][l] += W Phi_a(xi_s) N_l(xi_m),   D_p[a][b] += W Phi_a N_b(xi_s) (segment D).
+// Points no master covers contribute nothing.  Ownership is a bit mask per
+// thread.  The blocks keep the layout of the segment-based ones, so the
+// assembly is shared.
+#include <cmath>
+#include <vector>
+
+#include "clip.cuh"
+#include "context.h"
+
+namespace mortar {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kMaxRule = 16;
+constexpr double kInsideTol = 1e-10;
+
+template <int NS, int NM, bool SEG, bool DUAL>
+__global__ void __launch_bounds__(kThreads) k_integrate_elembased(
+    const int64_t* __restrict__ pair_off, const int32_t* __restrict__ pm, const double* __restrict__ srec,
+    const double* __restrict__ xm, const int32_t* __restrict__ conn_m, const double* __restrict__ rule, int n,
+    int64_t Es, double* __restrict__ Mblk, double* __restrict__ Dblk, uint8_t* __restrict__ flag,
+    DevStatus* st) {
+  unsigned long long n_live = 0, n_gp = 0;
+  const bool ok = st->over_pairs == 0 && st->over_bins == 0;
+  const int nq = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ok && e < Es;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p0 = pair_off[e], p1 = pair_off[e + 1];
+    if (p0 == p1) continue;
+    const double* r = srec + (int64_t)SR_STRIDE * e;
+    const bool live = r[SR_EPSIN] >= 0.0;
+    PlaneMap smap;
+    smap.c0u = r[SR_C + 0]; smap.c0v = r[SR_C + 1]; smap.c1u = r[SR_C + 2]; smap.c1v = r[SR_C + 3];
+    smap.c2u = r[SR_C + 4]; smap.c2v = r[SR_C + 5]; smap.c3u = r[SR_C + 6]; smap.c3v = r[SR_C + 7];
+    const double x0x = r[SR_X0], x0y = r[SR_X0 + 1], x0z = r[SR_X0 + 2];
+    const double t1x = r[SR_T1], t1y = r[SR_T1 + 1], t1z = r[SR_T1 + 2];
+    const double t2x = r[SR_T2], t2y = r[SR_T2 + 1], t2z = r[SR_T2 + 2];
+    uint32_t taken[kMaxRule * kMaxRule / 32];
+#pragma unroll
+    for (int k = 0; k < kMaxRule * kMaxRule / 32; ++k) taken[k] = 0u;
+    for (int64_t p = p0; p < p1; ++p) {
+      double M[4][4], D[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { M[a][b] = 0.0; D[a][b] = 0.0; }
+      int got = 0;
+      if (live) {
+        const int32_t m = pm[p];
+        double mu[4], mv[4];
+        double lo_u = 1e300, hi_u = -1e300, lo_v = 1e300, hi_v = -1e300;
+#pragma unroll
+        for (int l = 0; l < NM; ++l) {
+          const int64_t nd = conn_m[(int64_t)NM * m + l];
+          const double dx = xm[3 * nd] - x0x, dy = xm[3 * nd + 1] - x0y, dz = xm[3 * nd + 2] - x0z;
+          mu[l] = dx * t1x + dy * t1y + dz * t1z;
+          mv[l] = dx * t2x + dy * t2y + dz * t2z;
+          lo_u = fmin(lo_u, mu[l]); hi_u = fmax(hi_u, mu[l]);
+          lo_v = fmin(lo_v, mv[l]); hi_v = fmax(hi_v, mv[l]);
+        }
+        // box of the projected master element, widened far beyond the
+        // inside tolerance: a quick reject only
+        const double band = 1e-6 * fmax(hi_u - lo_u, hi_v - lo_v);
+        lo_u -= band; hi_u += band; lo_v -= band; hi_v += band;
+        const PlaneMap mmap = plane_map<NM>(mu, mv);
+        MapInverse mi;
+        mi.setup(mmap, NM == 3 || map_is_affine(mmap));
+        for (int q = 0; q < nq; ++q) {
+          if ((taken[q >> 5] >> (q & 31)) & 1u) continue;
+          const int i = q / n, j = q - (q / n) * n;
+          double xi, eta, wq;
+          if constexpr (NS == 4) {
+            xi = rule[i]; eta = rule[j];
+            wq = rule[n + i] * rule[n + j];
+          } else {
+            const double s = 0.5 * (rule[i] + 1.0), t = 0.5 * (rule[j] + 1.0);
+            xi = s; eta = t * (1.0 - s);
+            wq = 0.25 * rule[n + i] * rule[n + j] * (1.0 - s);
+          }
+          const double xe = xi * eta;
+          const double xu = smap.c0u + smap.c1u * xi + smap.c2u * eta + smap.c3u * xe;
+          const double xv = smap.c0v + smap.c1v * xi + smap.c2v * eta + smap.c3v * xe;
+          if (xu < lo_u || xu > hi_u || xv < lo_v || xv > hi_v) continue;
+          double m1, m2;
+          if (!mi.solve(xu, xv, m1, m2)) continue;
+          const bool inside = NM == 4
+              ? (fabs(m1) <= 1.0 + kInsideTol && fabs(m2) <= 1.0 + kInsideTol)
+              : (m1 >= -kInsideTol && m2 >= -kInsideTol && m1 + m2 <= 1.0 + kInsideTol);
+          if (!inside) continue;
+          taken[q >> 5] |= 1u << (q & 31);
+          ++got;
+          const double j00 = smap.c1u + smap.c3u * eta, j01 = smap.c2u + smap.c3u * xi;
+          const double j10 = smap.c1v + smap.c3v * eta, j11 = smap.c2v + smap.c3v * xi;
+          const double W = wq * fabs(j00 * j11 - j01 * j10);
+          double Ns[4], Nm[4], Phi[4];
+          shape_fn<NS>(xi, eta, Ns);
+          shape_fn<NM>(m1, m2, Nm);
+#pragma unroll
+          for (int a = 0; a < NS; ++a) {
+            double v = 0.0;
+            if (DUAL) {
+#pragma unroll
+              for (int c = 0; c < NS; ++c) v = fma(r[SR_A + 4 * a + c], Ns[c], v);
+            } else {
+              v = Ns[a];
+            }
+            Phi[a] = W * v;
+          }
+#pragma unroll
+          for (int a = 0; a < NS; ++a) {
+#pragma unroll
+            for (int l = 0; l < NM; ++l) M[a][l] = fma(Phi[a], Nm[l], M[a][l]);
+            if (SEG)
+#pragma unroll
+              for (int b = 0; b < NS; ++b) D[a][b] = fma(Phi[a], Ns[b], D[a][b]);
+          }
+        }
+      }
+      double2* mo = reinterpret_cast<double2*>(Mblk + 16 * p);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        mo[2 * a] = make_double2(M[a][0], M[a][1]);
+        mo[2 * a + 1] = make_double2(M[a][2], M[a][3]);
+      }
+      if (SEG) {
+        double2* dout = reinterpret_cast<double2*>(Dblk + 16 * p);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          dout[2 * a] = make_double2(D[a][0], D[a][1]);
+          dout[2 * a + 1] = make_double2(D[a][2], D[a][3]);
+        }
+      }
+      flag[p] = got > 0 ? 1 : 0;
+      n_live += got > 0 ? 1 : 0;
+      n_gp += (unsigned long long)got;
+    }
+  }
+  block_count_add(&st->nonempty, n_live);
+  block_count_add(&st->gauss_points, n_gp);
+}
+
+template <int NS, int NM>
+void launch_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid) {
+  const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
+  auto go = [&](auto kern) {
+    kern<<<grid, kThreads, 0, c->stream>>>(c->pair_off.as<int64_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(),
+                                           c->xm.as<double>(), c->conn_m.as<int32_t>(), c->rule_1d.as<double>(),
+                                           c->rule_1d_n, c->Es, c->Mblk.as<double>(), c->Dblk.as<double>(),
+                                           c->flag.as<uint8_t>(), c->dstat.as<DevStatus>());
+  };
+  if (seg && dual) go(k_integrate_elembased<NS, NM, true, true>);
+  else if (seg) go(k_integrate_elembased<NS, NM, true, false>);
+  else if (dual) go(k_integrate_elembased<NS, NM, false, true>);
+  else go(k_integrate_elembased<NS, NM, false, false>);
+}
+
+}  // namespace
+
+// n-point Gauss-Legendre rule on [-1, 1] (points ascending, then weights):
+// roots of P_n by Newton from cos(pi (i + 3/4) / (n + 1/2)), P_n and P_n' by
+// the three-term recurrence, weights 2 / ((1 - x^2) P_n'(x)^2).
+int upload_gauss_legendre(mortar_ctx* c, int n) {
+  std::vector<double> h(2 * (size_t)n);
+  const double pi = std::acos(-1.0);
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(pi * (n - i - 0.25) / (n + 0.5));   // ascending order
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double pk = 1.0, pk1 = 0.0;   // P_k, P_{k-1}
+      for (int k = 1; k <= n; ++k) {
+        const double pn = ((2.0 * k - 1.0) * x * pk - (k - 1.0) * pk1) / k;
+        pk1 = pk;
+        pk = pn;
+      }
+      dp = n * (x * pk - pk1) / (x * x - 1.0);
+      const double dx = pk / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double pk = 1.0, pk1 = 0.0;
+    for (int k = 1; k <= n; ++k) {
+      const double pn = ((2.0 * k - 1.0) * x * pk - (k - 1.0) * pk1) / k;
+      pk1 = pk;
+      pk = pn;
+    }
+    dp = n * (x * pk - pk1) / (x * x - 1.0);
+    h[i] = x;
+    h[n + i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  int r = buf_reserve(c->rule_1d, h.size() * sizeof(double));
+  if (r != MORTAR_OK) return r;
+  if (cudaMemcpy(c->rule_1d.p, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return MORTAR_ERR_CUDA;
+  }
+  c->rule_1d_n = n;
+  return MORTAR_OK;
+}
+
+void launch_integrate_element_based(mortar_ctx* c, const RunParams& rp) {
+  if (c->Es == 0) return;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate_elembased<4, 4, false, true>, kThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t need = (c->Es + kThreads - 1) / kThreads;
+  const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)c->n_sm * per_sm * 8);
+  if (c->nen_s == 4 && c->nen_m == 4) launch_nsnm<4, 4>(c, rp, grid);
+  else if (c->nen_s == 4 && c->nen_m == 3) launch_nsnm<4, 3>(c, rp, grid);
+  else if (c->nen_s == 3 && c->nen_m == 4) launch_nsnm<3, 4>(c, rp, grid);
+  else launch_nsnm<3, 3>(c, rp, grid);
+}
+
+}  // namespace mortar

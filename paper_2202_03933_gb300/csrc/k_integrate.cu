@@ -451,6 +451,11 @@ void launch_integrate_raw(const IntegrateArgs& a, const RunParams& rp, int nen_s
 }
 
 void launch_integrate(mortar_ctx* c, const RunParams& rp) {
+  if (rp.integration == 1) {
+    c->pair_grid = 0;
+    launch_integrate_element_based(c, rp);
+    return;
+  }
   IntegrateArgs a{c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xm.as<double>(),
                   c->conn_m.as<int32_t>(), c->Mblk.as<double>(), c->Dblk.as<double>(), c->flag.as<uint8_t>(),
                   c->pair_cap, c->dstat.as<DevStatus>(), c->stream};

@@ -435,6 +435,8 @@ RunParams run_params(const mortar_ctx* c) {
   rp.area_tol_rel = c->opt.area_tol_rel;
   rp.delta = c->opt.search_inflation;
   rp.bin_margin = c->opt.bin_margin;
+  rp.integration = c->opt.integration;
+  rp.rule_n = c->opt.element_rule_n;
   return rp;
 }
 

@@ -15,7 +15,7 @@ import ctypes
 import numpy as np
 
 from . import _native
-from ._native import Options, Stats, call, lib
+from ._native import MortarError, Options, Stats, call, lib  # noqa: F401
 
 QUAD4 = 4
 TRI3 = 3
@@ -27,6 +27,9 @@ MATRIX_D = 0
 MATRIX_M = 1
 
 _OK_OR_NEWTON = (0, -3)
+
+
+INTEGRATE_SEGMENT, INTEGRATE_ELEMENT = 0, 1
 
 
 def _torch():
@@ -70,7 +73,10 @@ class Mortar:
         self.opt.lm = lm
         self.opt.d_domain = d_domain
         self.opt.search_inflation = delta
+        names = {f[0] for f in Options._fields_}
         for k, v in kw.items():
+            if k not in names:
+                raise TypeError(f"unknown option {k!r}")
             setattr(self.opt, k, v)
         h = ctypes.c_void_p()
         if stream is None:
