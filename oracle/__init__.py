@@ -23,6 +23,9 @@ Parity status per function (how each is pinned is in ``tests/test_oracle_*.py``)
       and linear-field reproduction on full coverage, matching meshes, a
       brute-force point location over all master elements, convergence to the
       segment-based result)
+  nodal_normals / facing_pairs / weighted_normal_gap / ncp -- pinned (flat
+      and cylindrical closed forms, parallel and tilted planes, numpy
+      definitions, complementarity cases)
   tangent                            -- pinned (finite differences, Euler
       homogeneity, translation and rotation invariance, a closed-form
       overlap-area derivative, consistency with weighted_gap_grad)
@@ -105,6 +108,10 @@ def _load():
             lib.oracle_element_based_blocks.restype = ctypes.c_int
             lib.oracle_element_based_blocks.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(Opts),
                                                         P, P, i64, i32, P, P, P]
+            lib.oracle_nodal_normals.restype = ctypes.c_int
+            lib.oracle_nodal_normals.argtypes = [P, i64, P, i64, i32, P]
+            lib.oracle_element_normals.restype = ctypes.c_int
+            lib.oracle_element_normals.argtypes = [P, P, i64, i32, P]
             lib.oracle_slave_frames.restype = ctypes.c_int
             lib.oracle_slave_frames.argtypes = [P, P, i64, i32, P]
             lib.oracle_tri_rule.restype = ctypes.c_int
@@ -441,6 +448,52 @@ def bsr_dense(rowptr, colidx, vals, nrows, ncols):
             k = int(colidx[q])
             out[3 * j:3 * j + 3, 3 * k:3 * k + 3] += vals[q]
     return out
+
+
+def nodal_normals(itf) -> np.ndarray:
+    """Averaged unit nodal normals of the slave surface (Ns x 3)."""
+    lib = _load()
+    xs, cs, _, _ = _mesh_arrays(itf)
+    out = np.zeros_like(xs)
+    lib.oracle_nodal_normals(_p(xs), xs.shape[0], _p(cs), cs.shape[0], cs.shape[1], _p(out))
+    return out
+
+
+def element_normals(x, conn) -> np.ndarray:
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    conn = np.ascontiguousarray(conn, np.int32)
+    out = np.zeros((conn.shape[0], 3))
+    lib.oracle_element_normals(_p(x), _p(conn), conn.shape[0], conn.shape[1], _p(out))
+    return out
+
+
+def facing_pairs(itf, s, m):
+    """Candidate pairs whose slave and master element normals (at the element
+    centres) point against each other: n_s . n_m < 0 (the facing test)."""
+    ns = element_normals(itf.xs, itf.conn_s)
+    nm = element_normals(itf.xm, itf.conn_m)
+    s = np.asarray(s)
+    m = np.asarray(m)
+    keep = np.einsum("ij,ij->i", ns[s], nm[m]) < 0.0
+    return s[keep], m[keep]
+
+
+def weighted_normal_gap(itf, D, M, normals=None) -> np.ndarray:
+    """g_j = -n_j . ((D Xs)_j - (M Xm)_j): the weighted normal gap of slave node
+    j (positive when the bodies are apart along the outward slave normal)."""
+    n = nodal_normals(itf) if normals is None else np.asarray(normals)
+    v = D @ itf.xs - M @ itf.xm
+    return -np.einsum("ij,ij->i", n, v)
+
+
+def ncp(lam_n, gap, c: float):
+    """Active set and complementarity residual of the Hertz-Signorini-Moreau
+    conditions (gap >= 0, pressure <= 0, gap * pressure = 0) per slave node:
+    active = lam_n + c gap < 0; C = lam_n - min(0, lam_n + c gap)."""
+    lam_n = np.asarray(lam_n, np.float64)
+    t = lam_n + c * np.asarray(gap, np.float64)
+    return t < 0.0, lam_n - np.minimum(0.0, t)
 
 
 def tri_rule(which: int = 7) -> np.ndarray:

@@ -1115,6 +1115,67 @@ int oracle_tangent_blocks(const double* xs, const int32_t* cs, int64_t Es, int32
   return 0;
 }
 
+// Averaged nodal normals of a surface mesh (the continuous normal field of
+// Sec. 2.2 used by contact formulations): at each node, the sum over the
+// adjacent elements (element order) of each element's unit normal at that
+// node's parametric position, normalised.  out: N x 3 (zero for unused nodes).
+int oracle_nodal_normals(const double* x, int64_t N, const int32_t* conn, int64_t E, int32_t nen, double* out) {
+  for (int64_t i = 0; i < 3 * N; ++i) out[i] = 0.0;
+  static const double tri_pts[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+  for (int64_t e = 0; e < E; ++e) {
+    V3<double> X[4];
+    for (int a = 0; a < nen; ++a) {
+      const double* q = x + 3 * (int64_t)conn[(int64_t)nen * e + a];
+      X[a] = {q[0], q[1], q[2]};
+    }
+    for (int a = 0; a < nen; ++a) {
+      const double xi = nen == 4 ? kQuadCorner[a][0] : tri_pts[a][0];
+      const double eta = nen == 4 ? kQuadCorner[a][1] : tri_pts[a][1];
+      double dN[4][2];
+      shape_deriv<double>(nen, xi, eta, dN);
+      V3<double> g1{0.0, 0.0, 0.0}, g2{0.0, 0.0, 0.0};
+      for (int b = 0; b < nen; ++b) {
+        g1 = {g1.x + dN[b][0] * X[b].x, g1.y + dN[b][0] * X[b].y, g1.z + dN[b][0] * X[b].z};
+        g2 = {g2.x + dN[b][1] * X[b].x, g2.y + dN[b][1] * X[b].y, g2.z + dN[b][1] * X[b].z};
+      }
+      V3<double> n = cross(g1, g2);
+      const double ln = std::sqrt(dot(n, n));
+      double* o = out + 3 * (int64_t)conn[(int64_t)nen * e + a];
+      o[0] += n.x / ln; o[1] += n.y / ln; o[2] += n.z / ln;
+    }
+  }
+  for (int64_t i = 0; i < N; ++i) {
+    double* o = out + 3 * i;
+    const double l = std::sqrt(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
+    if (l > 0.0) { o[0] /= l; o[1] /= l; o[2] /= l; }
+  }
+  return 0;
+}
+
+// Unit normal of every element at its centre (quad4 xi = (0, 0), tri3 the
+// constant normal): E x 3.
+int oracle_element_normals(const double* x, const int32_t* conn, int64_t E, int32_t nen, double* out) {
+  for (int64_t e = 0; e < E; ++e) {
+    V3<double> X[4];
+    for (int a = 0; a < nen; ++a) {
+      const double* q = x + 3 * (int64_t)conn[(int64_t)nen * e + a];
+      X[a] = {q[0], q[1], q[2]};
+    }
+    const double xc = nen == 4 ? 0.0 : 1.0 / 3.0;
+    double dN[4][2];
+    shape_deriv<double>(nen, xc, xc, dN);
+    V3<double> g1{0.0, 0.0, 0.0}, g2{0.0, 0.0, 0.0};
+    for (int b = 0; b < nen; ++b) {
+      g1 = {g1.x + dN[b][0] * X[b].x, g1.y + dN[b][0] * X[b].y, g1.z + dN[b][0] * X[b].z};
+      g2 = {g2.x + dN[b][1] * X[b].x, g2.y + dN[b][1] * X[b].y, g2.z + dN[b][1] * X[b].z};
+    }
+    V3<double> n = cross(g1, g2);
+    const double ln = std::sqrt(dot(n, n));
+    out[3 * e] = n.x / ln; out[3 * e + 1] = n.y / ln; out[3 * e + 2] = n.z / ln;
+  }
+  return 0;
+}
+
 // Slave auxiliary planes (x0, n0, t1, t2) per element: Es x 12.
 int oracle_slave_frames(const double* xs, const int32_t* cs, int64_t Es, int32_t nen_s, double* out) {
   for (int64_t e = 0; e < Es; ++e) {
