@@ -90,6 +90,9 @@ typedef struct mortar_options {
                                of Sec. 3.3 for moving interfaces (0); bins are rebuilt every run */
   int32_t integration;      /* MORTAR_INTEGRATE_SEGMENT (default) or MORTAR_INTEGRATE_ELEMENT */
   int32_t element_rule_n;   /* points per direction of the element-based rule, 1..16 (8) */
+  int32_t facing_test;      /* 1: keep only candidate pairs whose slave and master element normals (at
+                               the element centres) point against each other, n_s . n_m < 0 (0) */
+  int32_t pad0;
 } mortar_options;
 
 typedef struct mortar_stats {
@@ -235,6 +238,22 @@ int mortar_tangent(mortar_ctx* ctx, const double* ys, const double* ym, int32_t 
  * mortar_tangent call or after a coordinate change. */
 int mortar_tangent_copy(mortar_ctx* ctx, int64_t* rowptr, int32_t* colidx, double* vals, int64_t capacity_nnzb,
                         int32_t on_device);
+
+/* Contact-specific terms of the last evaluation (Sec. 2.1: Hertz-Signorini-
+ * Moreau conditions gap >= 0, pressure <= 0, gap * pressure = 0; the gap is
+ * measured along a continuous field of normals):
+ *   normals (n_slave_nodes x 3): averaged nodal normals -- at each slave node
+ *     the sum, over its elements in element order, of the element's unit
+ *     normal at that node, normalised;
+ *   gap (n_slave_nodes): weighted normal gap g_j = -n_j . ((D X_s)_j - (M X_m)_j),
+ *     positive where the master lies beyond the slave along n_j;
+ *   with lambda_n (n_slave_nodes normal multipliers, compression negative) and
+ *   c > 0: active (bytes) = lambda_n + c g < 0, ncp = lambda_n - min(0, lambda_n + c g)
+ *   (zero exactly where the conditions hold).
+ * Any output may be NULL; lambda_n NULL skips active / ncp.  Evaluates first
+ * if the last evaluation is stale. */
+int mortar_contact_terms(mortar_ctx* ctx, const double* lambda_n, double c, double* normals, double* gap,
+                         uint8_t* active, double* ncp, int32_t on_device);
 
 /* Run search + integration + assembly (+ the adjoint if lambda != NULL) as
  * one stream-ordered sequence with device-side sizes, captured once into a

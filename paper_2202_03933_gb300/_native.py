@@ -26,6 +26,7 @@ EXPORTS = (
     "mortar_weighted_gap_grad", "mortar_run_graph", "mortar_get_gradient", "mortar_get_stats",
     "mortar_set_timing", "mortar_set_launch", "mortar_status_string", "mortar_probe_dfma",
     "mortar_integrate_pairs_static", "mortar_autotune", "mortar_tangent", "mortar_tangent_copy",
+    "mortar_contact_terms",
 )
 
 
@@ -41,7 +42,8 @@ class Options(ctypes.Structure):
                 ("search_inflation", ctypes.c_double), ("newton_tol", ctypes.c_double),
                 ("clip_tol_rel", ctypes.c_double), ("merge_tol_rel", ctypes.c_double),
                 ("area_tol_rel", ctypes.c_double), ("bin_margin", ctypes.c_double),
-                ("integration", ctypes.c_int32), ("element_rule_n", ctypes.c_int32)]
+                ("integration", ctypes.c_int32), ("element_rule_n", ctypes.c_int32),
+                ("facing_test", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +96,7 @@ def lib():
                                     ctypes.POINTER(ctypes.c_float)],
                 "mortar_tangent": [P, P, P, i32, i32, ctypes.POINTER(i64)],
                 "mortar_tangent_copy": [P, P, P, P, i64, i32],
+                "mortar_contact_terms": [P, P, f64, P, P, P, P, i32],
                 "mortar_status_string": [ctypes.c_int],
                 "mortar_probe_dfma": [P, i32, i32, i64, i32, P],
                 "mortar_integrate_pairs_static": [ctypes.POINTER(Options), P, P, i64, P, i64, i32,

@@ -343,6 +343,7 @@ int set_common(mortar_ctx* c, int32_t n_if, const int64_t* sn_off, const int64_t
   MORTAR_TRY(buf_reserve(c->De, Es * 16 * 8));
   MORTAR_TRY(buf_reserve(c->box_s, Es * 8 * 8));
   MORTAR_TRY(buf_reserve(c->box_m, Em * 8 * 8));
+  if (c->opt.facing_test) MORTAR_TRY(buf_reserve(c->nrm_m, Em * 3 * 8));
   MORTAR_TRY(buf_reserve(c->chunk_red, std::max<size_t>(ch.size(), 1) * 8 * 8));
   MORTAR_TRY(buf_reserve(c->grid, (size_t)n_if * sizeof(GridParams)));
   MORTAR_TRY(buf_reserve(c->mkey, Em * 8));
@@ -406,6 +407,8 @@ int mortar_default_options(mortar_options* o) {
   o->bin_margin = 0.0;
   o->integration = MORTAR_INTEGRATE_SEGMENT;
   o->element_rule_n = 8;
+  o->facing_test = 0;
+  o->pad0 = 0;
   return MORTAR_OK;
 }
 
@@ -417,7 +420,7 @@ int mortar_create(mortar_ctx** out, const mortar_options* o, void* stream) {
   if ((c->opt.lm != 0 && c->opt.lm != 1) || (c->opt.d_domain != 0 && c->opt.d_domain != 1) ||
       c->opt.newton_max_iter < 1 || !(c->opt.search_inflation >= 0.0) || !(c->opt.bin_margin >= 0.0) ||
       (c->opt.integration != MORTAR_INTEGRATE_SEGMENT && c->opt.integration != MORTAR_INTEGRATE_ELEMENT) ||
-      c->opt.element_rule_n < 1 || c->opt.element_rule_n > 16) {
+      c->opt.element_rule_n < 1 || c->opt.element_rule_n > 16 || (c->opt.facing_test != 0 && c->opt.facing_test != 1)) {
     delete c;
     return MORTAR_ERR_INVALID_ARG;
   }
@@ -455,7 +458,8 @@ void mortar_destroy(mortar_ctx* c) {
                     &c->col_M, &c->val_M, &c->scan_tmp, &c->lambda, &c->gs_pair, &c->gm_pair, &c->abar_pair,
                     &c->J_pair, &c->ge_elem, &c->mp_cnt, &c->mp_off, &c->mp_list, &c->grad_s, &c->grad_m,
                     &c->J_part, &c->dstat, &c->cta_t, &c->tan_ys, &c->tan_ym, &c->tan_Kp, &c->tan_Op,
-                    &c->tan_Ke, &c->tan_rowptr, &c->tan_col, &c->tan_val, &c->rule_1d};
+                    &c->tan_Ke, &c->tan_rowptr, &c->tan_col, &c->tan_val, &c->rule_1d, &c->nrm_m,
+                    &c->cn_normals, &c->cn_gap, &c->cn_lam, &c->cn_active, &c->cn_ncp};
   for (DevBuf* b : bufs) buf_free(*b);
   if (c->hstat) cudaFreeHost(c->hstat);
   for (int i = 0; i < 8; ++i)
@@ -617,6 +621,36 @@ int mortar_tangent(mortar_ctx* c, const double* ys, const double* ym, int32_t ad
   if (c->timing) cudaEventElapsedTime(&c->stats.ms_tangent, c->ev[6], c->ev[7]);
   c->tan_valid = true;
   if (nnzb) *nnzb = need;
+  return r0;
+}
+
+int mortar_contact_terms(mortar_ctx* c, const double* lambda_n, double cpen, double* normals, double* gap,
+                         uint8_t* active, double* ncp, int32_t on_device) {
+  if (!c) return MORTAR_ERR_INVALID_ARG;
+  if (!c->have_interface) return MORTAR_ERR_STATE;
+  if (lambda_n && !(cpen > 0.0)) return MORTAR_ERR_INVALID_ARG;
+  int r0 = MORTAR_OK;
+  if (!c->eval_valid) {
+    Phases ph;
+    r0 = run(c, ph);
+    if (r0 != MORTAR_OK && r0 != MORTAR_ERR_NEWTON && r0 != MORTAR_ERR_DEGENERATE) return r0;
+  }
+  const size_t Ns = (size_t)std::max<int64_t>(c->Ns, 1);
+  MORTAR_TRY(buf_reserve(c->cn_normals, Ns * 24));
+  MORTAR_TRY(buf_reserve(c->cn_gap, Ns * 8));
+  if (lambda_n) {
+    MORTAR_TRY(buf_reserve(c->cn_lam, Ns * 8));
+    MORTAR_TRY(buf_reserve(c->cn_active, Ns));
+    MORTAR_TRY(buf_reserve(c->cn_ncp, Ns * 8));
+    MORTAR_TRY(copy_in(c->cn_lam.p, lambda_n, (size_t)c->Ns * 8, on_device, c->stream));
+  }
+  launch_contact_terms(c, lambda_n != nullptr, cpen);
+  MORTAR_TRY(check_cuda());
+  if (normals) MORTAR_TRY(copy_out(normals, c->cn_normals.p, (size_t)c->Ns * 24, on_device, c->stream));
+  if (gap) MORTAR_TRY(copy_out(gap, c->cn_gap.p, (size_t)c->Ns * 8, on_device, c->stream));
+  if (lambda_n && active) MORTAR_TRY(copy_out(active, c->cn_active.p, (size_t)c->Ns, on_device, c->stream));
+  if (lambda_n && ncp) MORTAR_TRY(copy_out(ncp, c->cn_ncp.p, (size_t)c->Ns * 8, on_device, c->stream));
+  MORTAR_TRY(cuda_status(cudaStreamSynchronize(c->stream)));
   return r0;
 }
 

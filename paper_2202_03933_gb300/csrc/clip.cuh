@@ -156,14 +156,9 @@ struct MapInverse {
     a00 = j11 * id; a01 = -j01 * id; a10 = -j10 * id; a11 = j00 * id;
   }
 
-  // returns false if the FP32 iteration did not settle (xi then is the best found)
-  __device__ __forceinline__ bool solve(double xu, double xv, double& xi, double& eta) const {
+  // FP32 Newton of a bilinear map (error ~1e-7 in xi); false if it did not settle
+  __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
-    if (affine) {
-      xi = i00 * du + i01 * dv;
-      eta = i10 * du + i11 * dv;
-      return true;
-    }
     const float tu = (float)(du * sc), tv = (float)(dv * sc);
     float x = b00 * tu + b01 * tv, y = b10 * tu + b11 * tv;
     bool conv = false;
@@ -181,12 +176,30 @@ struct MapInverse {
     }
     xi = (double)x;
     eta = (double)y;
+    return conv;
+  }
+
+  // one FP64 Newton step of a bilinear map from (xi, eta)
+  __device__ __forceinline__ void polish(double xu, double xv, double& xi, double& eta) const {
+    const double du = xu - m.c0u, dv = xv - m.c0v;
     double k00, k01, k10, k11;
     jinv(xi, eta, k00, k01, k10, k11);
     const double ru = fma(fma(m.c3u, eta, m.c1u), xi, fma(m.c2u, eta, -du));
     const double rv = fma(fma(m.c3v, eta, m.c1v), xi, fma(m.c2v, eta, -dv));
     xi -= fma(k00, ru, k01 * rv);
     eta -= fma(k10, ru, k11 * rv);
+  }
+
+  // returns false if the FP32 iteration did not settle (xi then is the best found)
+  __device__ __forceinline__ bool solve(double xu, double xv, double& xi, double& eta) const {
+    if (affine) {
+      const double du = xu - m.c0u, dv = xv - m.c0v;
+      xi = i00 * du + i01 * dv;
+      eta = i10 * du + i11 * dv;
+      return true;
+    }
+    const bool conv = coarse(xu, xv, xi, eta);
+    polish(xu, xv, xi, eta);
     return conv;
   }
 };

@@ -30,6 +30,8 @@ struct RunParams {
   double bin_margin;
   int32_t integration;    // 0 segment-based, 1 element-based
   int32_t rule_n;         // element-based rule: points per direction
+  int32_t facing;         // facing test on candidate pairs
+  int32_t pad2;
 };
 
 // Slave element record (FP64 words).  Written once per evaluation by the

@@ -99,6 +99,8 @@ struct mortar_ctx {
   bool tan_valid = false;
 
   // ---- status / bookkeeping
+  mortar::DevBuf nrm_m;                     // master element centre normals (facing test), Em x 3
+  mortar::DevBuf cn_normals, cn_gap, cn_lam, cn_active, cn_ncp;   // contact terms per slave node
   mortar::DevBuf rule_1d;                   // element-based rule: Gauss-Legendre points and weights
   int32_t rule_1d_n = 0;
   mortar::DevBuf dstat;                     // mortar::DevStatus
@@ -135,6 +137,9 @@ void launch_candidates(mortar_ctx* c);
 
 // k_integrate.cu
 void launch_integrate(mortar_ctx* c, const RunParams& rp);
+
+// k_contact.cu
+void launch_contact_terms(mortar_ctx* c, bool with_ncp, double cpen);   // normals, gap (+ active, ncp)
 
 // k_elembased.cu
 int upload_gauss_legendre(mortar_ctx* c, int n);   // element-based rule table (host, at create)

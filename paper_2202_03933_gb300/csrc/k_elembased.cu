@@ -95,7 +95,16 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
           const double xv = smap.c0v + smap.c1v * xi + smap.c2v * eta + smap.c3v * xe;
           if (xu < lo_u || xu > hi_u || xv < lo_v || xv > hi_v) continue;
           double m1, m2;
-          if (!mi.solve(xu, xv, m1, m2)) continue;
+          if (mi.affine) {
+            mi.solve(xu, xv, m1, m2);
+          } else {   // FP32 iterate first: points clearly outside skip the FP64 step
+            if (!mi.coarse(xu, xv, m1, m2)) continue;
+            const bool near = NM == 4
+                ? (fabs(m1) <= 1.0 + 1e-5 && fabs(m2) <= 1.0 + 1e-5)
+                : (m1 >= -1e-5 && m2 >= -1e-5 && m1 + m2 <= 1.0 + 1e-5);
+            if (!near) continue;
+            mi.polish(xu, xv, m1, m2);
+          }
           const bool inside = NM == 4
               ? (fabs(m1) <= 1.0 + kInsideTol && fabs(m2) <= 1.0 + kInsideTol)
               : (m1 >= -kInsideTol && m2 >= -kInsideTol && m1 + m2 <= 1.0 + kInsideTol);

@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
 template <int NM>
 __global__ void __launch_bounds__(kThreads) k_master_boxes(const double* __restrict__ xm,
                                                             const int32_t* __restrict__ conn, int64_t Em,
-                                                            double delta, double* __restrict__ box) {
+                                                            double delta, double* __restrict__ box,
+                                                            double* __restrict__ nrm) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= Em) return;
   V3 X[4];
@@ -294,6 +295,22 @@ __global__ void __launch_bounds__(kThreads) k_master_boxes(const double* __restr
   }
   b[6] = sqrt(h2);
   b[7] = 0.0;
+  if (nrm) {   // unit normal at the element centre (facing test)
+    V3 g1, g2;
+    if constexpr (NM == 4) {
+      const V3 d10 = sub(X[1], X[0]), d23 = sub(X[2], X[3]), d21 = sub(X[2], X[1]), d30 = sub(X[3], X[0]);
+      g1 = {0.25 * (d10.x + d23.x), 0.25 * (d10.y + d23.y), 0.25 * (d10.z + d23.z)};
+      g2 = {0.25 * (d21.x + d30.x), 0.25 * (d21.y + d30.y), 0.25 * (d21.z + d30.z)};
+    } else {
+      g1 = sub(X[1], X[0]);
+      g2 = sub(X[2], X[0]);
+    }
+    const V3 n = {g1.y * g2.z - g1.z * g2.y, g1.z * g2.x - g1.x * g2.z, g1.x * g2.y - g1.y * g2.x};
+    const double l = sqrt(dot(n, n));
+    nrm[3 * e] = n.x / l;
+    nrm[3 * e + 1] = n.y / l;
+    nrm[3 * e + 2] = n.z / l;
+  }
 }
 
 // One block per chunk: min of lo, max of hi, max of h over its elements.
@@ -437,6 +454,8 @@ RunParams run_params(const mortar_ctx* c) {
   rp.bin_margin = c->opt.bin_margin;
   rp.integration = c->opt.integration;
   rp.rule_n = c->opt.element_rule_n;
+  rp.facing = c->opt.facing_test;
+  rp.pad2 = 0;
   return rp;
 }
 
@@ -470,10 +489,10 @@ void launch_master_boxes(mortar_ctx* c, const RunParams& rp) {
   const unsigned g = (unsigned)((c->Em + kThreads - 1) / kThreads);
   if (c->nen_m == 4)
     k_master_boxes<4><<<g, kThreads, 0, c->stream>>>(c->xm.as<double>(), c->conn_m.as<int32_t>(), c->Em, rp.delta,
-                                                     c->box_m.as<double>());
+                                                     c->box_m.as<double>(), rp.facing ? c->nrm_m.as<double>() : nullptr);
   else
     k_master_boxes<3><<<g, kThreads, 0, c->stream>>>(c->xm.as<double>(), c->conn_m.as<int32_t>(), c->Em, rp.delta,
-                                                     c->box_m.as<double>());
+                                                     c->box_m.as<double>(), rp.facing ? c->nrm_m.as<double>() : nullptr);
 }
 
 void launch_grid_params(mortar_ctx* c, const RunParams& rp) {

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(kThreads) k_candidates(
     const double* __restrict__ box_s, const double* __restrict__ box_m, const int64_t* __restrict__ se_off,
     int32_t n_if, int64_t Es, const GridParams* __restrict__ grid, const int64_t* __restrict__ start,
     const int32_t* __restrict__ elems, int32_t* __restrict__ cnt, const int64_t* __restrict__ pair_off,
-    int64_t pair_cap, int32_t* __restrict__ ps, int32_t* __restrict__ pm, DevStatus* st) {
+    int64_t pair_cap, int32_t* __restrict__ ps, int32_t* __restrict__ pm, const double* __restrict__ srec,
+    const double* __restrict__ nrm_m, DevStatus* st) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= Es || st->over_bins) return;
   if (MODE == 1 && pair_off[Es] > pair_cap) {
@@ -92,6 +93,12 @@ __global__ void __launch_bounds__(kThreads) k_candidates(
   for (int k = 0; k < 6; ++k) bs[k] = box_s[8 * s + k];
   int32_t ijk[3];
   bin_coords(g, box_s + 8 * s, ijk);
+  // facing test (optional): slave normal n0 of the element record vs the master centre normal
+  double nsx = 0.0, nsy = 0.0, nsz = 0.0;
+  if (nrm_m) {
+    const double* r = srec + (int64_t)SR_STRIDE * s;
+    nsx = r[SR_N0]; nsy = r[SR_N0 + 1]; nsz = r[SR_N0 + 2];
+  }
   int32_t local[kLocalCand];
   int32_t n = 0;
   const int64_t base = MODE == 1 ? pair_off[s] : 0;
@@ -109,6 +116,10 @@ __global__ void __launch_bounds__(kThreads) k_candidates(
         for (int64_t q = b0; q < b1; ++q) {
           const int32_t m = elems[q];
           if (!overlap(bs, box_m + 8 * (int64_t)m)) continue;
+          if (nrm_m) {
+            const double* q = nrm_m + 3 * (int64_t)m;
+            if (!(nsx * q[0] + nsy * q[1] + nsz * q[2] < 0.0)) continue;
+          }
           if (MODE == 1) {
             if (n < kLocalCand) local[n] = m;
             pm[base + n] = m;   // also written in place for the long-list path
@@ -174,7 +185,8 @@ void launch_candidates(mortar_ctx* c) {
     k_candidates<0><<<g, kThreads, 0, c->stream>>>(
         c->box_s.as<double>(), c->box_m.as<double>(), c->se_off.as<int64_t>(), c->n_if, c->Es,
         c->grid.as<GridParams>(), c->bin_start.as<int64_t>(), c->bin_elems.as<int32_t>(), c->cand_cnt.as<int32_t>(),
-        nullptr, 0, nullptr, nullptr, st);
+        nullptr, 0, nullptr, nullptr, c->srec.as<double>(), c->opt.facing_test ? c->nrm_m.as<double>() : nullptr,
+        st);
   launch_exclusive_scan_i32(c->cand_cnt.as<int32_t>(), c->pair_off.as<int64_t>(), nullptr, c->Es,
                             c->scan_tmp.as<int64_t>(), c->stream);
   k_pairs_total<<<1, 32, 0, c->stream>>>(c->pair_off.as<int64_t>(), c->Es, st);
@@ -182,7 +194,8 @@ void launch_candidates(mortar_ctx* c) {
     k_candidates<1><<<g, kThreads, 0, c->stream>>>(
         c->box_s.as<double>(), c->box_m.as<double>(), c->se_off.as<int64_t>(), c->n_if, c->Es,
         c->grid.as<GridParams>(), c->bin_start.as<int64_t>(), c->bin_elems.as<int32_t>(), nullptr,
-        c->pair_off.as<int64_t>(), c->pair_cap, c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), st);
+        c->pair_off.as<int64_t>(), c->pair_cap, c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(),
+        c->srec.as<double>(), c->opt.facing_test ? c->nrm_m.as<double>() : nullptr, st);
 }
 
 }  // namespace mortar

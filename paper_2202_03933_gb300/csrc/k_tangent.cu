@@ -507,9 +507,8 @@ struct RowKeys {
 
 constexpr int kRowCap = 64;
 
-// MODE 0: count the unique block columns of each row.  MODE 1: write the
-// sorted columns, then add every source block in visit order (the sums of a
-// block follow the gather order: reproducible).
+// One thread per block row.  MODE 0: count the unique block columns.
+// MODE 1: write them, sorted (the values follow in k_tangent_rows_warp).
 template <int MODE, class Src>
 __global__ void __launch_bounds__(kThreads) k_tangent_rows(Src src, int64_t N, int32_t* __restrict__ cnt,
                                                            const int64_t* __restrict__ rp, int64_t cap,
@@ -543,23 +542,118 @@ __global__ void __launch_bounds__(kThreads) k_tangent_rows(Src src, int64_t N, i
   } else if (MODE == 1) {
     for (int k = 0; k < u; ++k) col[o + k] = keys.col[k];
   }
-  if (MODE == 0) {
-    cnt[j] = u;
+  if (MODE == 0) cnt[j] = u;
+  (void)val;
+}
+
+// Value pass, one warp per block row: the row's sorted columns (written by
+// k_tangent_rows<1>) go to shared memory, then the row's sources are visited
+// in the fixed order and each source's
+// entries (72 of a pair row, 36 of an element row, contiguous in memory) are
+// read by the 32 lanes together and added to the row's blocks held in shared
+// memory.  Within one source no two entries share a block entry, and sources
+// follow each other after a warp barrier, so every block entry is summed in
+// the same order (sources in visit order).  Rows with more than kRowCap
+// columns are summed by lane 0 alone in global memory, in the same order.
+constexpr int kRowWarps = 4;
+
+template <int NS, int NM, bool SEG, bool DUAL, bool ELEMD>
+__global__ void __launch_bounds__(32 * kRowWarps) k_tangent_rows_warp(TanRowSource<NS, NM, SEG, DUAL, ELEMD> src,
+                                                                      int64_t N, const int64_t* __restrict__ rp,
+                                                                      int64_t cap, int32_t* __restrict__ col,
+                                                                      double* __restrict__ val, DevStatus* st) {
+  __shared__ int32_t keys_s[kRowWarps][kRowCap];
+  __shared__ double acc_s[kRowWarps][kRowCap * 9];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* keys = keys_s[w];
+  double* acc = acc_s[w];
+  if (st->over_pairs) return;
+  if (rp[N] > cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&st->over_K, 1ull);
     return;
   }
-  double* vrow = val + 9 * o;
-  for (int k = 0; k < 9 * u; ++k) vrow[k] = 0.0;
-  const int32_t* crow = col + o;
-  src.visit(j, [&](int32_t c, const double* blk, int stride, double diag) {
-    int lo = 0, hi = u;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (crow[mid] < c) lo = mid + 1; else hi = mid;
+  const int64_t nw = (int64_t)gridDim.x * kRowWarps;
+  for (int64_t j = (int64_t)blockIdx.x * kRowWarps + w; j < N; j += nw) {
+    const int64_t o = rp[j];
+    const int u = (int)(rp[j + 1] - o);
+    if (u > kRowCap) {   // long row: lane 0 accumulates in global memory, in the same order
+      if (lane == 0) {
+        double* vrow = val + 9 * o;
+        for (int k = 0; k < 9 * u; ++k) vrow[k] = 0.0;
+        const int32_t* crow = col + o;
+        src.visit(j, [&](int32_t c, const double* blk, int stride, double diag) {
+          int lo = 0, hi = u;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (crow[mid] < c) lo = mid + 1; else hi = mid;
+          }
+          double* vb = vrow + 9 * lo;
+          for (int cc = 0; cc < 3; ++cc)
+            for (int d = 0; d < 3; ++d) vb[3 * cc + d] += blk[stride * cc + d] + (cc == d ? diag : 0.0);
+        });
+      }
+      __syncwarp();
+      continue;
     }
-    double* vb = vrow + 9 * lo;
-    for (int cc = 0; cc < 3; ++cc)
-      for (int d = 0; d < 3; ++d) vb[3 * cc + d] += blk[stride * cc + d] + (cc == d ? diag : 0.0);
-  });
+    for (int k = lane; k < u; k += 32) keys[k] = col[o + k];
+    for (int k = lane; k < 9 * u; k += 32) acc[k] = 0.0;
+    __syncwarp();
+    auto find = [&](int32_t c) {
+      int lo = 0, hi = u;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < c) lo = mid + 1; else hi = mid;
+      }
+      return lo;
+    };
+    for (int64_t q = src.n2e_ptr[j]; q < src.n2e_ptr[j + 1]; ++q) {
+      const int64_t ee = src.n2e_ent[q];
+      const int64_t e = ee >> 2;
+      const int a = (int)(ee & 3);
+      bool any = false;
+      for (int64_t p = src.pair_off[e]; p < src.pair_off[e + 1]; ++p) {
+        if (!src.flag[p]) continue;
+        any = true;
+        const int64_t m = src.pm[p];
+        int mypos = 0;   // lanes 0..7: block position of the pair's node k = lane
+        if (lane < NS) mypos = find(src.conn_s[(int64_t)NS * e + lane]);
+        else if (lane >= 4 && lane < 4 + NM) mypos = find((int32_t)(src.Ns + src.conn_m[(int64_t)NM * m + lane - 4]));
+        const double* kb = src.Kp + 288 * p + 72 * a;
+        for (int it = 0; it < 3; ++it) {   // entries lane, lane + 32, lane + 64 (< 72)
+          const int idx = lane + 32 * it;
+          const int ic = idx < 72 ? idx : 0;
+          const int c = ic / 24, rem = ic - 24 * c, k = rem / 3, d = rem - 3 * k;
+          const int pos = __shfl_sync(0xffffffffu, mypos, k);   // every lane takes part
+          const bool valid = idx < 72 && (k < NS || (k >= 4 && k - 4 < NM));
+          if (!valid) continue;
+          double v = kb[idx];
+          if (src.direct && c == d)
+            v += k < 4 ? (SEG ? src.Dblk[16 * p + 4 * a + k] : 0.0) : -src.Mblk[16 * p + 4 * a + (k - 4)];
+          acc[9 * pos + 3 * c + d] += v;
+        }
+        __syncwarp();
+      }
+      if (ELEMD || (DUAL && any)) {
+        int mypos = 0;
+        if (lane < NS) mypos = find(src.conn_s[(int64_t)NS * e + lane]);
+        const double* kb = src.Ke + 144 * e + 36 * a;
+        for (int it = 0; it < 2; ++it) {   // entries lane, lane + 32 (< 36)
+          const int idx = lane + 32 * it;
+          const int ic = idx < 36 ? idx : 0;
+          const int c = ic / 12, rem = ic - 12 * c, k = rem / 3, d = rem - 3 * k;
+          const int pos = __shfl_sync(0xffffffffu, mypos, k);   // every lane takes part
+          if (idx >= 36 || k >= NS) continue;
+          double v = kb[idx];
+          if (ELEMD && src.direct && c == d) v += src.De[16 * e + 4 * a + k];
+          acc[9 * pos + 3 * c + d] += v;
+        }
+        __syncwarp();
+      }
+    }
+    double* vrow = val + 9 * o;
+    for (int k = lane; k < 9 * u; k += 32) vrow[k] = acc[k];
+    __syncwarp();
+  }
 }
 
 __global__ void k_tangent_nnzb(const int64_t* __restrict__ rp, int64_t N, DevStatus* st) {
@@ -617,7 +711,10 @@ void rows_t(mortar_ctx* c, int mode) {
     k_tangent_nnzb<<<1, 32, 0, c->stream>>>(c->tan_rowptr.as<int64_t>(), N, st);
   } else if (N > 0) {
     k_tangent_rows<1><<<g, kThreads, 0, c->stream>>>(src, N, nullptr, c->tan_rowptr.as<int64_t>(), c->tan_nnzb_cap,
-                                                     c->tan_col.as<int32_t>(), c->tan_val.as<double>(), st);
+                                                     c->tan_col.as<int32_t>(), nullptr, st);
+    const int64_t blocks = std::min<int64_t>((N + kRowWarps - 1) / kRowWarps, (int64_t)c->n_sm * 64);
+    k_tangent_rows_warp<NS, NM, SEG, DUAL, ELEMD><<<(unsigned)blocks, 32 * kRowWarps, 0, c->stream>>>(
+        src, N, c->tan_rowptr.as<int64_t>(), c->tan_nnzb_cap, c->tan_col.as<int32_t>(), c->tan_val.as<double>(), st);
   }
 }
 

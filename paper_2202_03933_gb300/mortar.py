@@ -215,6 +215,23 @@ class Mortar:
         return torch.sparse_bsr_tensor(rp, ci.to(torch.int64), va,
                                        size=(3 * self.Ns, 3 * (self.Ns + self.Nm)))
 
+    def contact_terms(self, lambda_n=None, c: float = 1.0):
+        """Averaged nodal normals (Ns x 3), weighted normal gap (Ns) and, with
+        normal multipliers lambda_n (Ns), the active set and complementarity
+        residual of the Hertz-Signorini-Moreau conditions (numpy arrays)."""
+        normals = np.empty((self.Ns, 3))
+        gap = np.empty(self.Ns)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        if lambda_n is None:
+            call("mortar_contact_terms", self.h, None, float(c), P(normals), P(gap), None, None, 0, ok=(0, -2, -3))
+            return {"normals": normals, "gap": gap}
+        lam = np.ascontiguousarray(lambda_n, np.float64)
+        active = np.empty(self.Ns, np.uint8)
+        ncp = np.empty(self.Ns)
+        call("mortar_contact_terms", self.h, P(lam), float(c), P(normals), P(gap), P(active), P(ncp), 0,
+             ok=(0, -2, -3))
+        return {"normals": normals, "gap": gap, "active": active.astype(bool), "ncp": ncp}
+
     def gradient(self):
         J = ctypes.c_double()
         gs = np.empty((self.Ns, 3))
