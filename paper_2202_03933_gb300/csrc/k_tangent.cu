@@ -8,12 +8,13 @@
 //     O_e,c = sum over quadrature points of W N_e(xi_s) Z_c,
 //     Z_c   = [segment D] sum_b N_b(xi_s) ys_b,c - sum_l N_l(xi_m) ym_l,c,
 // and the pair's rows are sum_e A[a][e] O_e,c (A = I for standard LMs).
-// One thread owns one pair and one component c and runs the reverse sweep of
-// the four outputs O_0..3,c together: the forward geometry (recorded clip,
-// back-projections, shape functions) is computed once, the per-point adjoints
-// of the four seeds are accumulated side by side (their map-coefficient
-// adjoints in shared memory), and only the reverse of the clip and of the
-// projection runs once per seed.  The derivatives through A (dual LMs) and of
+// Three lanes own one pair, one component c each, and run the reverse sweep
+// of the four outputs O_0..3,c together: each lane computes every third
+// quadrature point's back-projections and shape functions and shares them
+// with the other two through shared memory, the per-point adjoints of the
+// four seeds are accumulated side by side (their map-coefficient adjoints in
+// shared memory), and only the reverse of the clip and of the projection runs
+// once per seed.  The derivatives through A (dual LMs) and of
 // the element-domain D depend on the slave element alone: a per-element
 // kernel pushes the pair sums of O and the D term through A = Dh Me^-1 and
 // the element integrals in forward mode over the 12 slave coordinates.  Rows
@@ -32,7 +33,8 @@ namespace {
 constexpr int kTanWarps = 4;
 constexpr int kTanThreads = 32 * kTanWarps;
 constexpr int kThreads = 128;
-constexpr size_t kTanSmem = sizeof(double) * 16 * 4 * kTanThreads;   // map-coefficient adjoints of 4 seeds
+// map-coefficient adjoints of 4 seeds per thread, then 32 exchange slots per warp
+constexpr size_t kTanSmem = sizeof(double) * 16 * 4 * kTanThreads + 32 * kTanWarps * 28 * sizeof(double);
 
 struct TanArgs {
   const int32_t* ps;
@@ -50,11 +52,25 @@ struct TanArgs {
   DevStatus* st;
 };
 
-// Pair p, component cp.  acc: this thread's shared-memory accumulators,
-// entry i at acc[i * kTanThreads].
+// Quadrature-point data one lane computes and the other two lanes of its
+// pair group read (shared memory): back-projections, shape-function state of
+// both sides and both inverse Jacobians.
+struct GPX {
+  double xs1, xs2, xm1, xm2;
+  double sN[4], sq[4], mN[4], mq[4];
+  double a[4], b[4];
+};
+
+// Pair p, component cp, for the lanes of one pair group (lanes 3g, 3g + 1,
+// 3g + 2 hold components 0, 1, 2 of the same pair).  Every lane of the warp
+// calls this with the same control flow around the exchanges: lanes with
+// live = false (no pair) take part in the loops and exchanges without work.
+// acc: this thread's shared-memory accumulators, entry i at acc[i * kTanThreads];
+// gx: the warp's 32 exchange slots.
 template <int NS, int NM, bool SEG, bool DUAL>
-__device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, double* __restrict__ acc,
-                             unsigned long long& clip_over, unsigned long long& newton_fail) {
+__device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, double* __restrict__ acc,
+                             GPX* __restrict__ gx, unsigned long long& clip_over, unsigned long long& newton_fail) {
+  const int lane = threadIdx.x & 31;
   const int32_t s = g.ps[p], m = g.pm[p];
   const double* r = g.srec + (int64_t)SR_STRIDE * s;
   V3 X[4], Y[4];
@@ -87,16 +103,10 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, double* __rest
   const bool mrev = ma2 < 0.0;
   const bool srev = r[SR_REV] != 0.0;
   ClipRec<NS> clip;
-  const bool nonempty = clip.template run<NM>(r, mu, mv, mrev, clip_over);
+  unsigned long long clip_dummy = 0;
+  const bool nonempty = clip.template run<NM>(r, mu, mv, mrev, live ? clip_over : clip_dummy);
   double* kout = g.Kp + 288 * p + 24 * cp;   // row a at + 72 a
-  if (!nonempty) {   // not reached for pairs the count pass found non-empty; blocks stay defined
-    for (int a = 0; a < 4; ++a)
-      for (int k = 0; k < 24; ++k) kout[72 * a + k] = 0.0;
-    if (DUAL)
-      for (int e = 0; e < 4; ++e) g.Op[12 * p + 3 * e + cp] = 0.0;
-    return;
-  }
-  const int nr = clip.nr;
+  const int nr = nonempty ? clip.nr : 0;
   MapInverse mi;
   mi.setup(mmap, NM == 3 || map_is_affine(mmap));
   MapInverse si;
@@ -114,7 +124,7 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, double* __rest
     for (int e = 0; e < NS; ++e) { Rbu[e][k] = 0.0; Rbv[e][k] = 0.0; }
   }
   double cu = 0.0, cv = 0.0;
-  int ncell = 1;
+  int ncell = nr >= 3 ? 1 : 0;
   if (nr > 3) {
     double su = 0.0, sv = 0.0;
     for (int k = 0; k < nr; ++k) { su += Ru[k]; sv += Rv[k]; }
@@ -122,17 +132,24 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, double* __rest
     cv = sv / (double)nr;
     ncell = nr;
   }
+  if (!live) ncell = 0;
   for (int i = 0; i < 16 * NS; ++i) acc[i * kTanThreads] = 0.0;
   double O[4] = {0, 0, 0, 0}, cbu[4] = {0, 0, 0, 0}, cbv[4] = {0, 0, 0, 0};
-  for (int cI = 0; cI < ncell; ++cI) {
-    int ib, iw;
-    double au, av;
-    if (nr == 3) {
-      au = Ru[0]; av = Rv[0]; ib = 1; iw = 2;
-    } else {
-      au = cu; av = cv; ib = cI; iw = cI + 1 == nr ? 0 : cI + 1;
+  const int ncell_w = __reduce_max_sync(0xffffffffu, ncell);
+  const int gbase = 3 * (lane / 3);
+  for (int cI = 0; cI < ncell_w; ++cI) {
+    const bool cell_ok = cI < ncell;
+    int ib = 0, iw = 0;
+    double au = 0.0, av = 0.0;
+    if (cell_ok) {
+      if (nr == 3) {
+        au = Ru[0]; av = Rv[0]; ib = 1; iw = 2;
+      } else {
+        au = cu; av = cv; ib = cI; iw = cI + 1 == nr ? 0 : cI + 1;
+      }
     }
-    const double e1u = Ru[ib] - au, e1v = Rv[ib] - av, e2u = Ru[iw] - au, e2v = Rv[iw] - av;
+    const double e1u = cell_ok ? Ru[ib] - au : 0.0, e1v = cell_ok ? Rv[ib] - av : 0.0;
+    const double e2u = cell_ok ? Ru[iw] - au : 0.0, e2v = cell_ok ? Rv[iw] - av : 0.0;
     const double crs = cross2(e1u, e1v, e2u, e2v);
     const double area = 0.5 * fabs(crs);
     double arb[4], e1bu[4], e1bv[4], e2bu[4], e2bv[4], xbu_c[4], xbv_c[4];
@@ -141,91 +158,129 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, double* __rest
       arb[e] = 0.0; e1bu[e] = 0.0; e1bv[e] = 0.0; e2bu[e] = 0.0; e2bv[e] = 0.0; xbu_c[e] = 0.0; xbv_c[e] = 0.0;
     }
 #pragma unroll 1
-    for (int q = 0; q < 7; ++q) {
-      double l1, l2, w;
-      tri7_point(q, l1, l2, w);
-      const double xu = au + l1 * e1u + l2 * e2u;
-      const double xv = av + l1 * e1v + l2 * e2v;
-      const double W = w * area;
-      double xs1, xs2, xm1, xm2;
-      if (!si.solve(xu, xv, xs1, xs2)) newton_fail++;
-      if (!mi.solve(xu, xv, xm1, xm2)) newton_fail++;
-      ShapeAD<NS> SA;
-      ShapeAD<NM> MA;
-      SA.eval(xs1, xs2);
-      MA.eval(xm1, xm2);
-      double Z = 0.0;
-      if (SEG)
+    for (int rr = 0; rr < 3; ++rr) {
+      // this lane's quadrature point of the round (component cp computes point 3 rr + cp)
+      const int qo = 3 * rr + cp;
+      if (cell_ok && qo < 7) {
+        double l1, l2, w;
+        tri7_point(qo, l1, l2, w);
+        const double xu = au + l1 * e1u + l2 * e2u;
+        const double xv = av + l1 * e1v + l2 * e2v;
+        GPX& o = gx[lane];
+        double xs1, xs2, xm1, xm2;
+        if (!si.solve(xu, xv, xs1, xs2)) newton_fail++;
+        if (!mi.solve(xu, xv, xm1, xm2)) newton_fail++;
+        ShapeAD<NS> SA;
+        ShapeAD<NM> MA;
+        SA.eval(xs1, xs2);
+        MA.eval(xm1, xm2);
+        o.xs1 = xs1; o.xs2 = xs2; o.xm1 = xm1; o.xm2 = xm2;
 #pragma unroll
-        for (int b = 0; b < NS; ++b) Z = fma(SA.N[b], yS[b], Z);
-#pragma unroll
-      for (int l = 0; l < NM; ++l) Z = fma(-MA.N[l], yM[l], Z);
-      // gradients in the plane: J_s^-T grad_xi N_e, J^-T grad_xi of the interpolated y
-      double a00, a01, a10, a11;
-      si.jinv(xs1, xs2, a00, a01, a10, a11);
-      double dx[4], de[4];
-      if constexpr (NS == 4) {
-        dx[0] = -SA.qc; dx[1] = SA.qc; dx[2] = SA.qd; dx[3] = -SA.qd;
-        de[0] = -SA.qa; de[1] = -SA.qb; de[2] = SA.qb; de[3] = SA.qa;
-      } else {
-        dx[0] = -1.0; dx[1] = 1.0; dx[2] = 0.0; dx[3] = 0.0;
-        de[0] = -1.0; de[1] = 0.0; de[2] = 1.0; de[3] = 0.0;
+        for (int k = 0; k < 4; ++k) { o.sN[k] = SA.N[k]; o.mN[k] = MA.N[k]; }
+        o.sq[0] = SA.qa; o.sq[1] = SA.qb; o.sq[2] = SA.qc; o.sq[3] = SA.qd;
+        o.mq[0] = MA.qa; o.mq[1] = MA.qb; o.mq[2] = MA.qc; o.mq[3] = MA.qd;
+        si.jinv(xs1, xs2, o.a[0], o.a[1], o.a[2], o.a[3]);
+        mi.jinv(xm1, xm2, o.b[0], o.b[1], o.b[2], o.b[3]);
       }
-      double gu[4], gv[4], gYsu = 0.0, gYsv = 0.0;
+      __syncwarp();
+#pragma unroll 1
+      for (int jj = 0; jj < 3; ++jj) {
+        const int q = 3 * rr + jj;
+        if (!(cell_ok && q < 7)) continue;
+        const GPX& x = gx[gbase + jj];
+        double l1, l2, w;
+        tri7_point(q, l1, l2, w);
+        const double W = w * area;
+        const double xs1 = x.xs1, xs2 = x.xs2, xm1 = x.xm1, xm2 = x.xm2;
+        ShapeAD<NS> SA;
+        ShapeAD<NM> MA;
 #pragma unroll
-      for (int e = 0; e < NS; ++e) {
-        gu[e] = a00 * dx[e] + a10 * de[e];
-        gv[e] = a01 * dx[e] + a11 * de[e];
-        if (SEG) { gYsu = fma(yS[e], gu[e], gYsu); gYsv = fma(yS[e], gv[e], gYsv); }
+        for (int k = 0; k < 4; ++k) { SA.N[k] = x.sN[k]; MA.N[k] = x.mN[k]; }
+        SA.qa = x.sq[0]; SA.qb = x.sq[1]; SA.qc = x.sq[2]; SA.qd = x.sq[3];
+        MA.qa = x.mq[0]; MA.qb = x.mq[1]; MA.qc = x.mq[2]; MA.qd = x.mq[3];
+        double Z = 0.0;
+        if (SEG)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) Z = fma(SA.N[b], yS[b], Z);
+#pragma unroll
+        for (int l = 0; l < NM; ++l) Z = fma(-MA.N[l], yM[l], Z);
+        // gradients in the plane: J_s^-T grad_xi N_e, J^-T grad_xi of the interpolated y
+        const double a00 = x.a[0], a01 = x.a[1], a10 = x.a[2], a11 = x.a[3];
+        double dx[4], de[4];
+        if constexpr (NS == 4) {
+          dx[0] = -SA.qc; dx[1] = SA.qc; dx[2] = SA.qd; dx[3] = -SA.qd;
+          de[0] = -SA.qa; de[1] = -SA.qb; de[2] = SA.qb; de[3] = SA.qa;
+        } else {
+          dx[0] = -1.0; dx[1] = 1.0; dx[2] = 0.0; dx[3] = 0.0;
+          de[0] = -1.0; de[1] = 0.0; de[2] = 1.0; de[3] = 0.0;
+        }
+        double gu[4], gv[4], gYsu = 0.0, gYsv = 0.0;
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+          gu[e] = a00 * dx[e] + a10 * de[e];
+          gv[e] = a01 * dx[e] + a11 * de[e];
+          if (SEG) { gYsu = fma(yS[e], gu[e], gYsu); gYsv = fma(yS[e], gv[e], gYsv); }
+        }
+        double ym0, ym1;
+        MA.pull(yM, ym0, ym1);
+        const double b00 = x.b[0], b01 = x.b[1], b10 = x.b[2], b11 = x.b[3];
+        const double gYmu = b00 * ym0 + b10 * ym1, gYmv = b01 * ym0 + b11 * ym1;
+        const double WZ = W * Z, wZ = w * Z;
+        const double s12 = xs1 * xs2, m12 = xm1 * xm2;
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+          const double ne = SA.N[e];
+          const double wn = W * ne;
+          O[e] = fma(wn, Z, O[e]);
+          arb[e] = fma(wZ, ne, arb[e]);
+          double su = WZ * gu[e], sv = WZ * gv[e];   // J_s^-T (adjoint of xi_s)
+          if (SEG) { su = fma(wn, gYsu, su); sv = fma(wn, gYsv, sv); }
+          const double tu = -wn * gYmu, tv = -wn * gYmv;   // J_m^-T (adjoint of xi_m)
+          double* A = acc + (16 * e) * kTanThreads;
+          A[0 * kTanThreads] -= su;
+          A[1 * kTanThreads] -= sv;
+          A[2 * kTanThreads] = fma(-xs1, su, A[2 * kTanThreads]);
+          A[3 * kTanThreads] = fma(-xs1, sv, A[3 * kTanThreads]);
+          A[4 * kTanThreads] = fma(-xs2, su, A[4 * kTanThreads]);
+          A[5 * kTanThreads] = fma(-xs2, sv, A[5 * kTanThreads]);
+          A[6 * kTanThreads] = fma(-s12, su, A[6 * kTanThreads]);
+          A[7 * kTanThreads] = fma(-s12, sv, A[7 * kTanThreads]);
+          A[8 * kTanThreads] -= tu;
+          A[9 * kTanThreads] -= tv;
+          A[10 * kTanThreads] = fma(-xm1, tu, A[10 * kTanThreads]);
+          A[11 * kTanThreads] = fma(-xm1, tv, A[11 * kTanThreads]);
+          A[12 * kTanThreads] = fma(-xm2, tu, A[12 * kTanThreads]);
+          A[13 * kTanThreads] = fma(-xm2, tv, A[13 * kTanThreads]);
+          A[14 * kTanThreads] = fma(-m12, tu, A[14 * kTanThreads]);
+          A[15 * kTanThreads] = fma(-m12, tv, A[15 * kTanThreads]);
+          const double xbu = su + tu, xbv = sv + tv;
+          xbu_c[e] += xbu; xbv_c[e] += xbv;
+          e1bu[e] = fma(l1, xbu, e1bu[e]); e1bv[e] = fma(l1, xbv, e1bv[e]);
+          e2bu[e] = fma(l2, xbu, e2bu[e]); e2bv[e] = fma(l2, xbv, e2bv[e]);
+        }
       }
-      double ym0, ym1;
-      MA.pull(yM, ym0, ym1);
-      mi.jinv(xm1, xm2, a00, a01, a10, a11);
-      const double gYmu = a00 * ym0 + a10 * ym1, gYmv = a01 * ym0 + a11 * ym1;
-      const double WZ = W * Z, wZ = w * Z;
-      const double s12 = xs1 * xs2, m12 = xm1 * xm2;
+      __syncwarp();   // the slots are rewritten in the next round
+    }
+    if (cell_ok) {
 #pragma unroll
-      for (int e = 0; e < NS; ++e) {
-        const double ne = SA.N[e];
-        const double wn = W * ne;
-        O[e] = fma(wn, Z, O[e]);
-        arb[e] = fma(wZ, ne, arb[e]);
-        double su = WZ * gu[e], sv = WZ * gv[e];   // J_s^-T (adjoint of xi_s)
-        if (SEG) { su = fma(wn, gYsu, su); sv = fma(wn, gYsv, sv); }
-        const double tu = -wn * gYmu, tv = -wn * gYmv;   // J_m^-T (adjoint of xi_m)
-        double* A = acc + (16 * e) * kTanThreads;
-        A[0 * kTanThreads] -= su;
-        A[1 * kTanThreads] -= sv;
-        A[2 * kTanThreads] = fma(-xs1, su, A[2 * kTanThreads]);
-        A[3 * kTanThreads] = fma(-xs1, sv, A[3 * kTanThreads]);
-        A[4 * kTanThreads] = fma(-xs2, su, A[4 * kTanThreads]);
-        A[5 * kTanThreads] = fma(-xs2, sv, A[5 * kTanThreads]);
-        A[6 * kTanThreads] = fma(-s12, su, A[6 * kTanThreads]);
-        A[7 * kTanThreads] = fma(-s12, sv, A[7 * kTanThreads]);
-        A[8 * kTanThreads] -= tu;
-        A[9 * kTanThreads] -= tv;
-        A[10 * kTanThreads] = fma(-xm1, tu, A[10 * kTanThreads]);
-        A[11 * kTanThreads] = fma(-xm1, tv, A[11 * kTanThreads]);
-        A[12 * kTanThreads] = fma(-xm2, tu, A[12 * kTanThreads]);
-        A[13 * kTanThreads] = fma(-xm2, tv, A[13 * kTanThreads]);
-        A[14 * kTanThreads] = fma(-m12, tu, A[14 * kTanThreads]);
-        A[15 * kTanThreads] = fma(-m12, tv, A[15 * kTanThreads]);
-        const double xbu = su + tu, xbv = sv + tv;
-        xbu_c[e] += xbu; xbv_c[e] += xbv;
-        e1bu[e] = fma(l1, xbu, e1bu[e]); e1bv[e] = fma(l1, xbv, e1bv[e]);
-        e2bu[e] = fma(l2, xbu, e2bu[e]); e2bv[e] = fma(l2, xbv, e2bv[e]);
+      for (int e = 0; e < NS; ++e) {   // area = |cross| / 2, cell vertices, centroid
+        const double crb = 0.5 * (crs < 0.0 ? -arb[e] : arb[e]);
+        e1bu[e] += crb * e2v; e1bv[e] -= crb * e2u;
+        e2bu[e] -= crb * e1v; e2bv[e] += crb * e1u;
+        Rbu[e][ib] += e1bu[e]; Rbv[e][ib] += e1bv[e];
+        Rbu[e][iw] += e2bu[e]; Rbv[e][iw] += e2bv[e];
+        const double abu = xbu_c[e] - (e1bu[e] + e2bu[e]), abv = xbv_c[e] - (e1bv[e] + e2bv[e]);
+        if (nr == 3) { Rbu[e][0] += abu; Rbv[e][0] += abv; } else { cbu[e] += abu; cbv[e] += abv; }
       }
     }
-#pragma unroll
-    for (int e = 0; e < NS; ++e) {   // area = |cross| / 2, cell vertices, centroid
-      const double crb = 0.5 * (crs < 0.0 ? -arb[e] : arb[e]);
-      e1bu[e] += crb * e2v; e1bv[e] -= crb * e2u;
-      e2bu[e] -= crb * e1v; e2bv[e] += crb * e1u;
-      Rbu[e][ib] += e1bu[e]; Rbv[e][ib] += e1bv[e];
-      Rbu[e][iw] += e2bu[e]; Rbv[e][iw] += e2bv[e];
-      const double abu = xbu_c[e] - (e1bu[e] + e2bu[e]), abv = xbv_c[e] - (e1bv[e] + e2bv[e]);
-      if (nr == 3) { Rbu[e][0] += abu; Rbv[e][0] += abv; } else { cbu[e] += abu; cbv[e] += abv; }
-    }
+  }
+  if (!live) return;
+  if (!nonempty) {   // not reached for pairs the count pass found non-empty; blocks stay defined
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 24; ++k) kout[72 * a + k] = 0.0;
+    if (DUAL)
+      for (int e = 0; e < 4; ++e) g.Op[12 * p + 3 * e + cp] = 0.0;
+    return;
   }
   if (nr > 3) {
     const double inv = 1.0 / (double)nr;
@@ -270,8 +325,8 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, double* __rest
     for (int e = 0; e < 4; ++e) g.Op[12 * p + 3 * e + cp] = e < NS ? O[e] : 0.0;
 }
 
-// Persistent kernel over (warp batch of 32 R pairs, component) work items.
-// Each batch is sorted by cell count (ballot counting sort) before the sweep.
+// Persistent kernel over warp batches of 32 R pairs, each sorted by cell count
+// (ballot counting sort) and swept in rounds of 10 pairs x 3 components.
 template <int NS, int NM, bool SEG, bool DUAL, int R>
 __global__ void __launch_bounds__(kTanThreads) k_tangent_pairs(TanArgs g) {
   extern __shared__ double tan_acc[];
@@ -285,14 +340,14 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_pairs(TanArgs g) {
   DevStatus* st = g.st;
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
   const int64_t n = ok ? (int64_t)min((unsigned long long)g.pair_cap, st->n_pairs) : 0;
-  const int64_t items = 3 * ((n + B - 1) / B);
+  const int64_t items = (n + B - 1) / B;
+  GPX* gx = reinterpret_cast<GPX*>(tan_acc + 16 * 4 * kTanThreads) + 32 * (threadIdx.x >> 5);
   for (;;) {   // bounded: the shared counter only grows
     int64_t item = 0;
     if (lane == 0) item = (int64_t)atomicAdd(&st->work_ctr3, 1ull);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= items) break;
-    const int64_t base = (item / 3) * B;
-    const int cp = (int)(item % 3);
+    const int64_t base = item * B;
     int key[R];
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
@@ -325,9 +380,14 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_pairs(TanArgs g) {
     for (int rr = 0; rr < R; ++rr)
       if (key[rr] > 0) perm[pos[rr]] = (uint8_t)(rr * 32 + lane);
     __syncwarp();
-    for (int i0 = 0; i0 < n_live; i0 += 32) {
-      const int i = i0 + lane;
-      if (i < n_live) tangent_pair<NS, NM, SEG, DUAL>(g, base + perm[i], cp, acc, clip_over, newton_fail);
+    // rounds of 10 pairs: lanes 3 g .. 3 g + 2 take components 0..2 of pair g
+    const int grp = lane / 3, cp = lane - 3 * (lane / 3);
+    for (int i0 = 0; i0 < n_live; i0 += 10) {
+      const int i = i0 + grp;
+      const bool live = lane < 30 && i < n_live;
+      const int64_t p = base + perm[live ? i : i0];
+      tangent_pair<NS, NM, SEG, DUAL>(g, p, cp, live, acc, gx, clip_over, newton_fail);
+      __syncwarp();
     }
     __syncwarp();
   }
