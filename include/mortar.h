@@ -190,7 +190,8 @@ int mortar_csr_size(mortar_ctx* ctx, int32_t which, int64_t* nrows, int64_t* nco
 /* Copy a CSR matrix: rowptr (nrows + 1, int64), colidx (nnz, int32, sorted
  * within each row), vals (nnz, FP64).  capacity_nnz < nnz ->
  * MORTAR_ERR_CAPACITY.  A structural entry exists iff some non-empty pair
- * (or, for element-domain D, some slave element) touches it. */
+ * (or, for element-domain D, some slave element) touches it; element-domain D
+ * with dual LMs holds the diagonal only (int Phi_a N_b = delta_ab int N_b). */
 int mortar_csr_copy(mortar_ctx* ctx, int32_t which, int64_t* rowptr, int32_t* colidx, double* vals,
                     int64_t capacity_nnz, int32_t on_device);
 

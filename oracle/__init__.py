@@ -236,13 +236,16 @@ def _csr_from_triplets(rows, cols, vals, nrows, ncols):
     return sp.csr_matrix((sums, uc.astype(np.int32), rowptr), shape=(nrows, ncols))
 
 
-def assemble(itf, s, m, Mb, Db, nonempty, De=None, d_domain=0):
+def assemble(itf, s, m, Mb, Db, nonempty, De=None, d_domain=0, lm=None):
     """Assemble D (Ns x Ns) and M (Ns x Nm) CSR from element/pair blocks.
 
     A structural entry of M (and of D in segment mode) exists iff some
     non-empty pair touches it; in element mode every slave element contributes
-    its whole D_e block.  Values are summed in pair (or element) order.
-    """
+    its whole D_e block -- with dual LMs only its diagonal: the dual basis is
+    biorthogonal to the shape functions, int Phi_a N_b = delta_ab int N_b
+    (Sec. 2.2), so the off-diagonal entries are zero by definition.  Values are
+    summed in pair (or element) order."""
+    lm = itf.lm if lm is None else lm
     cs = np.asarray(itf.conn_s)
     cm = np.asarray(itf.conn_m)
     ns, nm = cs.shape[1], cm.shape[1]
@@ -258,6 +261,10 @@ def assemble(itf, s, m, Mb, Db, nonempty, De=None, d_domain=0):
         rows = np.repeat(cs[sk][:, :, None], ns, axis=2)
         cols = np.repeat(cs[sk][:, None, :], ns, axis=1)
         vals = Db[keep][:, :ns, :ns]
+    elif lm == 1:
+        rows = cs
+        cols = cs
+        vals = De[:, np.arange(ns), np.arange(ns)]
     else:
         rows = np.repeat(cs[:, :, None], ns, axis=2)
         cols = np.repeat(cs[:, None, :], ns, axis=1)
@@ -291,7 +298,7 @@ def evaluate(itf, opts: Opts | None = None, search: str = "binned", pairs=None) 
         s, m = search_binned(itf, o.delta)
     A, De = element_blocks(itf, o.lm)
     Mb, Db, ne, st = pair_blocks(itf, s, m, o)
-    D, M = assemble(itf, s, m, Mb, Db, ne, De, o.d_domain)
+    D, M = assemble(itf, s, m, Mb, Db, ne, De, o.d_domain, o.lm)
     return Result(s, m, Mb, Db, ne, A, De, D, M, st)
 
 
@@ -342,7 +349,7 @@ def evaluate_element_based(itf, n_rule: int = 8, opts: Opts | None = None, pairs
     s, m = pairs if pairs is not None else search_binned(itf, o.delta)
     _, De = element_blocks(itf, o.lm)
     Mb, Db, fl = element_based_blocks(itf, s, m, n_rule, o)
-    D, M = assemble(itf, s, m, Mb, Db, fl, De, o.d_domain)
+    D, M = assemble(itf, s, m, Mb, Db, fl, De, o.d_domain, o.lm)
     return D, M, (s, m), fl
 
 

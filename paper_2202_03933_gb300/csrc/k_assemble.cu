@@ -61,6 +61,7 @@ struct RowSource {
   const double* blk;       // De (per element) or Dblk / Mblk (per pair)
   const int32_t* conn_s;
   const int32_t* conn_m;
+  int diag_only;          // element-domain D with dual LMs: the diagonal only (biorthogonality)
 
   template <class F>
   __device__ __forceinline__ void visit(int64_t j, F&& f) const {
@@ -70,7 +71,10 @@ struct RowSource {
       const int64_t e = ee >> 2;
       const int a = (int)(ee & 3);
       if (WHICH == 0) {
-        for (int b = 0; b < NS; ++b) f(conn_s[NS * e + b], blk[16 * e + 4 * a + b]);
+        if (diag_only)
+          f(conn_s[NS * e + a], blk[16 * e + 4 * a + a]);
+        else
+          for (int b = 0; b < NS; ++b) f(conn_s[NS * e + b], blk[16 * e + 4 * a + b]);
       } else {
         const int64_t p0 = pair_off[e], p1 = pair_off[e + 1];
         for (int64_t p = p0; p < p1; ++p) {
@@ -203,10 +207,10 @@ template <int WHICHD, int NS, int NM>
 void assemble_t(mortar_ctx* c, const double* blkD) {
   RowSource<WHICHD, NS, NM> srcD{c->n2e_s_ptr.as<int64_t>(), c->n2e_s_ent.as<int64_t>(), c->pair_off.as<int64_t>(),
                                  c->pairs_m.as<int32_t>(), c->flag.as<uint8_t>(), blkD, c->conn_s.as<int32_t>(),
-                                 c->conn_m.as<int32_t>()};
+                                 c->conn_m.as<int32_t>(), WHICHD == 0 && c->opt.lm == MORTAR_LM_DUAL};
   RowSource<2, NS, NM> srcM{c->n2e_s_ptr.as<int64_t>(), c->n2e_s_ent.as<int64_t>(), c->pair_off.as<int64_t>(),
                             c->pairs_m.as<int32_t>(), c->flag.as<uint8_t>(), c->Mblk.as<double>(),
-                            c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>()};
+                            c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), 0};
   DevStatus* st = c->dstat.as<DevStatus>();
   const int64_t N = c->Ns;
   const unsigned g = (unsigned)((N + kThreads - 1) / kThreads);

@@ -238,12 +238,17 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     }
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) r[SR_A + 4 * a + b] = A[a][b];
-    // ---- element-domain D: De = sum_q w J Phi_a N_b = A Me
+    // ---- element-domain D: De = sum_q w J Phi_a N_b = A Me; with dual LMs
+    //      this is diag(Dh) exactly (biorthogonality), stored as such
     double* d = De + 16 * e;
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) {
         double v = 0.0;
-        for (int c = 0; c < NS; ++c) v += A[a][c] * Me[c][b];
+        if (rp.lm == 1) {
+          v = a == b ? Dh[a] : 0.0;
+        } else {
+          for (int c = 0; c < NS; ++c) v += A[a][c] * Me[c][b];
+        }
         d[4 * a + b] = (a < NS && b < NS) ? v : 0.0;
       }
     // ---- search box (delta-inflated) and diameter

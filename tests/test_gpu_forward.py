@@ -190,7 +190,7 @@ def _sampled_rows(orc, itf, s, m, rows, o):
     keep = touch[s]
     Mb, Db, ne, _ = orc.pair_blocks(itf, s[keep], m[keep], o)
     _, De = orc.element_blocks(itf, o.lm)
-    D, M = orc.assemble(itf, s[keep], m[keep], Mb, Db, ne, De, o.d_domain)
+    D, M = orc.assemble(itf, s[keep], m[keep], Mb, Db, ne, De, o.d_domain, o.lm)
     return D[rows], M[rows]
 
 
