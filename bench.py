@@ -18,6 +18,15 @@ path); value = all ranks' pairs / max-over-ranks time ("scaling": "weak").
 ``--impl reference`` times the CPU oracle (the only reference that exists for
 this method: the paper ships no code) on a bounded sample of the same
 workload, on the host cores.
+
+Besides the step, the JSON line carries (none of it inside the timed step):
+``forward_only`` (search + integration + assembly graph), ``element_based``
+(the same forward graph with the element-based rule, n = 4 and 8, and the
+deviation of its M from the segment-based M), ``dynamic`` (a master sliding
+0.3 h_m per step: device copy of the new coordinates + the full step, bins
+rebuilt every step), ``linearisation`` (the 3x3-block Jacobian of the weighted
+gap vector), ``fp64_probe`` (a DFMA chain: the measured FP64 rate), ``e2e``
+(the step through the C ABI with host buffers).
 """
 from __future__ import annotations
 
@@ -288,6 +297,7 @@ def run_batched(args, world, rank, local):
             "phases_ms": {"search": st["ms_search"], "integrate": st["ms_integrate"],
                           "assemble": st["ms_assemble"], "adjoint": st["ms_adjoint"]},
             "one_graph_per_interface_ms": round(ms_sep, 4), "batched_speedup": round(ms_sep / ms, 3),
+            "eta_t": round(float(st.get("eta_t", 0.0)), 4),
             "gpu_launches": int(st.get("graph_kernels", 0)) * args.steps,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]}}
     if rank == 0:
@@ -561,6 +571,7 @@ def run_ours(args, world, rank, local):
         "fp64_probe": probe,
         "e2e": e2e,
         "gpu_launches": int(st0.get("graph_kernels", 0)) * args.steps,
+        "eta_t": round(float(st.get("eta_t", 0.0)), 4),
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
     }
     if rank == 0 and not args.no_cpu_baseline:

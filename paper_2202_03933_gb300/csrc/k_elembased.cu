@@ -3,7 +3,8 @@
 // higher-order rule on the slave element copes with the kinks of the
 // integrand at master element edges, at lower accuracy).
 //
-// One thread per slave element.  Rule: n x n Gauss-Legendre points on quad4
+// One thread per slave element (points outermost, see the kernel).  Rule: n x n
+// Gauss-Legendre points on quad4
 // (collapsed n x n points on tri3), mapped into the element's auxiliary plane
 // by the projected slave map, weights w |det J_s|.  The element's candidate
 // pairs are visited in pair order; each takes the points not taken yet whose
@@ -27,6 +28,18 @@ constexpr int kThreads = 128;
 constexpr int kMaxRule = 16;
 constexpr double kInsideTol = 1e-10;
 
+constexpr int kChunk = 8;   // candidate pairs held per pass over the points
+
+// One thread per slave element, points outermost: for each rule point the
+// element's candidate pairs (a chunk of up to kChunk, with their projected
+// master maps kept in thread-local memory) are tried in pair order with a box
+// reject and the FP32 Newton iterate, and only the owner's FP64 step and the
+// point's contribution are computed.  The FP64 work then runs once per point
+// on every lane (interior elements own all points), instead of once per
+// (pair, point) behind lane-divergent tests.  Contributions are added into
+// the owner's block in global memory (this thread's own blocks, L1-resident)
+// in point order.  Elements with more than kChunk pairs take further passes
+// over the points not yet owned, so "first covering pair in pair order" holds.
 template <int NS, int NM, bool SEG, bool DUAL>
 __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
     const int64_t* __restrict__ pair_off, const int32_t* __restrict__ pm, const double* __restrict__ srec,
@@ -48,17 +61,28 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
     const double x0x = r[SR_X0], x0y = r[SR_X0 + 1], x0z = r[SR_X0 + 2];
     const double t1x = r[SR_T1], t1y = r[SR_T1 + 1], t1z = r[SR_T1 + 2];
     const double t2x = r[SR_T2], t2y = r[SR_T2 + 1], t2z = r[SR_T2 + 2];
+    double Phi_c[4][4];   // dual: Phi_a = sum_c A[a][c] N_c
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Phi_c[a][c] = r[SR_A + 4 * a + c];
     uint32_t taken[kMaxRule * kMaxRule / 32];
 #pragma unroll
     for (int k = 0; k < kMaxRule * kMaxRule / 32; ++k) taken[k] = 0u;
-    for (int64_t p = p0; p < p1; ++p) {
-      double M[4][4], D[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) { M[a][b] = 0.0; D[a][b] = 0.0; }
-      int got = 0;
-      if (live) {
+    for (int64_t c0 = p0; c0 < p1; c0 += kChunk) {
+      const int kc = (int)min((int64_t)kChunk, p1 - c0);
+      MapInverse mic[kChunk];
+      float box[kChunk][4];
+      int got[kChunk];
+      for (int k = 0; k < kc; ++k) {
+        got[k] = 0;
+        const int64_t p = c0 + k;
+        double* mo = Mblk + 16 * p;
+        for (int t = 0; t < 16; ++t) mo[t] = 0.0;
+        if (SEG) {
+          double* dout = Dblk + 16 * p;
+          for (int t = 0; t < 16; ++t) dout[t] = 0.0;
+        }
         const int32_t m = pm[p];
         double mu[4], mv[4];
         double lo_u = 1e300, hi_u = -1e300, lo_v = 1e300, hi_v = -1e300;
@@ -71,13 +95,15 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
           lo_u = fmin(lo_u, mu[l]); hi_u = fmax(hi_u, mu[l]);
           lo_v = fmin(lo_v, mv[l]); hi_v = fmax(hi_v, mv[l]);
         }
-        // box of the projected master element, widened far beyond the
-        // inside tolerance: a quick reject only
-        const double band = 1e-6 * fmax(hi_u - lo_u, hi_v - lo_v);
-        lo_u -= band; hi_u += band; lo_v -= band; hi_v += band;
+        // box of the projected master element in FP32, widened far beyond the
+        // inside tolerance and the FP32 rounding of the test point: a quick reject only
+        const double band = 1e-4 * fmax(hi_u - lo_u, hi_v - lo_v);
+        box[k][0] = (float)(lo_u - band); box[k][1] = (float)(hi_u + band);
+        box[k][2] = (float)(lo_v - band); box[k][3] = (float)(hi_v + band);
         const PlaneMap mmap = plane_map<NM>(mu, mv);
-        MapInverse mi;
-        mi.setup(mmap, NM == 3 || map_is_affine(mmap));
+        mic[k].setup(mmap, NM == 3 || map_is_affine(mmap));
+      }
+      if (live) {
         for (int q = 0; q < nq; ++q) {
           if ((taken[q >> 5] >> (q & 31)) & 1u) continue;
           const int i = q / n, j = q - (q / n) * n;
@@ -86,31 +112,41 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
             xi = rule[i]; eta = rule[j];
             wq = rule[n + i] * rule[n + j];
           } else {
-            const double s = 0.5 * (rule[i] + 1.0), t = 0.5 * (rule[j] + 1.0);
-            xi = s; eta = t * (1.0 - s);
+            const double s = 0.5 * (rule[i] + 1.0), tt = 0.5 * (rule[j] + 1.0);
+            xi = s; eta = tt * (1.0 - s);
             wq = 0.25 * rule[n + i] * rule[n + j] * (1.0 - s);
           }
           const double xe = xi * eta;
           const double xu = smap.c0u + smap.c1u * xi + smap.c2u * eta + smap.c3u * xe;
           const double xv = smap.c0v + smap.c1v * xi + smap.c2v * eta + smap.c3v * xe;
-          if (xu < lo_u || xu > hi_u || xv < lo_v || xv > hi_v) continue;
-          double m1, m2;
-          if (mi.affine) {
-            mi.solve(xu, xv, m1, m2);
-          } else {   // FP32 iterate first: points clearly outside skip the FP64 step
-            if (!mi.coarse(xu, xv, m1, m2)) continue;
-            const bool near = NM == 4
-                ? (fabs(m1) <= 1.0 + 1e-5 && fabs(m2) <= 1.0 + 1e-5)
-                : (m1 >= -1e-5 && m2 >= -1e-5 && m1 + m2 <= 1.0 + 1e-5);
-            if (!near) continue;
-            mi.polish(xu, xv, m1, m2);
+          const float fu = (float)xu, fv = (float)xv;
+          int owner = -1;
+          double m1 = 0.0, m2 = 0.0;
+          for (int k = 0; k < kc && owner < 0; ++k) {
+            if (fu < box[k][0] || fu > box[k][1] || fv < box[k][2] || fv > box[k][3]) continue;
+            const MapInverse& mi = mic[k];
+            double a1, a2;
+            if (mi.affine) {
+              mi.solve(xu, xv, a1, a2);
+            } else {   // FP32 iterate first: points clearly outside skip the FP64 step
+              if (!mi.coarse(xu, xv, a1, a2)) continue;
+              const bool near = NM == 4
+                  ? (fabs(a1) <= 1.0 + 1e-5 && fabs(a2) <= 1.0 + 1e-5)
+                  : (a1 >= -1e-5 && a2 >= -1e-5 && a1 + a2 <= 1.0 + 1e-5);
+              if (!near) continue;
+              mi.polish(xu, xv, a1, a2);
+            }
+            const bool inside = NM == 4
+                ? (fabs(a1) <= 1.0 + kInsideTol && fabs(a2) <= 1.0 + kInsideTol)
+                : (a1 >= -kInsideTol && a2 >= -kInsideTol && a1 + a2 <= 1.0 + kInsideTol);
+            if (!inside) continue;
+            owner = k;
+            m1 = a1;
+            m2 = a2;
           }
-          const bool inside = NM == 4
-              ? (fabs(m1) <= 1.0 + kInsideTol && fabs(m2) <= 1.0 + kInsideTol)
-              : (m1 >= -kInsideTol && m2 >= -kInsideTol && m1 + m2 <= 1.0 + kInsideTol);
-          if (!inside) continue;
+          if (owner < 0) continue;
           taken[q >> 5] |= 1u << (q & 31);
-          ++got;
+          got[owner] += 1;
           const double j00 = smap.c1u + smap.c3u * eta, j01 = smap.c2u + smap.c3u * xi;
           const double j10 = smap.c1v + smap.c3v * eta, j11 = smap.c2v + smap.c3v * xi;
           const double W = wq * fabs(j00 * j11 - j01 * j10);
@@ -122,39 +158,31 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
             double v = 0.0;
             if (DUAL) {
 #pragma unroll
-              for (int c = 0; c < NS; ++c) v = fma(r[SR_A + 4 * a + c], Ns[c], v);
+              for (int c = 0; c < NS; ++c) v = fma(Phi_c[a][c], Ns[c], v);
             } else {
               v = Ns[a];
             }
             Phi[a] = W * v;
           }
+          double* mo = Mblk + 16 * (c0 + owner);
 #pragma unroll
-          for (int a = 0; a < NS; ++a) {
+          for (int a = 0; a < NS; ++a)
 #pragma unroll
-            for (int l = 0; l < NM; ++l) M[a][l] = fma(Phi[a], Nm[l], M[a][l]);
-            if (SEG)
+            for (int l = 0; l < NM; ++l) mo[4 * a + l] = fma(Phi[a], Nm[l], mo[4 * a + l]);
+          if (SEG) {
+            double* dout = Dblk + 16 * (c0 + owner);
 #pragma unroll
-              for (int b = 0; b < NS; ++b) D[a][b] = fma(Phi[a], Ns[b], D[a][b]);
+            for (int a = 0; a < NS; ++a)
+#pragma unroll
+              for (int b = 0; b < NS; ++b) dout[4 * a + b] = fma(Phi[a], Ns[b], dout[4 * a + b]);
           }
         }
       }
-      double2* mo = reinterpret_cast<double2*>(Mblk + 16 * p);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        mo[2 * a] = make_double2(M[a][0], M[a][1]);
-        mo[2 * a + 1] = make_double2(M[a][2], M[a][3]);
+      for (int k = 0; k < kc; ++k) {
+        flag[c0 + k] = got[k] > 0 ? 1 : 0;
+        n_live += got[k] > 0 ? 1 : 0;
+        n_gp += (unsigned long long)got[k];
       }
-      if (SEG) {
-        double2* dout = reinterpret_cast<double2*>(Dblk + 16 * p);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          dout[2 * a] = make_double2(D[a][0], D[a][1]);
-          dout[2 * a + 1] = make_double2(D[a][2], D[a][3]);
-        }
-      }
-      flag[p] = got > 0 ? 1 : 0;
-      n_live += got > 0 ? 1 : 0;
-      n_gp += (unsigned long long)got;
     }
   }
   block_count_add(&st->nonempty, n_live);
