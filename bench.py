@@ -206,6 +206,32 @@ def cpu_baseline(itf, target_s: float = 12.0) -> dict:
                       f"forward-mode gradient, {dt:.1f} s on {threads} host threads"}
 
 
+def oracle_sample_extra(itf, rows: int = 2) -> dict:
+    """Oracle timings beside the extra bench sections, on the slave elements of
+    `rows` element rows against all master elements: the linearisation
+    (forward-mode Dual<24> blocks + assembly) and element-based integration
+    (n = 8), each in pairs per second on all host cores."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_2202_03933_gb300 import inputs
+    threads = os.cpu_count() or 1
+    n = int(round(len(itf.conn_s) ** 0.5))
+    ne = rows * n
+    sub = inputs.Interface("sample", itf.xs, itf.conn_s[:ne], itf.type_s, itf.xm, itf.conn_m, itf.type_m,
+                           lm=itf.lm, delta=itf.delta)
+    o = oracle.make_opts(lm=itf.lm, delta=itf.delta, n_threads=threads)
+    s, m = oracle.search_binned(sub, o.delta)
+    t0 = time.perf_counter()
+    oracle.tangent(sub, s, m, sub.xs, sub.xm, o, add_direct=True)
+    t_lin = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.evaluate_element_based(sub, 8, o, pairs=(s, m))
+    t_eb = time.perf_counter() - t0
+    what = f"{ne} of {len(itf.conn_s)} slave elements ({rows} element rows), {s.size} pairs, {threads} host threads"
+    return {"linearisation": {"pairs_per_s": s.size / t_lin, "s": round(t_lin, 2), "sample": what},
+            "element_based_n8": {"pairs_per_s": s.size / t_eb, "s": round(t_eb, 2), "sample": what}}
+
+
 def run_reference(args, world, rank):
     """--impl reference: the CPU oracle on a bounded sample per step."""
     if rank != 0:
@@ -576,6 +602,10 @@ def run_ours(args, world, rank, local):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(itf)
+        try:
+            line["oracle_beside_sections"] = oracle_sample_extra(itf)
+        except Exception as ex_:   # reported, not fatal
+            line["oracle_beside_sections"] = {"error": str(ex_)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
