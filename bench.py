@@ -200,10 +200,13 @@ def cpu_baseline(itf, target_s: float = 12.0) -> dict:
     pairs, dt, ne = oracle_sample_step(itf, 2, threads)
     rows = max(2, min(200, int(2 * target_s / max(dt, 1e-3))))
     pairs, dt, ne = oracle_sample_step(itf, rows, threads)
+    p1, d1, _ = oracle_sample_step(itf, 1, 1)   # one host thread, one element row
     return {"value": pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{ne} of {len(itf.conn_s)} slave elements ({rows} element rows) x all master "
                       f"elements: {pairs} pairs; oracle search + integration + assembly + "
-                      f"forward-mode gradient, {dt:.1f} s on {threads} host threads"}
+                      f"forward-mode gradient, {dt:.1f} s on {threads} host threads",
+            "single_thread": {"value": p1 / d1, "unit": UNIT, "cores": 1,
+                              "sample": f"1 element row, {p1} pairs, {d1:.1f} s"}}
 
 
 def oracle_sample_extra(itf, rows: int = 2) -> dict:
@@ -399,6 +402,24 @@ def run_ours(args, world, rank, local):
     if ex["dram_bytes"]:
         roof["traffic"] = int(ex["dram_bytes"] * n_pairs)
 
+    # ---- HBM rates of the two memory-bound phases (algorithmic bytes / phase
+    #      time): search = element boxes read (64 B per element, both sides) +
+    #      master keys and bin lists (16 B per master element) + pairs written
+    #      (8 B each) + per-slave counts and offsets (12 B per slave element);
+    #      assembly = per-pair M blocks and flags read (129 B per pair) + element
+    #      D blocks read (128 B per slave element) + CSR of D and M written
+    #      (12 B per entry, 16 B per row)
+    try:
+        n_nzD, n_nzM = m.csr_size(mortar.MATRIX_D)[2], m.csr_size(mortar.MATRIX_M)[2]
+        Es_, Em_ = itf.conn_s.shape[0], itf.conn_m.shape[0]
+        b_search = 64 * (Es_ + Em_) + 16 * Em_ + 8 * n_pairs + 12 * Es_
+        b_asm = 129 * n_pairs + 128 * Es_ + 12 * (n_nzD + n_nzM) + 16 * itf.xs.shape[0]
+        phase_bw = {"search_GBps": round(b_search / (mean(t_srch) / 1e3) / 1e9, 1),
+                    "assemble_GBps": round(b_asm / (mean(t_asm) / 1e3) / 1e9, 1),
+                    "hbm_peak_GBps": "6678 (measured copy; the phases are gathers, latency-bound)"}
+    except Exception as ex_:   # reported, not fatal
+        phase_bw = {"error": str(ex_)}
+
     # ---- forward only (integration kernel alone): forward pairs/s and its
     #      algorithmic rate (oracle-counted flops / kernel time)
     fwd = None
@@ -589,6 +610,7 @@ def run_ours(args, world, rank, local):
                       "adjoint_rest": round(mean(t_adj) - mean(t_adjp), 4),
                       "adjoint_pairs_separate": round(mean(t_adjp), 4), "graph_total": round(mean(per_step), 4)},
         "autotune": pick,
+        "phase_bandwidth": phase_bw,
         "forward_only": fwd,
         "linearisation": lin,
         "element_based": ebi,

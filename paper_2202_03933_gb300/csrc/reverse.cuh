@@ -12,7 +12,7 @@
 
 namespace mortar {
 
-constexpr int kPolyA = 12;   // vertex cap per recorded clipping stage (convex quads need <= 8)
+constexpr int kPolyA = 10;   // vertex cap per recorded clipping stage (convex polygons need <= 8)
 
 struct V3 {
   double x, y, z;
