@@ -89,12 +89,6 @@ __global__ void k_check_conn(const int32_t* __restrict__ conn, int nen, const in
   }
 }
 
-// ---- coordinate check: finite values only
-__global__ void k_check_finite(const double* __restrict__ x, int64_t n, unsigned long long* __restrict__ bad) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && !isfinite(x[i])) atomicAdd(bad, 1ull);
-}
-
 int alloc_pair_buffers(mortar_ctx* c, int64_t cap) {
   const size_t n = (size_t)std::max<int64_t>(cap, 1);
   MORTAR_TRY(buf_reserve(c->pairs_s, n * 4));
