@@ -42,6 +42,7 @@ def test_host_only_calls(native):
     assert L.mortar_default_options(ctypes.byref(o)) == 0
     assert o.newton_max_iter == 20 and o.newton_tol == 1e-14 and o.search_inflation == 1e-9
     assert o.clip_tol_rel == 1e-12 and o.merge_tol_rel == 1e-10 and o.area_tol_rel == 1e-14
+    assert o.bin_margin == 0.0 and o.integration == 0 and o.element_rule_n == 8 and o.facing_test == 0
     assert L.mortar_default_options(None) == -1
     assert L.mortar_status_string(-4) == b"MORTAR_ERR_CAPACITY"
     assert L.mortar_status_string(0) == b"MORTAR_OK"
