@@ -395,11 +395,16 @@ def run_ours(args, world, rank, local):
             "peak_kind": "derived FP64: 152 SM x 4 flop/clk x 2070 MHz (of derived; measured probe below)",
             "flops": "executed FP64 (ncu 2 DFMA + DADD + DMUL per pair, planar_600x520) x pairs",
             "achieved": None, "frac": None, "traffic": None}
-    if ex["flops"]:
+    # the per-pair counters were taken on the planar quad4/quad4 dual family;
+    # other element types execute other per-pair work, so they get no fraction
+    same_family = args.workload.startswith("planar_") and itf.lm == 1
+    if ex["flops"] and same_family:
         achieved = ex["flops"] * n_pairs / (ms_pair / 1e3) / 1e12
         roof.update(achieved=round(achieved, 4), frac=round(achieved / FP64_PEAK_TFLOPS, 4),
                     flops_per_pair=ex["flops"])
-    if ex["dram_bytes"]:
+    elif ex["flops"]:
+        roof["note"] = "executed FP64 per pair measured on the planar quad4/quad4 dual family only"
+    if ex["dram_bytes"] and same_family:
         roof["traffic"] = int(ex["dram_bytes"] * n_pairs)
 
     # ---- HBM rates of the two memory-bound phases (algorithmic bytes / phase
