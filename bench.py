@@ -384,7 +384,8 @@ def run_ours(args, world, rank, local):
     n_pairs = st["n_pairs"]
     value = weak_value(world, n_pairs, ms)
 
-    mean = lambda v: sum(v) / len(v)  # noqa: E731
+    # per-phase figures: median over the timed steps (CUDA events in the graph)
+    mean = statistics.median
     ms_pair = mean(t_int)   # the pair kernel that produced the forward blocks (fused with the adjoint)
     fused = bool(st.get("fused", 0))
     # ---- roofline of the dominant kernel: executed FP64 flops / its CUDA-event time
