@@ -385,8 +385,8 @@ def run_ours(args, world, rank, local):
     value = weak_value(world, n_pairs, ms)
 
     # per-phase figures: median over the timed steps (CUDA events in the graph)
-    mean = statistics.median
-    ms_pair = mean(t_int)   # the pair kernel that produced the forward blocks (fused with the adjoint)
+    med = statistics.median
+    ms_pair = med(t_int)   # the pair kernel that produced the forward blocks (fused with the adjoint)
     fused = bool(st.get("fused", 0))
     # ---- roofline of the dominant kernel: executed FP64 flops / its CUDA-event time
     ex = EXEC_PER_PAIR["fused" if fused else "integrate"]
@@ -420,8 +420,8 @@ def run_ours(args, world, rank, local):
         Es_, Em_ = itf.conn_s.shape[0], itf.conn_m.shape[0]
         b_search = 64 * (Es_ + Em_) + 16 * Em_ + 8 * n_pairs + 12 * Es_
         b_asm = 129 * n_pairs + 128 * Es_ + 12 * (n_nzD + n_nzM) + 16 * itf.xs.shape[0]
-        phase_bw = {"search_GBps": round(b_search / (mean(t_srch) / 1e3) / 1e9, 1),
-                    "assemble_GBps": round(b_asm / (mean(t_asm) / 1e3) / 1e9, 1),
+        phase_bw = {"search_GBps": round(b_search / (med(t_srch) / 1e3) / 1e9, 1),
+                    "assemble_GBps": round(b_asm / (med(t_asm) / 1e3) / 1e9, 1),
                     "hbm_peak_GBps": "6678 (measured copy; the phases are gathers, latency-bound)"}
     except Exception as ex_:   # reported, not fatal
         phase_bw = {"error": str(ex_)}
@@ -443,10 +443,10 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         ms_f = g0.elapsed_time(g1) / args.steps
         fwd = {"ms_per_step": round(ms_f, 4), "pairs_per_s": world * n_pairs / (ms_f / 1e3),
-               "ms_integrate": round(mean(t_fi), 4)}
+               "ms_integrate": round(med(t_fi), 4)}
         af = ALGO_FLOPS.get(args.workload)
         if af and af["pairs"] == n_pairs:
-            a = af["flops"] / (mean(t_fi) / 1e3) / 1e12
+            a = af["flops"] / (med(t_fi) / 1e3) / 1e12
             fwd["integration_algorithmic"] = {
                 "tflops": round(a, 4), "frac_of_derived_peak": round(a / FP64_PEAK_TFLOPS, 4),
                 "flops_per_launch": af["flops"],
@@ -518,7 +518,7 @@ def run_ours(args, world, rank, local):
             ms_e = e0.elapsed_time(e1) / args.steps
             Me = me.scipy(mortar.MATRIX_M)
             dev = abs(Me - ref).max() / abs(ref).max()
-            ebi[f"n{n_r}"] = {"forward_ms_per_step": round(ms_e, 3), "ms_integrate": round(mean(t_e), 3),
+            ebi[f"n{n_r}"] = {"forward_ms_per_step": round(ms_e, 3), "ms_integrate": round(med(t_e), 3),
                              "pairs_per_s": world * n_pairs / (ms_e / 1e3),
                              "max_rel_dev_M_vs_segment": float(dev), "sum_M": float(Me.sum())}
             me.close()
@@ -538,7 +538,7 @@ def run_ours(args, world, rank, local):
             m.tangent(xs, xm, add_direct=True, out_device=True)
             t_l.append(m.stats()["ms_tangent"])
         sl = m.stats()
-        lin = {"ms": round(mean(t_l), 3), "pairs_per_s": world * n_pairs / (mean(t_l) / 1e3),
+        lin = {"ms": round(med(t_l), 3), "pairs_per_s": world * n_pairs / (med(t_l) / 1e3),
                "blocks_3x3": sl["nnzb_K"],
                "what": "K = d/dX[(D (x) I3) Xs - (M (x) I3) Xm] + [D (x) I3 | -M (x) I3]: pair blocks, "
                        "element blocks, BSR assembly"}
@@ -611,10 +611,10 @@ def run_ours(args, world, rank, local):
                    "step": "search + integrate + assemble D,M + adjoint, one CUDA graph",
                    "l2": "inputs and workspaces (~GBs) larger than the 129 MB L2; no flush",
                    "parallelism": f"replicas x{world}"},
-        "phases_ms": {"search": round(mean(t_srch), 4), "pair_kernel": round(ms_pair, 4),
-                      "fused_forward_adjoint": fused, "assemble": round(mean(t_asm), 4),
-                      "adjoint_rest": round(mean(t_adj) - mean(t_adjp), 4),
-                      "adjoint_pairs_separate": round(mean(t_adjp), 4), "graph_total": round(mean(per_step), 4)},
+        "phases_ms": {"search": round(med(t_srch), 4), "pair_kernel": round(ms_pair, 4),
+                      "fused_forward_adjoint": fused, "assemble": round(med(t_asm), 4),
+                      "adjoint_rest": round(med(t_adj) - med(t_adjp), 4),
+                      "adjoint_pairs_separate": round(med(t_adjp), 4), "graph_total": round(med(per_step), 4)},
         "autotune": pick,
         "phase_bandwidth": phase_bw,
         "forward_only": fwd,
