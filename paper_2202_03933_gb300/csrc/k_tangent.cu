@@ -726,7 +726,8 @@ void launch_pairs_t(mortar_ctx* c) {
             c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->tan_ys.as<double>(),
             c->tan_ym.as<double>(), c->tan_Kp.as<double>(), c->tan_Op.as<double>(), c->tan_pair_cap,
             c->dstat.as<DevStatus>()};
-  auto kern = k_tangent_pairs<NS, NM, SEG, DUAL, 2>;
+  // batches of 160 pairs: 16 full rounds of 10 pair groups (lanes 30, 31 idle)
+  auto kern = k_tangent_pairs<NS, NM, SEG, DUAL, 5>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTanSmem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTanThreads, kTanSmem);
