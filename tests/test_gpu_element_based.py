@@ -109,3 +109,26 @@ def test_element_based_sampled_rows_planar_600x520(mt, orc):
         g, rr = G.getrow(j), R.getrow(j)
         assert np.array_equal(g.indices, rr.indices), j
         assert np.abs(g.data - rr.data).max() <= 1e-12 * max(np.abs(rr.data).max(), 1e-2 * scale), j
+
+
+def test_element_based_batched(mt, orc):
+    """A batch of independent interfaces: M equals the oracle's element-based M
+    on the concatenated meshes (no pair crosses interfaces)."""
+    itfs = inputs.batched_512(n_interfaces=6, n_hi=10.0)
+    m = mt.Mortar(lm=0, d_domain=0, delta=1e-9, integration=mt.INTEGRATE_ELEMENT, element_rule_n=5)
+    m.set_batch(itfs)
+    m.evaluate()
+    xs = np.concatenate([i.xs for i in itfs])
+    xm = np.concatenate([i.xm for i in itfs])
+    cs, cm, ns, nm = [], [], 0, 0
+    for i in itfs:
+        cs.append(i.conn_s + ns)
+        cm.append(i.conn_m + nm)
+        ns += i.xs.shape[0]
+        nm += i.xm.shape[0]
+    big = inputs.Interface("cat", xs, np.concatenate(cs).astype(np.int32), inputs.QUAD4, xm,
+                           np.concatenate(cm).astype(np.int32), inputs.QUAD4, lm=0, delta=1e-9)
+    s, mm = m.pairs()
+    D, M, _, _ = orc.evaluate_element_based(big, 5, orc.make_opts(lm=0, delta=1e-9), pairs=(s, mm))
+    csr_parity(m.scipy(mt.MATRIX_M), M)
+    csr_parity(m.scipy(mt.MATRIX_D), D)
