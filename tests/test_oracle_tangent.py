@@ -29,6 +29,14 @@ def _case(orc, name):
         itf.xm[:, :2] = 0.5 + 1.08 * (itf.xm[:, :2] - 0.5)
         itf.xs[:, 2] = 2e-3 * inputs.uniform(7, 1, itf.xs.shape[0], -1, 1)   # warped slave quads
         o = orc.make_opts(lm=0, d_domain=1, delta=4e-3)
+    elif name == "tri_slave_dual_seg":
+        base = inputs.mixed_tri(4, 3, lm=1, name="tsd")
+        itf = inputs.Interface("swap", base.xm, base.conn_m, base.type_m, base.xs, base.conn_s, base.type_s,
+                               lm=1, delta=1e-9)
+        # master (now the quad grid) stretched beyond the slave: no coincident boundary edges
+        itf.xm = itf.xm.copy()
+        itf.xm[:, :2] = 0.5 + 1.2 * (itf.xm[:, :2] - 0.5)
+        o = orc.make_opts(lm=1, d_domain=1, delta=1e-9)
     else:
         itf = inputs.cylinder_patch(4, 3, name="cyl_tiny")
         th = np.arctan2(itf.xm[:, 1], itf.xm[:, 0])
@@ -40,7 +48,7 @@ def _case(orc, name):
     return itf, o, s, m
 
 
-CASES = ["mixed_std_elem", "noisy_dual_seg", "noisy_std_seg_warped", "cylinder_dual_elem"]
+CASES = ["mixed_std_elem", "noisy_dual_seg", "noisy_std_seg_warped", "cylinder_dual_elem", "tri_slave_dual_seg"]
 
 
 def _G(orc, itf, o, s, m, ys, ym):
