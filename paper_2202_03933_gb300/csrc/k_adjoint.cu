@@ -748,7 +748,16 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
       for (int b = 0; b < NS; ++b) Me[a][b] += wj * N[a] * N[b];
     }
   }
-  if (ELEMD) {
+  if (ELEMD && DUAL) {
+    // dual LMs: De = A Me = diag(Dh) exactly, J_e = sum_a Dh_a (lam_a . X_a)
+    for (int a = 0; a < NS; ++a) {
+      const double dla = dot(lam[a], X[a]);
+      const double dab = De[16 * e + 5 * a];
+      Je += dab * dla;
+      Xb[a] = Xb[a] + dab * lam[a];
+      Dhb[a] += dla;
+    }
+  } else if (ELEMD) {
     // J_e = sum_ab (lam_a . X_b) De_ab with De = A Me
     for (int a = 0; a < NS; ++a)
       for (int b = 0; b < NS; ++b) {
