@@ -20,6 +20,7 @@ __device__ __forceinline__ int clip_polygon(const double* __restrict__ r, const 
                                             unsigned long long& clip_over) {
   const double eps_in = r[SR_EPSIN];
   if (!(eps_in >= 0.0)) return 0;
+  const long long eps_bits = __double_as_longlong(eps_in);
   const double x0x = r[SR_X0], x0y = r[SR_X0 + 1], x0z = r[SR_X0 + 2];
   const double t1x = r[SR_T1], t1y = r[SR_T1 + 1], t1z = r[SR_T1 + 2];
   const double t2x = r[SR_T2], t2y = r[SR_T2 + 1], t2z = r[SR_T2 + 2];
@@ -48,12 +49,17 @@ __device__ __forceinline__ int clip_polygon(const double* __restrict__ r, const 
     const int i1 = i + 1 == NS ? 0 : i + 1;
     const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
     const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
-    for (int k = 0; k < n; ++k) d[k] = cross2(eu, ev, Wu[k] - au, Wv[k] - av);
+    int side[kMaxPoly];
+    for (int k = 0; k < n; ++k) {
+      d[k] = cross2(eu, ev, Wu[k] - au, Wv[k] - av);
+      side[k] = band_side(d[k], eps_bits);
+    }
     int o = 0;
     for (int k = 0; k < n; ++k) {
       const int k1 = k + 1 == n ? 0 : k + 1;
       const double dp = d[k], dq = d[k1];
-      if ((dp > eps_in && dq < -eps_in) || (dp < -eps_in && dq > eps_in)) {
+      const int sp = side[k], sq = side[k1];
+      if ((sp == 1 && sq == -1) || (sp == -1 && sq == 1)) {   // dp, dq beyond the band on both sides
         const double t = dp / (dp - dq);
         if (o < kMaxPoly) {
           Qu[o] = Wu[k] + t * (Wu[k1] - Wu[k]);
@@ -61,7 +67,7 @@ __device__ __forceinline__ int clip_polygon(const double* __restrict__ r, const 
         }
         ++o;
       }
-      if (dq >= -eps_in) {
+      if (sq == 0 || sq == 1) {   // dq >= -eps_in
         if (o < kMaxPoly) { Qu[o] = Wu[k1]; Qv[o] = Wv[k1]; }
         ++o;
       }

@@ -97,6 +97,19 @@ __device__ __forceinline__ double cross2(double au, double av, double bu, double
   return au * bv - av * bu;
 }
 
+// Side of a signed distance d with respect to the inside band [-eps, eps]
+// (eps finite, >= 0): 1 if d > eps, -1 if d < -eps, 0 inside the band, 2 for
+// NaN.  Decided with integer compares on the IEEE bit patterns (sign and
+// magnitude order equal the numeric order for finite values), so the result
+// is exactly that of the FP64 comparisons while keeping them off the FP64 pipe.
+__device__ __forceinline__ int band_side(double d, long long eps_bits) {
+  const long long b = __double_as_longlong(d);
+  const long long mag = b & 0x7fffffffffffffffLL;
+  if (mag > 0x7ff0000000000000LL) return 2;
+  if (mag <= eps_bits) return 0;
+  return b < 0 ? -1 : 1;
+}
+
 template <int NEN>
 __device__ __forceinline__ void shape_fn(double xi, double eta, double N[4]) {
   if constexpr (NEN == 4) {

@@ -90,6 +90,7 @@ struct ClipRec {
   __device__ __forceinline__ bool run(const double* __restrict__ r, const double* mu, const double* mv, bool mrev,
                                       unsigned long long& clip_over) {
     const double eps_in = r[SR_EPSIN];
+    const long long eps_bits = __double_as_longlong(eps_in >= 0.0 ? eps_in : 0.0);
     for (int k = 0; k < NM; ++k) {
       const int l = mrev ? NM - 1 - k : k;
       Vu[0][k] = mu[l];
@@ -104,12 +105,17 @@ struct ClipRec {
       const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
       const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
       double d[kPolyA];
-      for (int k = 0; k < n; ++k) d[k] = cross2(eu, ev, Vu[i][k] - au, Vv[i][k] - av);
+      int side[kPolyA];
+      for (int k = 0; k < n; ++k) {
+        d[k] = cross2(eu, ev, Vu[i][k] - au, Vv[i][k] - av);
+        side[k] = band_side(d[k], eps_bits);
+      }
       int o = 0;
       for (int k = 0; k < n; ++k) {
         const int k1 = k + 1 == n ? 0 : k + 1;
         const double dp = d[k], dq = d[k1];
-        if ((dp > eps_in && dq < -eps_in) || (dp < -eps_in && dq > eps_in)) {
+        const int sp = side[k], sq = side[k1];
+        if ((sp == 1 && sq == -1) || (sp == -1 && sq == 1)) {   // dp, dq beyond the band on both sides
           const double t = dp / (dp - dq);
           if (o < kPolyA) {
             Vu[i + 1][o] = Vu[i][k] + t * (Vu[i][k1] - Vu[i][k]);
@@ -119,7 +125,7 @@ struct ClipRec {
           }
           ++o;
         }
-        if (dq >= -eps_in) {
+        if (sq == 0 || sq == 1) {   // dq >= -eps_in
           if (o < kPolyA) {
             Vu[i + 1][o] = Vu[i][k1];
             Vv[i + 1][o] = Vv[i][k1];
