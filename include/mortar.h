@@ -252,7 +252,11 @@ int mortar_tangent_copy(mortar_ctx* ctx, int64_t* rowptr, int32_t* colidx, doubl
  *   c > 0: active (bytes) = lambda_n + c g < 0, ncp = lambda_n - min(0, lambda_n + c g)
  *   (zero exactly where the conditions hold).
  * Any output may be NULL; lambda_n NULL skips active / ncp.  Evaluates first
- * if the last evaluation is stale. */
+ * if the last evaluation is stale (its status, e.g. MORTAR_ERR_NEWTON, is
+ * returned).  Caller-owned buffers; on_device says where all of them live.
+ * MORTAR_ERR_INVALID_ARG for lambda_n with c <= 0 (or NaN), MORTAR_ERR_STATE
+ * without an interface.  The facing test (mortar_options.facing_test) acts
+ * on the candidate pairs of the search and so on D and M themselves. */
 int mortar_contact_terms(mortar_ctx* ctx, const double* lambda_n, double c, double* normals, double* gap,
                          uint8_t* active, double* ncp, int32_t on_device);
 
