@@ -458,7 +458,7 @@ def run_ours(args, world, rank, local):
     #      0.3 h_m per step in-plane; each step uploads the new master
     #      coordinates (device copy) and replays the forward + adjoint graph,
     #      which re-bins and re-searches from scratch; bins carry the
-    #      2 dt |v| margin of Sec. 3.3
+    #      2 dt |v| margin of Sec. 3.5
     dyn = None
     try:
         K = max(min(args.steps, 8), 2)
@@ -517,10 +517,10 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize()
             ms_e = e0.elapsed_time(e1) / args.steps
             Me = me.scipy(mortar.MATRIX_M)
-            dev = abs(Me - ref).max() / abs(ref).max()
+            dev_M = abs(Me - ref).max() / abs(ref).max()
             ebi[f"n{n_r}"] = {"forward_ms_per_step": round(ms_e, 3), "ms_integrate": round(med(t_e), 3),
                              "pairs_per_s": world * n_pairs / (ms_e / 1e3),
-                             "max_rel_dev_M_vs_segment": float(dev), "sum_M": float(Me.sum())}
+                             "max_rel_dev_M_vs_segment": float(dev_M), "sum_M": float(Me.sum())}
             me.close()
         ebi["segment_sum_M"] = float(ref.sum())
         del sp

@@ -11,7 +11,7 @@
  * standard or dual Lagrange-multiplier shape functions Phi
  * (Eq. AnsatzDiscretizationLagrangeMult), segment-based integration on one
  * auxiliary plane per slave element (Sec. 2.3, Algorithm 1: project, clip,
- * triangulate, quadrature), a binned contact search (Sec. 3.3, Algorithm 2),
+ * triangulate, quadrature), a binned contact search (Sec. 3.5, Algorithm 2),
  * and the gradient of the weighted gap functional
  *   J = sum_j lambda_j . ( (D X_s)_j - (M X_m)_j )
  * with respect to every slave and master nodal coordinate (the consistent
@@ -87,7 +87,7 @@ typedef struct mortar_options {
   double merge_tol_rel;     /* vertex merge distance = merge_tol_rel * h_s (1e-10) */
   double area_tol_rel;      /* discard polygons below area_tol_rel * slave area (1e-14) */
   double bin_margin;        /* added to the minimal bin size: the 2 dt |mean interface velocity| term
-                               of Sec. 3.3 for moving interfaces (0); bins are rebuilt every run */
+                               of Sec. 3.5 for moving interfaces (0); bins are rebuilt every run */
   int32_t integration;      /* MORTAR_INTEGRATE_SEGMENT (default) or MORTAR_INTEGRATE_ELEMENT */
   int32_t element_rule_n;   /* points per direction of the element-based rule, 1..16 (8) */
   int32_t facing_test;      /* 1: keep only candidate pairs whose slave and master element normals (at
@@ -119,7 +119,7 @@ typedef struct mortar_stats {
   float ms_search, ms_integrate, ms_assemble, ms_adjoint, ms_adjoint_pairs, ms_total;
   /* CTA busy-time imbalance max/min of the batched pair kernel in the last run
    * (timing on; the measure eta_t of the paper's load-balancing trigger,
-   * Sec. 4.3, taken over CTAs instead of processes); 0 if not measured */
+   * Sec. 4.4, taken over CTAs instead of processes); 0 if not measured */
   float eta_t;
   /* linearisation (mortar_tangent): time of its kernels (timing on) and 3x3 blocks */
   float ms_tangent;
@@ -284,28 +284,36 @@ int mortar_set_timing(mortar_ctx* ctx, int32_t enabled);
 int mortar_set_launch(mortar_ctx* ctx, int32_t variant, int32_t block_size, int32_t chunk_pairs, int32_t rounds);
 
 /* Per-pair integration without any device allocation.  The paper has no
- * counterpart to this call; it exists for callers that cannot call
- * cudaMalloc -- code running while a host framework captures a CUDA graph or
- * inside an allocator callback (allocating there is illegal or re-enters the
- * allocator), and processes held to a device-memory budget fixed up front.
+ * counterpart to this call.  It exists for callers that cannot call
+ * cudaMalloc: code inside a device-memory allocator's own callback (an
+ * allocation there re-enters the allocator), and processes whose device
+ * memory is reserved up front by a pool or a fixed budget (a new allocation
+ * fails or breaks the budget).
  *
- * Computes, for a caller-given pair list, what mortar_evaluate computes per
- * pair (slave-element precomputation, then Algorithm 1 per pair): M_blocks /
- * D_blocks (n_pairs x 16 FP64, layout of mortar_get_pair_blocks; D_blocks only
- * in segment mode, may be NULL otherwise) and nonempty (n_pairs bytes).  All
- * pointers are device memory of the current device, owned by the caller; ids
- * are 0-based (pair_s < n_slave_elems, pair_m < n_master_elems).
+ * Computes, for a caller-given pair list, the per-pair blocks that
+ * mortar_evaluate computes (the slave-element precomputation, then the
+ * segment-based integration of each pair): M_blocks / D_blocks (n_pairs x 16
+ * FP64, layout of mortar_get_pair_blocks; D_blocks only in segment mode, may be
+ * NULL otherwise) and nonempty (n_pairs bytes).  All pointers are device
+ * memory of the current device, owned by the caller; ids are 0-based
+ * (pair_s < n_slave_elems, pair_m < n_master_elems).
  *
  * Scratch lives in one static device array of this library (room for
  * 8192 slave elements, 5.2 MB, held on every device that loads the library
  * until the process exits): n_slave_elems > 8192 returns MORTAR_ERR_CAPACITY
  * and nothing runs.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the array and clears its counters itself; calls
- * whose work overlaps on the GPU (other streams, other threads) race on it.
- * Always segment-based (o->integration is ignored).  Ids out of range return MORTAR_ERR_INVALID_ARG before any geometry kernel
- * runs (this check synchronises `stream` once); the integration itself is
- * stream-ordered on `stream` when the call returns MORTAR_OK. */
+ * address (cudaGetSymbolAddress) with that device current.  Every call shares
+ * the array and clears its counters itself; calls whose work overlaps on the
+ * GPU (other streams, other threads) race on it.
+ *
+ * Always segment-based (o->integration is ignored).  Every call first checks
+ * all ids on the GPU and reads the verdict back, so it synchronises `stream`
+ * once: ids out of range return MORTAR_ERR_INVALID_ARG before any geometry
+ * kernel runs.  After that the precomputation and the integration are
+ * enqueued on `stream` and the call returns MORTAR_OK without waiting for
+ * them.  Unlike mortar_evaluate, this call does not report degenerate slave
+ * elements or back-projection failures: a degenerate slave element gives
+ * nonempty = 0 and zero blocks for its pairs, and nothing else is signalled. */
 int mortar_integrate_pairs_static(const mortar_options* o, void* stream,
                                   const double* xs, int64_t n_slave_nodes,
                                   const int32_t* conn_s, int64_t n_slave_elems, int32_t type_s,

@@ -19,7 +19,7 @@
 //     n_0, Fig. 1), projection along n_0, mortar segments = clip polygons.
 //   * Algorithm 1: for each slave element and each nearby master element --
 //     project, clip, triangulate into cells, quadrature.
-//   * Sec. 3.3 / Algorithm 2: Cartesian bins covering the interface's bounding
+//   * Sec. 3.5 / Algorithm 2: Cartesian bins covering the interface's bounding
 //     box, elements sorted into bins, neighbours of a bin searched.
 //   * Sec. 1 (consistent linearisation): derivatives of the weighted gap
 //     functional by forward-mode dual numbers (exact to rounding).

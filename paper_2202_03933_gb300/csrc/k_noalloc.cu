@@ -2,11 +2,13 @@
 // plus per-pair integration over a caller-supplied pair list, with all scratch
 // in one file-scope static device array.
 //
-// Some callers cannot call cudaMalloc: code that runs while a host framework
-// is capturing a CUDA graph or inside an allocator callback (an allocation
-// there is illegal or re-enters the allocator), and processes held to a fixed
-// device-memory budget that is reserved up front.  They pass inputs and
+// Some callers cannot call cudaMalloc: code inside a device-memory
+// allocator's own callback (an allocation there re-enters the allocator), and
+// processes whose device memory is reserved up front by a pool or a fixed
+// budget (a new allocation fails or breaks the budget).  They pass inputs and
 // outputs; everything else the kernels need lives in g_static_scratch below.
+// Each call synchronises its stream once, to read the id check back before
+// any kernel dereferences an id.
 //
 // Scratch layout (FP64 words): [DevStatus | slave records | element D blocks |
 // slave boxes], sized for kStaticMaxSlave slave elements.  The array exists on

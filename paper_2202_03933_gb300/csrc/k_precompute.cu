@@ -6,7 +6,7 @@
 //    A = Dh Me^-1, biorthogonal to N, Sec. 2.2) and the element-domain D
 //    block; inflated bounding box and diameter for the search.
 //  * Master elements: inflated bounding box and diameter.
-//  * Search grid per interface (Sec. 3.3): bounding box of the interface,
+//  * Search grid per interface (Sec. 3.5): bounding box of the interface,
 //    minimal bin size beta_min = (1 + 1e-9) max diameter + 2 delta (+ the
 //    velocity margin of moving interfaces), box
 //    expanded by beta_min, n_d = max(1, floor(L_d / beta_min)) bins per

@@ -1,4 +1,4 @@
-// Binned contact search (Sec. 3.3, Algorithm 2, restated for one device).
+// Binned contact search (Sec. 3.5, Algorithm 2, restated for one device).
 //
 // Master elements are sorted into the bins of their interface's grid by the
 // centre of their inflated bounding box (counting sort: per-bin counts, a

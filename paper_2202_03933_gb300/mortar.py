@@ -338,6 +338,18 @@ def integrate_pairs_static(xs, conn_s, xm, conn_m, pair_s, pair_m, lm: int = LM_
     torch -- a caller that cannot allocate passes its own buffers to the C ABI
     directly."""
     torch = _torch()
+    for name, t, dt in (("xs", xs, torch.float64), ("xm", xm, torch.float64), ("conn_s", conn_s, torch.int32),
+                        ("conn_m", conn_m, torch.int32), ("pair_s", pair_s, torch.int32),
+                        ("pair_m", pair_m, torch.int32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA tensor of {dt}")
+    if xs.dim() != 2 or xs.shape[1] != 3 or xm.dim() != 2 or xm.shape[1] != 3:
+        raise ValueError("xs and xm must be (N, 3)")
+    for name, c in (("conn_s", conn_s), ("conn_m", conn_m)):
+        if c.dim() != 2 or c.shape[1] not in (TRI3, QUAD4):
+            raise ValueError(f"{name} must be (E, 3) (tri3) or (E, 4) (quad4)")
+    if pair_s.shape != pair_m.shape or pair_s.dim() != 1:
+        raise ValueError("pair_s and pair_m must be 1-D of equal length")
     o = default_options()
     o.lm, o.d_domain, o.search_inflation = lm, d_domain, delta
     P = int(pair_s.shape[0])

@@ -303,7 +303,7 @@ def test_autotune_keeps_results(mt, orc):
 def test_moving_interface_reevaluation(mt, orc):
     """Repeated evaluation of one context while the master slides and turns
     (coordinates updated on the device between graph replays, bins rebuilt
-    every step, bin size with the velocity margin of Sec. 3.3)."""
+    every step, bin size with the velocity margin of Sec. 3.5)."""
     import math
     import torch
     base = inputs.planar_noisy(24, 21, 1, 48, "mov")

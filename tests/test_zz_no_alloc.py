@@ -1,10 +1,12 @@
-"""The no-allocation entry point (mortar_integrate_pairs_static) against the
-regular context path, through the C ABI, on two calls in a row.
+"""The no-allocation entry point (mortar_integrate_pairs_static) through the
+C ABI, on two calls in a row: against the regular context path (the existing
+entry point) and against the oracle's per-pair blocks.
 
-Some callers of this library cannot call cudaMalloc (code running during a
-host framework's graph capture or inside an allocator callback, processes with
-a device-memory budget fixed up front); this entry point keeps its scratch in a
-static device array instead.  This file is collected last on purpose.
+Some callers of this library cannot call cudaMalloc: code inside a
+device-memory allocator's own callback, where an allocation re-enters the
+allocator, and processes whose device memory is reserved up front by a pool or
+a fixed budget.  This entry point keeps its scratch in a static device array
+instead.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -12,6 +14,7 @@ import numpy as np
 import pytest
 
 from paper_2202_03933_gb300 import inputs
+from gpu_util import blocks_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -26,32 +29,50 @@ def mt():
     return mortar
 
 
+def _swap(itf, name):
+    return inputs.Interface(name, itf.xm, itf.conn_m, itf.type_m, itf.xs, itf.conn_s, itf.type_s,
+                            lm=itf.lm, delta=itf.delta)
+
+
 def _cases():
     return [
         ("planar_dual", inputs.planar_noisy(60, 52, 1, 91, "p"), 0),
         ("planar_dual_segment", inputs.planar_noisy(40, 35, 1, 92, "ps"), 1),
         ("mixed_tri3_master", inputs.mixed_tri(50, 64, name="mx"), 0),
+        ("tri3_slave_quad4_master", _swap(inputs.mixed_tri(24, 19, name="ts"), "ts"), 1),
+        ("tri3_both", _tri_both(), 0),
     ]
 
 
+def _tri_both():
+    a = inputs.mixed_tri(18, 15, name="a")   # tri3 master of a 15x15 grid
+    b = inputs.mixed_tri(13, 11, name="b")   # tri3 master of an 11x11 grid
+    return inputs.Interface("tri3_both", a.xm, a.conn_m, 3, b.xm, b.conn_m, 3, lm=0, delta=1e-9)
+
+
 @pytest.mark.parametrize("name,itf,d_domain", _cases(), ids=[c[0] for c in _cases()])
-def test_static_entry_point_matches_context_path(mt, name, itf, d_domain):
+def test_static_entry_point_matches_context_path_and_oracle(mt, orc, name, itf, d_domain):
     import torch
     ref = mt.Mortar(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
     ref.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
     ref.evaluate()
     s, m = ref.pairs()
     Mr, Dr, ner = ref.pair_blocks(with_D=d_domain == 1)
+    Mo, Do, neo, _ = orc.pair_blocks(itf, s, m, orc.make_opts(lm=itf.lm, d_domain=d_domain, delta=itf.delta))
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     args = (dev(itf.xs), dev(itf.conn_s), dev(itf.xm), dev(itf.conn_m), dev(s), dev(m))
-    scale = np.abs(Mr).max()
     for call in range(2):   # two calls in a row share the static scratch
         Mb, Db, ne = mt.integrate_pairs_static(*args, lm=itf.lm, d_domain=d_domain, delta=itf.delta)
         torch.cuda.synchronize()
-        assert np.array_equal(ne.cpu().numpy().astype(bool), ner), call
-        assert np.abs(Mb.cpu().numpy() - Mr).max() <= 1e-12 * scale, call
+        ne = ne.cpu().numpy().astype(bool)
+        Mb = Mb.cpu().numpy()
+        assert np.array_equal(ne, ner) and np.array_equal(ne, neo), call
+        blocks_parity(Mb, Mr)    # the existing entry point
+        blocks_parity(Mb, Mo)    # the oracle
         if d_domain == 1:
-            assert np.abs(Db.cpu().numpy() - Dr).max() <= 1e-12 * np.abs(Dr).max(), call
+            Db = Db.cpu().numpy()
+            blocks_parity(Db, Dr)
+            blocks_parity(Db, Do)
 
 
 def test_static_entry_point_rejects_oversize_and_bad_ids(mt):
@@ -68,3 +89,6 @@ def test_static_entry_point_rejects_oversize_and_bad_ids(mt):
     m = np.array([0, 0, 0], np.int32)
     with pytest.raises(mt._native.MortarError, match="INVALID_ARG"):
         mt.integrate_pairs_static(dev(itf.xs), dev(itf.conn_s), dev(itf.xm), dev(itf.conn_m), dev(s), dev(m))
+    with pytest.raises(TypeError):   # int64 pair ids are refused by the binding, not misread
+        mt.integrate_pairs_static(dev(itf.xs), dev(itf.conn_s), dev(itf.xm), dev(itf.conn_m),
+                                  dev(s.astype(np.int64)), dev(m.astype(np.int64)))
