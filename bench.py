@@ -20,7 +20,9 @@ this method: the paper ships no code) on a bounded sample of the same
 workload, on the host cores.
 
 Besides the step, the JSON line carries (none of it inside the timed step):
-``forward_only`` (search + integration + assembly graph), ``element_based``
+``forward_only`` (search + integration + assembly graph), ``batched`` (the
+512 uneven interfaces in one graph against one graph per interface: the
+batched speed-up and the CTA busy-time imbalance eta_t), ``element_based``
 (the same forward graph with the element-based rule, n = 4 and 8, and the
 deviation of its M from the segment-based M), ``dynamic`` (a master sliding
 0.3 h_m per step: device copy of the new coordinates + the full step, bins
@@ -46,15 +48,6 @@ sys.path.insert(0, ROOT)
 METRIC = "mortar pairs integrated/sec (D+M, FP64) and fwd+adjoint time on 1 GB300 vs FP64 roofline"
 UNIT = "pairs/s"
 
-# Algorithmic FP64 flops of the per-pair integration, counted by the oracle's
-# flop-counting scalar over the workload's full pair set
-# (`python -m oracle.count_flops <workload>`; + - * / sqrt = 1 flop each).
-ALGO_FLOPS = {
-    "planar_2000x1733": {"pairs": 14936836, "flops": 425035751226},
-    "mixed_300x400": {"pairs": 960724, "flops": 7494813947},
-    "cylinder_200x173": {"pairs": 171739, "flops": 3512674839},
-}
-
 # Executed FP64 flops (2 x DFMA + DADD + DMUL thread instructions, predicated
 # on) and DRAM bytes per pair of the per-pair kernels, from ncu counters of
 # this build on planar_600x520 (same element types and density as the full
@@ -73,6 +66,17 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def measured_peaks() -> dict:
+    """HBM copy bandwidth and bf16 GEMM rates measured on the GB300s
+    (MEASURED_PEAKS.json beside this file), else the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "kind": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "kind": "fallback"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -82,6 +86,8 @@ def parse():
     ap.add_argument("--workload", default="planar_2000x1733")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sections", default="forward,dynamic,element_based,linearisation,batched,probe",
+                    help="extra sections measured after the timed step (comma list; 'none' for the step only)")
     return ap.parse_args()
 
 
@@ -263,35 +269,42 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------------- GPU
-def run_batched(args, world, rank, local):
-    """512 uneven interfaces: one batched context (one search, one persistent
-    integration and adjoint launch over all pairs, one CUDA graph) against one
-    context per interface, each replaying its own graph, back to back."""
+def batched_measure(steps: int, warmup: int, stream, clk_gpu=None) -> dict:
+    """512 uneven interfaces (the batched workload): one batched context (one
+    search, one persistent pair kernel over all pairs, one CUDA graph; launch
+    shape from the autotuner) against one context per interface, each
+    replaying its own graph, back to back.  Forward + adjoint in both."""
     import numpy as np
     import torch
-    from paper_2202_03933_gb300 import build, inputs, mortar
+    from paper_2202_03933_gb300 import inputs, mortar
 
-    build()
     itfs = inputs.batched_512()
-    stream = torch.cuda.current_stream()
     lam_all = np.random.default_rng(1).uniform(-1, 1, (sum(i.xs.shape[0] for i in itfs), 3))
     m = mortar.Mortar(lm=0, delta=1e-9, stream=stream.cuda_stream)
     m.set_batch(itfs)
     pick = m.autotune(lam_all)
     m.set_timing(True)
     lam_d = torch.from_numpy(lam_all).cuda()
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         m.run_graph(lam_d)
     torch.cuda.synchronize()
-    barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    clocks = None
+    if clk_gpu is not None:
+        with ClockSampler(clk_gpu) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                m.run_graph(lam_d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        clocks = clk.summary()
+    else:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             m.run_graph(lam_d)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+    ms = e0.elapsed_time(e1) / steps
     st = m.stats()
     # one context (and one graph) per interface
     ctxs, lams = [], []
@@ -309,28 +322,55 @@ def run_batched(args, world, rank, local):
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for c, lam in zip(ctxs, lams):
             c.run_graph(lam)
     f1.record(stream)
     torch.cuda.synchronize()
-    ms_sep = f0.elapsed_time(f1) / args.steps
-    clocks = clk.summary()
-    line = {"metric": METRIC, "value": weak_value(world, st["n_pairs"], ms), "unit": UNIT, "n_gpus": world,
+    ms_sep = f0.elapsed_time(f1) / steps
+    for c in ctxs:
+        c.close()
+    out = {"interfaces": len(itfs), "pairs": st["n_pairs"],
+           "slave_elements": int(sum(i.conn_s.shape[0] for i in itfs)),
+           "step": "batched search + integrate + assemble + adjoint, one CUDA graph",
+           "autotune": pick, "ms_per_step": round(ms, 4), "pairs_per_s": st["n_pairs"] / (ms / 1e3),
+           "phases_ms": {"search": st["ms_search"], "pair_kernel": st["ms_integrate"],
+                         "assemble": st["ms_assemble"], "adjoint_rest": st["ms_adjoint"]},
+           "one_graph_per_interface_ms": round(ms_sep, 4), "batched_speedup": round(ms_sep / ms, 3),
+           "eta_t": round(float(st.get("eta_t", 0.0)), 4),
+           "graph_kernels": int(st.get("graph_kernels", 0))}
+    if clocks is not None:
+        out["clocks"] = clocks
+    m.close()
+    return out
+
+
+def run_batched(args, world, rank, local):
+    """--workload batched_512: the batched measurement as its own JSON line."""
+    import torch
+    from paper_2202_03933_gb300 import build
+
+    build()
+    stream = torch.cuda.current_stream()
+    barrier(world)
+    b = batched_measure(args.steps, args.warmup, stream, clk_gpu=local)
+    ms = max_over_ranks(world, b["ms_per_step"])
+    clocks = b.pop("clocks")
+    line = {"metric": METRIC, "value": weak_value(world, b["pairs"], ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched_512", "interfaces": len(itfs), "pairs": st["n_pairs"],
-                       "slave_elements": int(sum(i.conn_s.shape[0] for i in itfs)),
-                       "step": "batched search + integrate + assemble + adjoint, one CUDA graph",
-                       "autotune": pick},
-            "phases_ms": {"search": st["ms_search"], "integrate": st["ms_integrate"],
-                          "assemble": st["ms_assemble"], "adjoint": st["ms_adjoint"]},
-            "one_graph_per_interface_ms": round(ms_sep, 4), "batched_speedup": round(ms_sep / ms, 3),
-            "eta_t": round(float(st.get("eta_t", 0.0)), 4),
-            "gpu_launches": int(st.get("graph_kernels", 0)) * args.steps,
+            "config": {"workload": "batched_512", "interfaces": b["interfaces"], "pairs": b["pairs"],
+                       "slave_elements": b["slave_elements"], "step": b["step"], "autotune": b["autotune"]},
+            "phases_ms": b["phases_ms"], "one_graph_per_interface_ms": b["one_graph_per_interface_ms"],
+            "batched_speedup": b["batched_speedup"], "eta_t": b["eta_t"],
+            "gpu_launches": b["graph_kernels"] * args.steps,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+class _Skip(Exception):
+    """An extra section left out by --sections."""
 
 
 def run_ours(args, world, rank, local):
@@ -339,6 +379,7 @@ def run_ours(args, world, rank, local):
     from paper_2202_03933_gb300 import build, inputs, mortar
 
     build()
+    sections = set(args.sections.split(","))
     itf = inputs.by_name(args.workload)
     if isinstance(itf, list):
         raise SystemExit("use a single-interface workload for the headline benchmark")
@@ -422,14 +463,17 @@ def run_ours(args, world, rank, local):
         b_asm = 129 * n_pairs + 128 * Es_ + 12 * (n_nzD + n_nzM) + 16 * itf.xs.shape[0]
         phase_bw = {"search_GBps": round(b_search / (med(t_srch) / 1e3) / 1e9, 1),
                     "assemble_GBps": round(b_asm / (med(t_asm) / 1e3) / 1e9, 1),
-                    "hbm_peak_GBps": "6678 (measured copy; the phases are gathers, latency-bound)"}
+                    "hbm_peak_GBps": measured_peaks().get("hbm_gbs"),
+                    "note": "of measured copy bandwidth; the phases are gathers, latency-bound"}
     except Exception as ex_:   # reported, not fatal
         phase_bw = {"error": str(ex_)}
 
-    # ---- forward only (integration kernel alone): forward pairs/s and its
-    #      algorithmic rate (oracle-counted flops / kernel time)
+    # ---- forward only (search + integration + assembly graph): forward pairs/s
+    #      and the integration kernel's executed-FP64 roofline fraction
     fwd = None
     try:
+        if "forward" not in sections:
+            raise _Skip()
         for _ in range(3):
             m.run_graph()
         torch.cuda.synchronize()
@@ -444,13 +488,17 @@ def run_ours(args, world, rank, local):
         ms_f = g0.elapsed_time(g1) / args.steps
         fwd = {"ms_per_step": round(ms_f, 4), "pairs_per_s": world * n_pairs / (ms_f / 1e3),
                "ms_integrate": round(med(t_fi), 4)}
-        af = ALGO_FLOPS.get(args.workload)
-        if af and af["pairs"] == n_pairs:
-            a = af["flops"] / (med(t_fi) / 1e3) / 1e12
-            fwd["integration_algorithmic"] = {
-                "tflops": round(a, 4), "frac_of_derived_peak": round(a / FP64_PEAK_TFLOPS, 4),
-                "flops_per_launch": af["flops"],
-                "note": "oracle-counted flops of its textbook formulation; the kernel executes fewer"}
+        exf = EXEC_PER_PAIR["integrate"]
+        if exf["flops"] and args.workload.startswith("planar_") and itf.lm == 1:
+            a = exf["flops"] * n_pairs / (med(t_fi) / 1e3) / 1e12
+            fwd["roofline"] = {
+                "bound": "alu", "kernel": "k_integrate_batched", "ms_per_launch": round(med(t_fi), 4),
+                "achieved": round(a, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(a / FP64_PEAK_TFLOPS, 4), "flops_per_pair": exf["flops"],
+                "flops": "executed FP64 (ncu 2 DFMA + DADD + DMUL per pair, planar_600x520) x pairs",
+                "traffic": int(exf["dram_bytes"] * n_pairs) if exf["dram_bytes"] else None}
+    except _Skip:
+        pass
     except Exception as ex_:   # reported, not fatal
         fwd = {"error": str(ex_)}
 
@@ -461,12 +509,14 @@ def run_ours(args, world, rank, local):
     #      2 dt |v| margin of Sec. 3.5
     dyn = None
     try:
+        if "dynamic" not in sections:
+            raise _Skip()
         K = max(min(args.steps, 8), 2)
         hm = 1.0 / itf.info.get("nm", 1) if "nm" in itf.info else 0.0
         shift = 0.3 * hm
         md = mortar.Mortar(lm=itf.lm, delta=itf.delta, stream=stream.cuda_stream, bin_margin=2 * shift)
         md.set_interface(xs, cs, xm, cm)
-        md.set_launch(pick.get("variant", 0), 0, 0, pick.get("rounds", 0))
+        md.set_launch(pick.get("variant", 0), pick.get("block", 0), 0, pick.get("rounds", 0))
         xm_k = [xm + torch.tensor([shift * (k + 1), 0.0, 0.0], dtype=torch.float64, device=dev)
                 for k in range(K + 2)]
         for k in range(2):
@@ -488,6 +538,8 @@ def run_ours(args, world, rank, local):
                "step": "device copy of the moved master coordinates + search + integrate + assemble + adjoint"}
         md.close()
         del xm_k
+    except _Skip:
+        pass
     except Exception as ex_:   # reported, not fatal
         dyn = {"error": str(ex_)}
 
@@ -496,6 +548,8 @@ def run_ours(args, world, rank, local):
     #      deviation of M from the segment-based M of this workload
     ebi = None
     try:
+        if "element_based" not in sections:
+            raise _Skip()
         import scipy.sparse as sp
         m.run_graph()
         ref = m.scipy(mortar.MATRIX_M)
@@ -524,6 +578,8 @@ def run_ours(args, world, rank, local):
             me.close()
         ebi["segment_sum_M"] = float(ref.sum())
         del sp
+    except _Skip:
+        pass
     except Exception as ex_:   # reported, not fatal
         ebi = {"error": str(ex_)}
 
@@ -531,6 +587,8 @@ def run_ours(args, world, rank, local):
     #      separate call, not part of the step; device time of its kernels
     lin = None
     try:
+        if "linearisation" not in sections:
+            raise _Skip()
         for _ in range(1):
             m.tangent(xs, xm, add_direct=True, out_device=True)
         t_l = []
@@ -542,12 +600,28 @@ def run_ours(args, world, rank, local):
                "blocks_3x3": sl["nnzb_K"],
                "what": "K = d/dX[(D (x) I3) Xs - (M (x) I3) Xm] + [D (x) I3 | -M (x) I3]: pair blocks, "
                        "element blocks, BSR assembly"}
+    except _Skip:
+        pass
     except Exception as ex_:   # reported, not fatal
         lin = {"error": str(ex_)}
+
+    # ---- batched uneven interfaces (512 interfaces, one graph) against one
+    #      graph per interface: the batched speed-up and the CTA imbalance eta_t
+    bat = None
+    try:
+        if "batched" not in sections:
+            raise _Skip()
+        bat = batched_measure(max(min(args.steps, 10), 3), 3, stream)
+    except _Skip:
+        pass
+    except Exception as ex_:   # reported, not fatal
+        bat = {"error": str(ex_)}
 
     # ---- FP64 probe (measured peak, for context)
     probe = None
     try:
+        if "probe" not in sections:
+            raise _Skip()
         blocks, threads, iters = SM_COUNT * 8, 256, 20000
         sink = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
         mortar.probe_dfma(blocks, threads, 100, sink=sink)
@@ -558,6 +632,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         pm = e0.elapsed_time(e1)
         probe = {"tflops": round(blocks * threads * 8 * 2 * iters / (pm / 1e3) / 1e12, 4), "ms": round(pm, 3)}
+    except _Skip:
+        pass
     except Exception as ex:   # measurement context only
         probe = {"error": str(ex)}
 
@@ -619,6 +695,7 @@ def run_ours(args, world, rank, local):
         "phase_bandwidth": phase_bw,
         "forward_only": fwd,
         "linearisation": lin,
+        "batched": bat,
         "element_based": ebi,
         "dynamic": dyn,
         "roofline": roof,

@@ -47,7 +47,9 @@ extern "C" {
 
 typedef enum mortar_status {
   MORTAR_OK = 0,
-  MORTAR_ERR_INVALID_ARG = -1, /* null pointer, bad element type, node id out of range, bad size */
+  MORTAR_ERR_INVALID_ARG = -1, /* null pointer, bad element type, node id out of range, bad size;
+                                  from a run: a non-finite node coordinate (elements touching it get
+                                  no pairs, the rest is still computed) */
   MORTAR_ERR_DEGENERATE = -2,  /* zero-area, non-finite or inverted slave element */
   MORTAR_ERR_NEWTON = -3,      /* a back-projection did not converge; results are still written */
   MORTAR_ERR_CAPACITY = -4,    /* caller buffer too small; nothing written */
@@ -80,7 +82,8 @@ typedef struct mortar_options {
   int32_t lm;               /* MORTAR_LM_STANDARD or MORTAR_LM_DUAL */
   int32_t d_domain;         /* MORTAR_D_ELEMENT (default) or MORTAR_D_SEGMENT */
   int32_t newton_max_iter;  /* back-projection Newton cap (20) */
-  int32_t block_size;       /* threads per block of the pair kernels, 0 = tuned default */
+  int32_t block_size;       /* threads per block of the pair kernels: 0 (default 128) or a multiple of
+                               32 up to 256 */
   double search_inflation;  /* delta: absolute AABB inflation of the search (1e-9) */
   double newton_tol;        /* stop when |dxi|_inf <= tol, then one more update (1e-14) */
   double clip_tol_rel;      /* inside tolerance eps_in = clip_tol_rel * h_s^2 (1e-12) */
@@ -92,7 +95,9 @@ typedef struct mortar_options {
   int32_t element_rule_n;   /* points per direction of the element-based rule, 1..16 (8) */
   int32_t facing_test;      /* 1: keep only candidate pairs whose slave and master element normals (at
                                the element centres) point against each other, n_s . n_m < 0 (0) */
-  int32_t pad0;
+  int32_t watchdog_us;      /* time budget of the persistent pair kernels in microseconds, 0 = none (0):
+                               a kernel whose thread blocks run longer stops taking work and the call
+                               returns MORTAR_ERR_TIMEOUT (results not valid; the context stays usable) */
 } mortar_options;
 
 typedef struct mortar_stats {
@@ -276,11 +281,18 @@ int mortar_get_stats(mortar_ctx* ctx, mortar_stats* out);
 /* Enable (1) / disable (0) CUDA-event phase timing (default 0). */
 int mortar_set_timing(mortar_ctx* ctx, int32_t enabled);
 
+/* Change the pair kernels' time budget (mortar_options.watchdog_us; 0 = none).
+ * A captured graph is re-captured on its next run.  MORTAR_ERR_INVALID_ARG
+ * for a negative budget. */
+int mortar_set_watchdog(mortar_ctx* ctx, int32_t watchdog_us);
+
 /* Launch shape of the pair kernels (used by the autotuner; 0 = default):
- * variant 0 = integration in warp batches of 32 * rounds pairs sorted by
- * cell count (rounds 1, 2 or 4), variant 1 = one pair per thread;
- * block_size (multiple of 32) and chunk_pairs (pairs per work-counter fetch)
- * for the one-pair-per-thread kernels (variant 1 and the adjoint). */
+ * variant 0 = integration and adjoint in warp batches of 32 * rounds pairs
+ * sorted by cell count (rounds 1, 2 or 4), variant 1 = one pair per thread;
+ * block_size = threads per block of either variant (a multiple of 32 up to
+ * 256; default 128); chunk_pairs = pairs per work-counter fetch of variant 1
+ * (default 32).  MORTAR_ERR_INVALID_ARG for other values, or when the warp
+ * batches of variant 0 would not fit the shared memory of one block. */
 int mortar_set_launch(mortar_ctx* ctx, int32_t variant, int32_t block_size, int32_t chunk_pairs, int32_t rounds);
 
 /* Per-pair integration without any device allocation.  The paper has no
@@ -322,13 +334,17 @@ int mortar_integrate_pairs_static(const mortar_options* o, void* stream,
                                   const int32_t* pair_s, const int32_t* pair_m, int64_t n_pairs,
                                   double* M_blocks, double* D_blocks, uint8_t* nonempty);
 
-/* Autotuner: runs the context's workload once per candidate launch shape
- * (batched integration with 32, 64 or 128 pairs per warp batch, and one pair
- * per thread), times the pair kernels (integration, plus the adjoint's
- * per-pair kernel when lambda != NULL) with CUDA events, and keeps the
- * fastest shape for later calls.  Writes the choice and its time (ms). */
+/* Autotuner (the batched persistent schedule of many uneven interfaces picks
+ * its launch shape on the workload itself): runs the context's workload three
+ * times per candidate shape -- warp batches of 32, 64 or 128 pairs (rounds 1,
+ * 2, 4) with 64, 128 or 256 threads per block, and one pair per thread with
+ * 64, 128 or 256 threads per block and 32 or 128 pairs per work fetch --
+ * times the pair kernels (integration, plus the adjoint's per-pair kernel when
+ * lambda != NULL) with CUDA events, and keeps the fastest shape for later
+ * calls.  Writes the choice (any output pointer may be NULL) and its time in
+ * ms. */
 int mortar_autotune(mortar_ctx* ctx, const double* lambda, int32_t on_device, int32_t* variant,
-                    int32_t* rounds, float* best_ms);
+                    int32_t* rounds, int32_t* block_size, float* best_ms);
 
 /* Name of a status code. */
 const char* mortar_status_string(int status);

@@ -96,9 +96,6 @@ def _load():
             lib.oracle_pair_blocks.restype = ctypes.c_int
             lib.oracle_pair_blocks.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(Opts),
                                                P, P, i64, P, P, P, P]
-            lib.oracle_count_pair_flops.restype = i64
-            lib.oracle_count_pair_flops.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(Opts),
-                                                    P, P, i64]
             lib.oracle_weighted_gap_grad.restype = ctypes.c_int
             lib.oracle_weighted_gap_grad.argtypes = [P, i64, P, i64, i32, P, i64, P, i32,
                                                      ctypes.POINTER(Opts), P, P, i64, P, P, P, P]
@@ -201,16 +198,6 @@ def pair_blocks(itf, s, m, opts: Opts | None = None):
                            ctypes.byref(o), _p(s), _p(m), P, _p(Mb), _p(Db), _p(ne), _p(st))
     return (Mb[:P].reshape(P, 4, 4), Db[:P].reshape(P, 4, 4), ne[:P].astype(bool),
             dict(zip(STAT_NAMES, (int(x) for x in st))))
-
-
-def count_pair_flops(itf, s, m, opts: Opts | None = None) -> int:
-    lib = _load()
-    o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
-    xs, cs, xm, cm = _mesh_arrays(itf)
-    s = np.ascontiguousarray(s, np.int32)
-    m = np.ascontiguousarray(m, np.int32)
-    return int(lib.oracle_count_pair_flops(_p(xs), _p(cs), cs.shape[1], _p(xm), _p(cm),
-                                           cm.shape[1], ctypes.byref(o), _p(s), _p(m), s.shape[0]))
 
 
 def _csr_from_triplets(rows, cols, vals, nrows, ncols):

@@ -33,8 +33,8 @@
 // one extra update after |dxi|_inf <= tol; dual basis built on the whole slave
 // element with a 3x3 Gauss-Legendre rule (quad4) or the 7-point rule (tri3).
 //
-// Scalar type T is double, Dual<N> (forward-mode derivatives) or Counted (flop
-// counting: + - * / sqrt each count 1).  All branch decisions use val(x).
+// Scalar type T is double or Dual<N> (forward-mode derivatives).  All branch
+// decisions use val(x).
 
 #include <algorithm>
 #include <cmath>
@@ -94,30 +94,6 @@ template <int N> inline Dual<N> operator*(double a, const Dual<N>& b) {
 template <int N> inline Dual<N> operator*(const Dual<N>& a, double b) { return b * a; }
 template <int N> inline Dual<N> operator/(const Dual<N>& a, double b) { return a / Dual<N>(b); }
 template <int N> inline Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
-
-// Flop-counting scalar: every + - * / sqrt on a Counted value counts one.
-static thread_local uint64_t g_flops = 0;
-struct Counted {
-  double v;
-  Counted() : v(0) {}
-  Counted(double x) : v(x) {}
-};
-inline double val(const Counted& x) { return x.v; }
-inline Counted operator+(Counted a, Counted b) { ++g_flops; return Counted(a.v + b.v); }
-inline Counted operator-(Counted a, Counted b) { ++g_flops; return Counted(a.v - b.v); }
-inline Counted operator-(Counted a) { return Counted(-a.v); }
-inline Counted operator*(Counted a, Counted b) { ++g_flops; return Counted(a.v * b.v); }
-inline Counted operator/(Counted a, Counted b) { ++g_flops; return Counted(a.v / b.v); }
-inline Counted sqrt(Counted a) { ++g_flops; return Counted(std::sqrt(a.v)); }
-inline Counted& operator+=(Counted& a, Counted b) { a = a + b; return a; }
-inline Counted& operator-=(Counted& a, Counted b) { a = a - b; return a; }
-inline Counted operator+(double a, Counted b) { return Counted(a) + b; }
-inline Counted operator+(Counted a, double b) { return a + Counted(b); }
-inline Counted operator-(double a, Counted b) { return Counted(a) - b; }
-inline Counted operator-(Counted a, double b) { return a - Counted(b); }
-inline Counted operator*(double a, Counted b) { return Counted(a) * b; }
-inline Counted operator*(Counted a, double b) { return a * Counted(b); }
-inline Counted operator/(Counted a, double b) { return a / Counted(b); }
 
 using std::sqrt;
 
@@ -874,45 +850,6 @@ int oracle_element_based_blocks(const double* xs, const int32_t* cs, int32_t nen
     }
   }
   return 0;
-}
-
-// Algorithmic flop count of the per-pair integration (+ - * / sqrt = 1 each)
-// for the given pairs, with the slave element data taken as given (the
-// auxiliary plane and LM coefficients are element-level precomputation).
-int64_t oracle_count_pair_flops(const double* xs, const int32_t* cs, int32_t nen_s,
-                                const double* xm, const int32_t* cm, int32_t nen_m,
-                                const Opts* o, const int32_t* ps, const int32_t* pm, int64_t P) {
-  uint64_t total = 0;
-  const int nt = o->n_threads > 0 ? o->n_threads : 1;
-#ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 1024) num_threads(nt) reduction(+ : total)
-#endif
-  for (int64_t p = 0; p < P; ++p) {
-    Stats st;
-    SlaveData<double> Sd;
-    load_slave<double>(Sd, xs, cs, nen_s, ps[p], o->lm);
-    SlaveData<Counted> S;
-    S.nen = Sd.nen;
-    for (int a = 0; a < 4; ++a) {
-      S.X[a] = {Counted(Sd.X[a].x), Counted(Sd.X[a].y), Counted(Sd.X[a].z)};
-      for (int b = 0; b < 4; ++b) S.A[a][b] = Counted(Sd.A[a][b]);
-    }
-    S.x0 = {Sd.x0.x, Sd.x0.y, Sd.x0.z};
-    S.n0 = {Sd.n0.x, Sd.n0.y, Sd.n0.z};
-    S.t1 = {Sd.t1.x, Sd.t1.y, Sd.t1.z};
-    S.t2 = {Sd.t2.x, Sd.t2.y, Sd.t2.z};
-    V3<Counted> Xm[4];
-    for (int l = 0; l < 4; ++l) Xm[l] = {Counted(0.0), Counted(0.0), Counted(0.0)};
-    for (int l = 0; l < nen_m; ++l) {
-      const double* q = xm + 3 * (int64_t)cm[(int64_t)nen_m * pm[p] + l];
-      Xm[l] = {Counted(q[0]), Counted(q[1]), Counted(q[2])};
-    }
-    PairOut<Counted> r;
-    g_flops = 0;
-    integrate_pair<Counted>(S, Xm, nen_m, *o, r, st);
-    total += g_flops;
-  }
-  return (int64_t)total;
 }
 
 // Weighted gap functional J = sum_j lambda_j . ((D X_s)_j - (M X_m)_j) and its

@@ -26,7 +26,7 @@ EXPORTS = (
     "mortar_weighted_gap_grad", "mortar_run_graph", "mortar_get_gradient", "mortar_get_stats",
     "mortar_set_timing", "mortar_set_launch", "mortar_status_string", "mortar_probe_dfma",
     "mortar_integrate_pairs_static", "mortar_autotune", "mortar_tangent", "mortar_tangent_copy",
-    "mortar_contact_terms",
+    "mortar_contact_terms", "mortar_set_watchdog",
 )
 
 
@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("clip_tol_rel", ctypes.c_double), ("merge_tol_rel", ctypes.c_double),
                 ("area_tol_rel", ctypes.c_double), ("bin_margin", ctypes.c_double),
                 ("integration", ctypes.c_int32), ("element_rule_n", ctypes.c_int32),
-                ("facing_test", ctypes.c_int32), ("pad0", ctypes.c_int32)]
+                ("facing_test", ctypes.c_int32), ("watchdog_us", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -91,8 +91,9 @@ def lib():
                 "mortar_get_gradient": [P, ctypes.POINTER(f64), P, P, i32],
                 "mortar_get_stats": [P, ctypes.POINTER(Stats)],
                 "mortar_set_timing": [P, i32],
+                "mortar_set_watchdog": [P, i32],
                 "mortar_set_launch": [P, i32, i32, i32, i32],
-                "mortar_autotune": [P, P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                "mortar_autotune": [P, P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float)],
                 "mortar_tangent": [P, P, P, i32, i32, ctypes.POINTER(i64)],
                 "mortar_tangent_copy": [P, P, P, P, i64, i32],

@@ -28,8 +28,28 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA library cannot be built")
 
 
+# Sources whose pair kernels are built once per element-type combination
+# (slave nodes, master nodes): the same file is compiled into a main object
+# and one object per combination, so the large kernel templates compile in
+# parallel (see the part declarations in csrc/context.h).
+SPLIT = ("k_adjoint.cu", "k_integrate.cu", "k_tangent.cu")
+COMBOS = ((4, 4), (4, 3), (3, 4), (3, 3))
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _units():
+    """(source, object name, extra nvcc flags) for every object of the library."""
+    units = []
+    for src in _sources():
+        base = os.path.basename(src)[:-3]
+        units.append((src, base, []))
+        if os.path.basename(src) in SPLIT:
+            for ns, nm in COMBOS:
+                units.append((src, f"{base}_p{ns}{nm}", [f"-DMORTAR_PAIR_NS={ns}", f"-DMORTAR_PAIR_NM={nm}"]))
+    return units
 
 
 def _deps():
@@ -49,19 +69,22 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         return LIB
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
-    srcs = _sources()
+    units = _units()
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *CFLAGS, *extra, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, name, defs = unit
+        obj = os.path.join(OUT_DIR, name + ".o")
+        cmd = [nvcc, *ARCH, *CFLAGS, *extra, *defs, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed on {src} {' '.join(defs)}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(compile_one, srcs))
+    # the slowest units first, so that they do not start last
+    units.sort(key=lambda u: (not u[2], -os.path.getsize(u[0])))
+    with cf.ThreadPoolExecutor(max_workers=min(len(units), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(compile_one, units))
     if verbose or ptxas_verbose:
         for _, err in results:
             if err:

@@ -239,6 +239,15 @@ int finish_run(mortar_ctx* c, const Phases& ph) {
   return MORTAR_OK;
 }
 
+// Status of a completed run: non-finite coordinates first, then Newton
+// failures, then degenerate slave elements.
+int run_status(const DevStatus& h, const Phases& ph) {
+  if (h.nonfinite) return MORTAR_ERR_INVALID_ARG;
+  if (ph.integrate && h.newton_fail) return MORTAR_ERR_NEWTON;
+  if (h.degenerate) return MORTAR_ERR_DEGENERATE;
+  return MORTAR_OK;
+}
+
 int run(mortar_ctx* c, const Phases& ph) {
   if (!c->have_interface) return MORTAR_ERR_STATE;
   if (ph.adjoint && c->opt.integration != MORTAR_INTEGRATE_SEGMENT) return MORTAR_ERR_INVALID_ARG;
@@ -252,10 +261,7 @@ int run(mortar_ctx* c, const Phases& ph) {
       c->tan_valid = false;
       c->eval_valid = ph.integrate && ph.assemble;
       c->grad_valid = ph.adjoint;
-      const DevStatus& h = *c->hstat;
-      if (ph.integrate && h.newton_fail) return MORTAR_ERR_NEWTON;
-      if (h.degenerate) return MORTAR_ERR_DEGENERATE;
-      return MORTAR_OK;
+      return run_status(*c->hstat, ph);
     }
     if (r != 1) return r;
     c->stats.reruns++;
@@ -402,7 +408,7 @@ int mortar_default_options(mortar_options* o) {
   o->integration = MORTAR_INTEGRATE_SEGMENT;
   o->element_rule_n = 8;
   o->facing_test = 0;
-  o->pad0 = 0;
+  o->watchdog_us = 0;
   return MORTAR_OK;
 }
 
@@ -414,11 +420,14 @@ int mortar_create(mortar_ctx** out, const mortar_options* o, void* stream) {
   if ((c->opt.lm != 0 && c->opt.lm != 1) || (c->opt.d_domain != 0 && c->opt.d_domain != 1) ||
       c->opt.newton_max_iter < 1 || !(c->opt.search_inflation >= 0.0) || !(c->opt.bin_margin >= 0.0) ||
       (c->opt.integration != MORTAR_INTEGRATE_SEGMENT && c->opt.integration != MORTAR_INTEGRATE_ELEMENT) ||
-      c->opt.element_rule_n < 1 || c->opt.element_rule_n > 16 || (c->opt.facing_test != 0 && c->opt.facing_test != 1)) {
+      c->opt.element_rule_n < 1 || c->opt.element_rule_n > 16 || (c->opt.facing_test != 0 && c->opt.facing_test != 1) ||
+      c->opt.block_size < 0 || c->opt.block_size > kMaxPairBlock || (c->opt.block_size % 32) != 0 ||
+      c->opt.watchdog_us < 0) {
     delete c;
     return MORTAR_ERR_INVALID_ARG;
   }
   c->block_size = c->opt.block_size;
+  c->watchdog_us = c->opt.watchdog_us;
   int r = cuda_status(cudaGetDevice(&c->device));
   if (r == MORTAR_OK) r = cuda_status(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device));
   if (r == MORTAR_OK) {
@@ -719,7 +728,7 @@ int mortar_run_graph(mortar_ctx* c, const double* lambda, int32_t on_device) {
     c->search_valid = true;
     c->eval_valid = true;
     c->grad_valid = ph.adjoint;
-    if (c->hstat->newton_fail) r = MORTAR_ERR_NEWTON;
+    r = run_status(*c->hstat, ph);
   }
   return r;
 }
@@ -740,9 +749,21 @@ int mortar_set_timing(mortar_ctx* c, int32_t enabled) {
   return MORTAR_OK;
 }
 
+int mortar_set_watchdog(mortar_ctx* c, int32_t watchdog_us) {
+  if (!c || watchdog_us < 0) return MORTAR_ERR_INVALID_ARG;
+  c->watchdog_us = watchdog_us;
+  if (c->graph_exec) {   // the budget is a kernel argument of the captured launches
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  return MORTAR_OK;
+}
+
 int mortar_set_launch(mortar_ctx* c, int32_t variant, int32_t block_size, int32_t chunk_pairs, int32_t rounds) {
-  if (!c || variant < 0 || variant > 1 || block_size < 0 || block_size > 1024 || (block_size % 32) != 0 ||
+  if (!c || variant < 0 || variant > 1 || block_size < 0 || block_size > kMaxPairBlock || (block_size % 32) != 0 ||
       chunk_pairs < 0 || (rounds != 0 && rounds != 1 && rounds != 2 && rounds != 4))
+    return MORTAR_ERR_INVALID_ARG;
+  if (variant == 0 && !integrate_batched_fits(rounds > 0 ? rounds : 2, block_size > 0 ? block_size : 128))
     return MORTAR_ERR_INVALID_ARG;
   c->variant = variant;
   c->block_size = block_size;
@@ -756,7 +777,7 @@ int mortar_set_launch(mortar_ctx* c, int32_t variant, int32_t block_size, int32_
 }
 
 int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int32_t* variant, int32_t* rounds,
-                    float* best_ms) {
+                    int32_t* block_size, float* best_ms) {
   if (!c) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
   Phases ph;
@@ -765,16 +786,27 @@ int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int3
     MORTAR_TRY(buf_reserve(c->lambda, (size_t)std::max<int64_t>(c->Ns, 1) * 24));
     MORTAR_TRY(copy_in(c->lambda.p, lambda, (size_t)c->Ns * 24, on_device, c->stream));
   }
-  struct Cand { int32_t variant, rounds; };
-  const Cand cands[] = {{0, 1}, {0, 2}, {0, 4}, {1, 0}};
+  // candidate launch shapes: the warp-batched kernels with 32, 64 or 128
+  // pairs per warp batch (rounds 1, 2, 4) and 2, 4 or 8 warps per block, and
+  // the one-pair-per-thread kernels with 64, 128 or 256 threads per block and
+  // 32 or 128 pairs per work-counter fetch
+  struct Cand { int32_t variant, rounds, block, chunk; };
+  std::vector<Cand> cands;
+  for (int32_t r : {1, 2, 4})
+    for (int32_t b : {64, 128, 256})
+      if (integrate_batched_fits(r, b)) cands.push_back({0, r, b, 0});   // the shape serves both kernels
+  for (int32_t b : {64, 128, 256})
+    for (int32_t k : {32, 128}) cands.push_back({1, 0, b, k});
   const bool timing = c->timing;
   c->timing = true;
   float best = 1e30f;
-  Cand pick = {0, 2};
+  Cand pick = {0, 2, 128, 0};
   int r = MORTAR_OK;
   for (const Cand& k : cands) {
     c->variant = k.variant;
     c->rounds = k.rounds;
+    c->block_size = k.block;
+    c->chunk_pairs = k.chunk;
     float t_best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {   // first run sizes buffers and warms up
       r = run(c, ph);
@@ -791,12 +823,15 @@ int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int3
   c->timing = timing;
   c->variant = pick.variant;
   c->rounds = pick.rounds;
+  c->block_size = pick.block;
+  c->chunk_pairs = pick.chunk;
   if (c->graph_exec) {
     cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
   }
   if (variant) *variant = pick.variant;
   if (rounds) *rounds = pick.rounds;
+  if (block_size) *block_size = pick.block;
   if (best_ms) *best_ms = best;
   return (r == MORTAR_ERR_NEWTON || r == MORTAR_ERR_DEGENERATE) ? MORTAR_OK : r;
 }

@@ -197,7 +197,31 @@ struct MapInverse {
     eta -= fma(k10, ru, k11 * rv);
   }
 
-  // returns false if the FP32 iteration did not settle (xi then is the best found)
+  // FP64 Newton from the current (xi, eta), with the oracle's stopping rule:
+  // stop once |dxi|_inf <= 1e-14, then apply one more update; at most 20
+  // updates.  Taken only when the FP32 iteration did not settle (strongly
+  // distorted elements: a corner angle near 180 degrees makes the FP32
+  // Jacobian too inaccurate for its 3e-7 step test).
+  __device__ __noinline__ bool newton64(double xu, double xv, double& xi, double& eta) const {
+    const double du = xu - m.c0u, dv = xv - m.c0v;
+    bool last = false;
+    for (int it = 0; it < 20; ++it) {
+      const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
+      const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
+      const double ru = fma(j00, xi, fma(m.c2u, eta, -du));
+      const double rv = fma(j10, xi, fma(m.c2v, eta, -dv));
+      const double id = 1.0 / (j00 * j11 - j01 * j10);
+      const double d0 = (j11 * ru - j01 * rv) * id, d1 = (j00 * rv - j10 * ru) * id;
+      xi -= d0;
+      eta -= d1;
+      if (last) return true;
+      if (fmax(fabs(d0), fabs(d1)) <= 1e-14) last = true;
+    }
+    return false;
+  }
+
+  // Converged xi of a point; false only if the FP64 fallback did not converge
+  // either (xi then is the last iterate).
   __device__ __forceinline__ bool solve(double xu, double xv, double& xi, double& eta) const {
     if (affine) {
       const double du = xu - m.c0u, dv = xv - m.c0v;
@@ -205,9 +229,9 @@ struct MapInverse {
       eta = i10 * du + i11 * dv;
       return true;
     }
-    const bool conv = coarse(xu, xv, xi, eta);
+    if (!coarse(xu, xv, xi, eta)) return newton64(xu, xv, xi, eta);
     polish(xu, xv, xi, eta);
-    return conv;
+    return true;
   }
 };
 

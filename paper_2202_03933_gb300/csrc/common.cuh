@@ -14,6 +14,11 @@
 namespace mortar {
 
 constexpr int kMaxPoly = 16;   // polygon vertex cap; convex quad vs quad needs <= 8
+// Largest block of the pair kernels.  They hold up to 255 registers per
+// thread, so 256 threads already fill the 64 K register file of an SM; a
+// 512-thread block would cap them at 128 registers and spill.
+constexpr int kMaxPairBlock = 256;
+constexpr size_t kMaxDynSmem = 227 * 1024;   // dynamic shared memory per block on sm_103a
 constexpr int kMaxRow = 256;   // CSR entries gathered per row before the slow path
 
 // Per-run numeric parameters, passed by value to the kernels.
@@ -31,7 +36,7 @@ struct RunParams {
   int32_t integration;    // 0 segment-based, 1 element-based
   int32_t rule_n;         // element-based rule: points per direction
   int32_t facing;         // facing test on candidate pairs
-  int32_t pad2;
+  int32_t watchdog_us;    // per-CTA time budget of the persistent pair kernels (0 = none)
 };
 
 // Slave element record (FP64 words).  Written once per evaluation by the
@@ -77,6 +82,7 @@ struct DevStatus {
   unsigned long long work_ctr3;    // work counter of the linearisation pair kernel
   unsigned long long nnzb_K;       // 3x3 blocks of the linearisation
   unsigned long long over_K;       // linearisation block buffer too small
+  unsigned long long nonfinite;    // elements with a non-finite node coordinate
   double J;
 };
 
@@ -235,6 +241,26 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+
+// Watchdog of the persistent pair kernels: a warp stops fetching work once
+// its CTA has run longer than the budget (watchdog_us > 0) and flags
+// st->timeout; the host then reports MORTAR_ERR_TIMEOUT and the context stays
+// usable (every run starts from cleared counters).
+struct Watchdog {
+  unsigned long long t0, budget_ns;
+  __device__ __forceinline__ explicit Watchdog(int32_t us)
+      : t0(global_ns()), budget_ns(us > 0 ? 1000ull * (unsigned long long)us : 0ull) {}
+  // warp-uniform: true if the budget ran out (lane 0 reads the clock)
+  __device__ __forceinline__ bool expired(unsigned long long* timeout_flag) const {
+    if (budget_ns == 0) return false;
+    int out = 0;
+    if ((threadIdx.x & 31) == 0 && global_ns() - t0 > budget_ns) {
+      out = 1;
+      atomicAdd(timeout_flag, 1ull);
+    }
+    return __shfl_sync(0xffffffffu, out, 0) != 0;
+  }
+};
 
 // Busy interval of this CTA of a persistent kernel (first / last thread
 // activity), recorded only when cta_t is non-null.

@@ -42,6 +42,7 @@ struct mortar_ctx {
   int32_t block_size = 0;     // pair kernels (0 = default)
   int32_t chunk_pairs = 0;    // pairs per work item of the one-pair-per-thread kernels (0 = default)
   int32_t rounds = 0;         // batched kernel: 32 * rounds pairs per warp batch (0 = default)
+  int32_t watchdog_us = 0;    // per-CTA time budget of the persistent pair kernels (0 = none)
 
   // ---- interface definition
   bool have_interface = false;
@@ -137,6 +138,7 @@ void launch_candidates(mortar_ctx* c);
 
 // k_integrate.cu
 void launch_integrate(mortar_ctx* c, const RunParams& rp);
+bool integrate_batched_fits(int rounds, int block);   // shared memory of the batched kernel fits
 
 // k_contact.cu
 void launch_contact_terms(mortar_ctx* c, bool with_ncp, double cpen);   // normals, gap (+ active, ncp)
@@ -162,6 +164,21 @@ void launch_tangent_blocks(mortar_ctx* c, const RunParams& rp);   // per-pair an
 void launch_tangent_rows(mortar_ctx* c, const RunParams& rp, int mode);   // 0: count + rowptr, 1: write
 
 RunParams run_params(const mortar_ctx* c);
+
+// Per element-type combination (slave NS, master NM nodes) parts of the pair
+// kernels.  Each is built as an object of its own from the same source file
+// with MORTAR_PAIR_NS / MORTAR_PAIR_NM defined, so the large kernel templates
+// compile in parallel; the main part of each file only dispatches to them.
+struct IntegrateArgs;
+template <int NS, int NM>
+void integrate_nsnm(const IntegrateArgs& a, const RunParams& rp, int n_sm, int variant, int block, int chunk,
+                    int rounds);
+template <int NS, int NM>
+void adjoint_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk, bool fused);
+template <int NS, int NM>
+void tangent_pairs_nsnm(mortar_ctx* c, const RunParams& rp);
+template <int NS, int NM>
+void tangent_rows_nsnm(mortar_ctx* c, const RunParams& rp, int mode);
 
 // Launchers on explicit pointers (no context), used by the no-allocation entry point.
 struct IntegrateArgs {

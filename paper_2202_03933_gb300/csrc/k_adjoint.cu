@@ -249,7 +249,7 @@ __device__ void adjoint_one(int64_t p, const int32_t* __restrict__ ps, const int
 }
 
 template <int NS, int NM, bool SEG, bool DUAL>
-__global__ void __launch_bounds__(kThreads) k_adjoint_pairs(
+__global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_pairs(
     const int32_t* __restrict__ ps, const int32_t* __restrict__ pm, const double* __restrict__ srec,
     const double* __restrict__ xs, const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
     const int32_t* __restrict__ conn_m, const double* __restrict__ lambda, RunParams rp, int64_t pair_cap,
@@ -259,7 +259,9 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_pairs(
   const int lane = threadIdx.x & 31;
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
+  const Watchdog wd(rp.watchdog_us);
   for (;;) {   // bounded: the shared counter only grows
+    if (wd.expired(&st->timeout)) break;
     int64_t base = 0;
     if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr2, (unsigned long long)chunk);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -557,25 +559,25 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
   J_out[p] = Jp;
 }
 
-constexpr int kAdjWarps = 4;
-
 template <int NS, int NM, bool SEG, bool DUAL, bool FWD, int R>
-__global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_batched(
+__global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
     const int32_t* __restrict__ ps, const int32_t* __restrict__ pm, const double* __restrict__ srec,
     const double* __restrict__ xs, const double* __restrict__ xm, const int32_t* __restrict__ conn_s,
     const int32_t* __restrict__ conn_m, const double* __restrict__ lambda, int64_t pair_cap,
     double* __restrict__ gs_out, double* __restrict__ gm_out, double* __restrict__ ab_out,
-    double* __restrict__ J_out, FwdOut fo, DevStatus* st, unsigned long long* cta_t) {
+    double* __restrict__ J_out, FwdOut fo, DevStatus* st, unsigned long long* cta_t, int32_t watchdog_us) {
   cta_mark(cta_t, 0);
   constexpr int B = 32 * R;
-  __shared__ uint8_t perm_s[kAdjWarps][B];
+  __shared__ uint8_t perm_s[kMaxPairBlock / 32][B];
   uint8_t* perm = perm_s[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   AdjCounters ctr;
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
+  const Watchdog wd(watchdog_us);
   for (;;) {   // bounded: the shared counter only grows
+    if (wd.expired(&st->timeout)) break;
     int64_t base = 0;
     if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr2, (unsigned long long)B);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -840,6 +842,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
   out[12] = Je;
 }
 
+#ifndef MORTAR_PAIR_NS
 // master element -> pairs (non-empty ones), counting sort + per-element sort
 __global__ void k_mp_count(const int32_t* __restrict__ pm, const uint8_t* __restrict__ flag, int64_t pair_cap,
                            int32_t* __restrict__ cnt, const DevStatus* st) {
@@ -947,9 +950,16 @@ __global__ void __launch_bounds__(256) k_J_final(const double* __restrict__ part
   }
   if (threadIdx.x == 0) st->J = sh[0];
 }
+#endif  // !MORTAR_PAIR_NS
 
+#ifdef MORTAR_PAIR_NS
 template <int NS, int NM, bool SEG, bool DUAL>
 void launch_pairs_t(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk) {
+  if (grid == 0) {   // persistent grid: every SM filled to the kernel's occupancy
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_pairs<NS, NM, SEG, DUAL>, (int)block, 0);
+    grid = (unsigned)(c->n_sm * (per_sm < 1 ? 1 : per_sm));
+  }
   k_adjoint_pairs<NS, NM, SEG, DUAL><<<grid, block, 0, c->stream>>>(
       c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
       c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->lambda.as<double>(), rp, c->pair_cap,
@@ -961,32 +971,37 @@ template <int NS, int NM, bool SEG, bool DUAL, bool FWD>
 void launch_batched_f(mortar_ctx* c, int rounds) {
   const FwdOut fo{c->Mblk.as<double>(), c->Dblk.as<double>(), c->flag.as<uint8_t>()};
   unsigned long long* cta_t = (FWD && c->timing && c->cta_t.p) ? c->cta_t.as<unsigned long long>() : nullptr;
+  const int block = c->block_size > 0 ? c->block_size : 128;
   auto go = [&](auto kern) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjWarps * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
     if (per_sm < 1) per_sm = 1;
     const unsigned grid = (unsigned)(c->n_sm * per_sm);
     if (cta_t) c->pair_grid = (int)grid;
-    kern<<<grid, kAdjWarps * 32, 0, c->stream>>>(
+    kern<<<grid, block, 0, c->stream>>>(
         c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
         c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->lambda.as<double>(), c->pair_cap,
         c->gs_pair.as<double>(), c->gm_pair.as<double>(), c->abar_pair.as<double>(), c->J_pair.as<double>(), fo,
-        c->dstat.as<DevStatus>(), cta_t);
+        c->dstat.as<DevStatus>(), cta_t, c->watchdog_us);
   };
   if (rounds <= 1) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 1>);
   else if (rounds == 2) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 2>);
   else go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 4>);
 }
 
+// The warp-batched adjoint always produces the forward blocks as well (the
+// run pipeline fuses the two whenever the batched schedule is selected); a
+// non-fused call only rewrites the same blocks.
 template <int NS, int NM, bool SEG, bool DUAL>
-void launch_batched_t(mortar_ctx* c, int rounds, bool fused) {
-  if (fused) launch_batched_f<NS, NM, SEG, DUAL, true>(c, rounds);
-  else launch_batched_f<NS, NM, SEG, DUAL, false>(c, rounds);
+void launch_batched_t(mortar_ctx* c, int rounds, bool) {
+  launch_batched_f<NS, NM, SEG, DUAL, true>(c, rounds);
 }
 
+}  // namespace
+
 template <int NS, int NM>
-void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk,
-                       bool fused) {
+void adjoint_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsigned block, int32_t chunk,
+                        bool fused) {
   const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
   if (c->variant == 1) {
     if (seg && dual) launch_pairs_t<NS, NM, true, true>(c, rp, grid, block, chunk);
@@ -1001,6 +1016,9 @@ void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid, unsign
   else if (dual) launch_batched_t<NS, NM, false, true>(c, rounds, fused);
   else launch_batched_t<NS, NM, false, false>(c, rounds, fused);
 }
+template void adjoint_pairs_nsnm<MORTAR_PAIR_NS, MORTAR_PAIR_NM>(mortar_ctx*, const RunParams&, unsigned, unsigned,
+                                                                  int32_t, bool);
+#else   // the main part: element adjoint, gathers, J, dispatch
 
 template <int NS>
 void launch_elems_ns(mortar_ctx* c, const RunParams& rp) {
@@ -1045,14 +1063,11 @@ bool adjoint_fuses_forward(const mortar_ctx* c) { return c->variant == 0; }
 void launch_adjoint_pairs(mortar_ctx* c, const RunParams& rp, bool fused) {
   const unsigned block = c->block_size > 0 ? (unsigned)c->block_size : 128u;
   const int32_t chunk = c->chunk_pairs > 0 ? c->chunk_pairs : 32;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint_pairs<4, 4, false, true>, (int)block, 0);
-  if (per_sm < 1) per_sm = 1;
-  const unsigned grid = (unsigned)(c->n_sm * per_sm);
-  if (c->nen_s == 4 && c->nen_m == 4) launch_pairs_nsnm<4, 4>(c, rp, grid, block, chunk, fused);
-  else if (c->nen_s == 4 && c->nen_m == 3) launch_pairs_nsnm<4, 3>(c, rp, grid, block, chunk, fused);
-  else if (c->nen_s == 3 && c->nen_m == 4) launch_pairs_nsnm<3, 4>(c, rp, grid, block, chunk, fused);
-  else launch_pairs_nsnm<3, 3>(c, rp, grid, block, chunk, fused);
+  const unsigned grid = 0;   // the one-pair-per-thread kernels size their own grid
+  if (c->nen_s == 4 && c->nen_m == 4) adjoint_pairs_nsnm<4, 4>(c, rp, grid, block, chunk, fused);
+  else if (c->nen_s == 4 && c->nen_m == 3) adjoint_pairs_nsnm<4, 3>(c, rp, grid, block, chunk, fused);
+  else if (c->nen_s == 3 && c->nen_m == 4) adjoint_pairs_nsnm<3, 4>(c, rp, grid, block, chunk, fused);
+  else adjoint_pairs_nsnm<3, 3>(c, rp, grid, block, chunk, fused);
 }
 
 void launch_adjoint_rest(mortar_ctx* c, const RunParams& rp) {
@@ -1082,5 +1097,6 @@ void launch_adjoint_rest(mortar_ctx* c, const RunParams& rp) {
                                                c->J_part.as<double>(), st);
   k_J_final<<<1, 256, 0, c->stream>>>(c->J_part.as<double>(), st);
 }
+#endif  // MORTAR_PAIR_NS
 
 }  // namespace mortar

@@ -128,13 +128,14 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
             double a1, a2;
             if (mi.affine) {
               mi.solve(xu, xv, a1, a2);
-            } else {   // FP32 iterate first: points clearly outside skip the FP64 step
-              if (!mi.coarse(xu, xv, a1, a2)) continue;
+            } else if (mi.coarse(xu, xv, a1, a2)) {   // FP32 iterate first: points clearly outside skip the FP64 step
               const bool near = NM == 4
                   ? (fabs(a1) <= 1.0 + 1e-5 && fabs(a2) <= 1.0 + 1e-5)
                   : (a1 >= -1e-5 && a2 >= -1e-5 && a1 + a2 <= 1.0 + 1e-5);
               if (!near) continue;
               mi.polish(xu, xv, a1, a2);
+            } else if (!mi.newton64(xu, xv, a1, a2)) {   // FP32 did not settle: FP64 Newton from its iterate
+              continue;
             }
             const bool inside = NM == 4
                 ? (fabs(a1) <= 1.0 + kInsideTol && fabs(a2) <= 1.0 + kInsideTol)

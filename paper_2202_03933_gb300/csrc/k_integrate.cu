@@ -176,7 +176,7 @@ __device__ __forceinline__ void integrate_one(int64_t p, const int32_t* __restri
 }
 
 template <int NS, int NM, bool SEG>
-__global__ void __launch_bounds__(128) k_integrate(const int32_t* __restrict__ ps, const int32_t* __restrict__ pm,
+__global__ void __launch_bounds__(kMaxPairBlock) k_integrate(const int32_t* __restrict__ ps, const int32_t* __restrict__ pm,
                                                    const double* __restrict__ srec, const double* __restrict__ xm,
                                                    const int32_t* __restrict__ conn_m, RunParams rp,
                                                    double* __restrict__ Mblk, double* __restrict__ Dblk,
@@ -186,8 +186,10 @@ __global__ void __launch_bounds__(128) k_integrate(const int32_t* __restrict__ p
   const int lane = threadIdx.x & 31;
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
+  const Watchdog wd(rp.watchdog_us);
   // bounded work loop: the counter only grows, so at most n / chunk fetches succeed
   for (;;) {
+    if (wd.expired(&st->timeout)) break;
     int64_t base = 0;
     if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr, (unsigned long long)chunk);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -217,7 +219,7 @@ struct BatchSmem {   // per-warp shared layout for 32 R pairs
 };
 
 template <int NS, int NM, bool SEG, int R>
-__global__ void __launch_bounds__(128) k_integrate_batched(
+__global__ void __launch_bounds__(kMaxPairBlock) k_integrate_batched(
     const int32_t* __restrict__ ps, const int32_t* __restrict__ pm, const double* __restrict__ srec,
     const double* __restrict__ xm, const int32_t* __restrict__ conn_m, RunParams rp, double* __restrict__ Mblk,
     double* __restrict__ Dblk, uint8_t* __restrict__ flag, int64_t pair_cap, DevStatus* st,
@@ -242,7 +244,9 @@ __global__ void __launch_bounds__(128) k_integrate_batched(
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
   const unsigned lt_mask = (1u << lane) - 1u;
+  const Watchdog wd(rp.watchdog_us);
   for (;;) {   // bounded: the shared counter only grows
+    if (wd.expired(&st->timeout)) break;
     int64_t base = 0;
     if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr, (unsigned long long)B);
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -393,9 +397,9 @@ __global__ void __launch_bounds__(128) k_integrate_batched(
   cta_mark(cta_t, 1);
 }
 
+#ifdef MORTAR_PAIR_NS
 template <int NS, int NM, bool SEG, int R>
-void launch_batched_t(const IntegrateArgs& a, const RunParams& rp, int n_sm) {
-  constexpr int kWarps = 4;
+void launch_batched_t(const IntegrateArgs& a, const RunParams& rp, int n_sm, int kWarps) {
   const size_t shm = (size_t)kWarps * BatchSmem<R>::kBytes;
   auto kern = k_integrate_batched<NS, NM, SEG, R>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -409,42 +413,54 @@ void launch_batched_t(const IntegrateArgs& a, const RunParams& rp, int n_sm) {
 }
 
 template <int NS, int NM, bool SEG>
-void launch_batched_r(const IntegrateArgs& a, const RunParams& rp, int n_sm, int rounds) {
-  if (rounds <= 1) launch_batched_t<NS, NM, SEG, 1>(a, rp, n_sm);
-  else if (rounds == 2) launch_batched_t<NS, NM, SEG, 2>(a, rp, n_sm);
-  else launch_batched_t<NS, NM, SEG, 4>(a, rp, n_sm);
+void launch_batched_r(const IntegrateArgs& a, const RunParams& rp, int n_sm, int rounds, int warps) {
+  if (rounds <= 1) launch_batched_t<NS, NM, SEG, 1>(a, rp, n_sm, warps);
+  else if (rounds == 2) launch_batched_t<NS, NM, SEG, 2>(a, rp, n_sm, warps);
+  else launch_batched_t<NS, NM, SEG, 4>(a, rp, n_sm, warps);
 }
 
-template <int NS, int NM>
-void launch_any(const IntegrateArgs& a, const RunParams& rp, int n_sm, int variant, int block, int chunk,
-                int rounds) {
-  const bool seg = rp.d_domain == 1;
-  if (variant == 1) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NS, NM, false>, block, 0);
-    if (per_sm < 1) per_sm = 1;
-    const unsigned grid = (unsigned)(n_sm * per_sm);
-    if (seg)
-      k_integrate<NS, NM, true><<<grid, block, 0, a.stream>>>(a.ps, a.pm, a.srec, a.xm, a.conn_m, rp, a.Mblk,
-                                                             a.Dblk, a.flag, a.pair_cap, chunk, a.st);
-    else
-      k_integrate<NS, NM, false><<<grid, block, 0, a.stream>>>(a.ps, a.pm, a.srec, a.xm, a.conn_m, rp, a.Mblk,
-                                                              a.Dblk, a.flag, a.pair_cap, chunk, a.st);
-    return;
-  }
-  if (seg) launch_batched_r<NS, NM, true>(a, rp, n_sm, rounds);
-  else launch_batched_r<NS, NM, false>(a, rp, n_sm, rounds);
-}
-
-void launch_dispatch(const IntegrateArgs& a, const RunParams& rp, int nen_s, int nen_m, int n_sm, int variant,
-                     int block, int chunk, int rounds) {
-  if (nen_s == 4 && nen_m == 4) launch_any<4, 4>(a, rp, n_sm, variant, block, chunk, rounds);
-  else if (nen_s == 4 && nen_m == 3) launch_any<4, 3>(a, rp, n_sm, variant, block, chunk, rounds);
-  else if (nen_s == 3 && nen_m == 4) launch_any<3, 4>(a, rp, n_sm, variant, block, chunk, rounds);
-  else launch_any<3, 3>(a, rp, n_sm, variant, block, chunk, rounds);
+template <int NS, int NM, bool SEG>
+void launch_one_pair_per_thread(const IntegrateArgs& a, const RunParams& rp, int n_sm, int block, int chunk) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate<NS, NM, SEG>, block, 0);
+  if (per_sm < 1) per_sm = 1;
+  const unsigned grid = (unsigned)(n_sm * per_sm);
+  k_integrate<NS, NM, SEG><<<grid, block, 0, a.stream>>>(a.ps, a.pm, a.srec, a.xm, a.conn_m, rp, a.Mblk, a.Dblk,
+                                                         a.flag, a.pair_cap, chunk, a.st);
 }
 
 }  // namespace
+
+template <int NS, int NM>
+void integrate_nsnm(const IntegrateArgs& a, const RunParams& rp, int n_sm, int variant, int block, int chunk,
+                    int rounds) {
+  const bool seg = rp.d_domain == 1;
+  if (variant == 1) {
+    if (seg) launch_one_pair_per_thread<NS, NM, true>(a, rp, n_sm, block, chunk);
+    else launch_one_pair_per_thread<NS, NM, false>(a, rp, n_sm, block, chunk);
+    return;
+  }
+  if (seg) launch_batched_r<NS, NM, true>(a, rp, n_sm, rounds, block / 32);
+  else launch_batched_r<NS, NM, false>(a, rp, n_sm, rounds, block / 32);
+}
+template void integrate_nsnm<MORTAR_PAIR_NS, MORTAR_PAIR_NM>(const IntegrateArgs&, const RunParams&, int, int, int,
+                                                              int, int);
+#else   // the main part: dispatch
+
+void launch_dispatch(const IntegrateArgs& a, const RunParams& rp, int nen_s, int nen_m, int n_sm, int variant,
+                     int block, int chunk, int rounds) {
+  if (nen_s == 4 && nen_m == 4) integrate_nsnm<4, 4>(a, rp, n_sm, variant, block, chunk, rounds);
+  else if (nen_s == 4 && nen_m == 3) integrate_nsnm<4, 3>(a, rp, n_sm, variant, block, chunk, rounds);
+  else if (nen_s == 3 && nen_m == 4) integrate_nsnm<3, 4>(a, rp, n_sm, variant, block, chunk, rounds);
+  else integrate_nsnm<3, 3>(a, rp, n_sm, variant, block, chunk, rounds);
+}
+
+}  // namespace
+
+bool integrate_batched_fits(int rounds, int block) {
+  const size_t per_warp = rounds <= 1 ? BatchSmem<1>::kBytes : (rounds == 2 ? BatchSmem<2>::kBytes : BatchSmem<4>::kBytes);
+  return block >= 32 && block <= kMaxPairBlock && (size_t)(block / 32) * per_warp <= kMaxDynSmem;
+}
 
 void launch_integrate_raw(const IntegrateArgs& a, const RunParams& rp, int nen_s, int nen_m, int n_sm) {
   launch_dispatch(a, rp, nen_s, nen_m, n_sm, 0, 128, 32, 2);
@@ -469,5 +485,6 @@ void launch_integrate(mortar_ctx* c, const RunParams& rp) {
   const int rounds = c->rounds > 0 ? c->rounds : 2;
   launch_dispatch(a, rp, c->nen_s, c->nen_m, c->n_sm, c->variant, block, chunk, rounds);
 }
+#endif  // MORTAR_PAIR_NS
 
 }  // namespace mortar

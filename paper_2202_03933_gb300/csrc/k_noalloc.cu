@@ -149,6 +149,8 @@ extern "C" int mortar_integrate_pairs_static(const mortar_options* o, void* stre
   rp.bin_margin = o->bin_margin;
   rp.integration = 0;   // segment-based only: element-based integration needs the pair offsets of a search
   rp.rule_n = 0;
+  rp.facing = 0;
+  rp.watchdog_us = 0;
   launch_slave_precompute_raw(xs, conn_s, n_slave_elems, type_s, rp, srec, De, box, status, st);
   if (n_pairs > 0) {
     IntegrateArgs a{pair_s, pair_m, srec, xm, conn_m, M_blocks, D_blocks, nonempty, n_pairs, status, st};

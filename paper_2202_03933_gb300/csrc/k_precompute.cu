@@ -69,17 +69,26 @@ __device__ __forceinline__ void elem_point(int k, double& xi, double& eta, doubl
   }
 }
 
+// An element with a non-finite node coordinate gets an all-NaN box: every
+// box-overlap test (closed <= compares) is false for it, so it has no pairs,
+// and the grid's min / max reductions (fmin / fmax) skip it.
+__device__ __forceinline__ void set_nan_box(double* b) {
+  const double q = __longlong_as_double(0x7ff8000000000000LL);
+  for (int k = 0; k < 7; ++k) b[k] = q;
+}
+
 template <int NS>
 __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     const double* __restrict__ xs, const int32_t* __restrict__ conn, int64_t Es, RunParams rp,
     double* __restrict__ srec, double* __restrict__ De, double* __restrict__ box, DevStatus* st) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool degenerate = false;
+  bool degenerate = false, bad = false;
   if (e < Es) {
     V3 X[4];
     for (int a = 0; a < NS; ++a) {
       const int64_t n = conn[NS * e + a];
       X[a] = {xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]};
+      bad |= !(isfinite(X[a].x) && isfinite(X[a].y) && isfinite(X[a].z));
     }
     // ---- auxiliary plane at the element centre
     V3 x0, g1, g2;
@@ -151,7 +160,17 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     r[SR_EPSIN] = rp.clip_tol_rel * h * h;
     r[SR_EPSM2] = em * em;
     r[SR_EPSA] = rp.area_tol_rel * (0.5 * fabs(area2));
-    degenerate = !(ln > 0.0) || !(le > 0.0) || !(fabs(area2) > 0.0) || !isfinite(h);
+    // an inverted (folded) quad4: its projected corners do not form a convex
+    // polygon of one orientation, and its Jacobian changes sign inside
+    bool folded = false;
+    if constexpr (NS == 4) {
+      for (int a = 0; a < 4; ++a) {
+        const int a1 = (a + 1) & 3, a2 = (a + 2) & 3;
+        const double c = cross2(pu[a1] - pu[a], pv[a1] - pv[a], pu[a2] - pu[a1], pv[a2] - pv[a1]);
+        folded |= !(c * area2 > 0.0);
+      }
+    }
+    degenerate = !(ln > 0.0) || !(le > 0.0) || !(fabs(area2) > 0.0) || !isfinite(h) || folded;
     if (degenerate) r[SR_EPSIN] = -1.0;   // marks the element; its pairs integrate to nothing
     // ---- element integrals Me[a][b] = int N_a N_b, Dh[a] = int N_a (surface measure)
     // An element whose bilinear term is negligible (parallelogram, any tri3) has a
@@ -265,21 +284,29 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     }
     b[6] = h;
     b[7] = 0.0;
+    if (bad) {
+      set_nan_box(b);
+      r[SR_EPSIN] = -1.0;
+      degenerate = true;
+    }
   }
   block_count_add(&st->degenerate, degenerate ? 1ull : 0ull);
+  block_count_add(&st->nonfinite, bad ? 1ull : 0ull);
 }
 
 template <int NM>
 __global__ void __launch_bounds__(kThreads) k_master_boxes(const double* __restrict__ xm,
                                                             const int32_t* __restrict__ conn, int64_t Em,
                                                             double delta, double* __restrict__ box,
-                                                            double* __restrict__ nrm) {
+                                                            double* __restrict__ nrm, DevStatus* st) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Em) return;
+  bool bad = false;
+  if (e < Em) {
   V3 X[4];
   for (int a = 0; a < NM; ++a) {
     const int64_t n = conn[NM * e + a];
     X[a] = {xm[3 * n], xm[3 * n + 1], xm[3 * n + 2]};
+    bad |= !(isfinite(X[a].x) && isfinite(X[a].y) && isfinite(X[a].z));
   }
   double lo[3] = {X[0].x, X[0].y, X[0].z}, hi[3] = {X[0].x, X[0].y, X[0].z};
   double h2 = 0.0;
@@ -316,6 +343,9 @@ __global__ void __launch_bounds__(kThreads) k_master_boxes(const double* __restr
     nrm[3 * e + 1] = n.y / l;
     nrm[3 * e + 2] = n.z / l;
   }
+  if (bad) set_nan_box(b);
+  }
+  block_count_add(&st->nonfinite, bad ? 1ull : 0ull);
 }
 
 // One block per chunk: min of lo, max of hi, max of h over its elements.
@@ -460,7 +490,7 @@ RunParams run_params(const mortar_ctx* c) {
   rp.integration = c->opt.integration;
   rp.rule_n = c->opt.element_rule_n;
   rp.facing = c->opt.facing_test;
-  rp.pad2 = 0;
+  rp.watchdog_us = c->watchdog_us;
   return rp;
 }
 
@@ -494,10 +524,12 @@ void launch_master_boxes(mortar_ctx* c, const RunParams& rp) {
   const unsigned g = (unsigned)((c->Em + kThreads - 1) / kThreads);
   if (c->nen_m == 4)
     k_master_boxes<4><<<g, kThreads, 0, c->stream>>>(c->xm.as<double>(), c->conn_m.as<int32_t>(), c->Em, rp.delta,
-                                                     c->box_m.as<double>(), rp.facing ? c->nrm_m.as<double>() : nullptr);
+                                                     c->box_m.as<double>(), rp.facing ? c->nrm_m.as<double>() : nullptr,
+                                                     c->dstat.as<DevStatus>());
   else
     k_master_boxes<3><<<g, kThreads, 0, c->stream>>>(c->xm.as<double>(), c->conn_m.as<int32_t>(), c->Em, rp.delta,
-                                                     c->box_m.as<double>(), rp.facing ? c->nrm_m.as<double>() : nullptr);
+                                                     c->box_m.as<double>(), rp.facing ? c->nrm_m.as<double>() : nullptr,
+                                                     c->dstat.as<DevStatus>());
 }
 
 void launch_grid_params(mortar_ctx* c, const RunParams& rp) {

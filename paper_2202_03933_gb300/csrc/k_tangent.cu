@@ -50,6 +50,7 @@ struct TanArgs {
   double* Op;          // per pair 12: O_e,c (dual LMs)
   int64_t pair_cap;
   DevStatus* st;
+  int32_t watchdog_us;
 };
 
 // Quadrature-point data one lane computes and the other two lanes of its
@@ -342,7 +343,9 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_pairs(TanArgs g) {
   const int64_t n = ok ? (int64_t)min((unsigned long long)g.pair_cap, st->n_pairs) : 0;
   const int64_t items = (n + B - 1) / B;
   GPX* gx = reinterpret_cast<GPX*>(tan_acc + 16 * 4 * kTanThreads) + 32 * (threadIdx.x >> 5);
+  const Watchdog wd(g.watchdog_us);
   for (;;) {   // bounded: the shared counter only grows
+    if (wd.expired(&st->timeout)) break;
     int64_t item = 0;
     if (lane == 0) item = (int64_t)atomicAdd(&st->work_ctr3, 1ull);
     item = __shfl_sync(0xffffffffu, item, 0);
@@ -775,6 +778,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_tangent_rows_warp(TanRowSour
   }
 }
 
+#ifdef MORTAR_PAIR_NS
 __global__ void k_tangent_nnzb(const int64_t* __restrict__ rp, int64_t N, DevStatus* st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) st->nnzb_K = (unsigned long long)rp[N];
 }
@@ -784,7 +788,7 @@ void launch_pairs_t(mortar_ctx* c) {
   TanArgs g{c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
             c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->tan_ys.as<double>(),
             c->tan_ym.as<double>(), c->tan_Kp.as<double>(), c->tan_Op.as<double>(), c->tan_pair_cap,
-            c->dstat.as<DevStatus>()};
+            c->dstat.as<DevStatus>(), c->watchdog_us};
   // batches of 160 pairs: 16 full rounds of 10 pair groups (lanes 30, 31 idle)
   auto kern = k_tangent_pairs<NS, NM, SEG, DUAL, 5>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTanSmem);
@@ -792,24 +796,6 @@ void launch_pairs_t(mortar_ctx* c) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTanThreads, kTanSmem);
   if (per_sm < 1) per_sm = 1;
   kern<<<(unsigned)(c->n_sm * per_sm), kTanThreads, kTanSmem, c->stream>>>(g);
-}
-
-template <int NS, int NM>
-void launch_pairs_nsnm(mortar_ctx* c, const RunParams& rp) {
-  const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
-  if (seg && dual) launch_pairs_t<NS, NM, true, true>(c);
-  else if (seg) launch_pairs_t<NS, NM, true, false>(c);
-  else if (dual) launch_pairs_t<NS, NM, false, true>(c);
-  else launch_pairs_t<NS, NM, false, false>(c);
-}
-
-template <int NS, bool DUAL, bool ELEMD>
-void launch_elems_t(mortar_ctx* c) {
-  if (c->Es == 0) return;
-  k_tangent_elems<NS, DUAL, ELEMD><<<(unsigned)((c->Es + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(
-      c->xs.as<double>(), c->conn_s.as<int32_t>(), c->tan_ys.as<double>(), c->srec.as<double>(),
-      c->pair_off.as<int64_t>(), c->flag.as<uint8_t>(), c->tan_Op.as<double>(), c->Es, c->tan_Ke.as<double>(),
-      c->dstat.as<DevStatus>());
 }
 
 template <int NS, int NM, bool SEG, bool DUAL, bool ELEMD>
@@ -838,13 +824,37 @@ void rows_t(mortar_ctx* c, int mode) {
   }
 }
 
+}  // namespace
+
 template <int NS, int NM>
-void rows_nsnm(mortar_ctx* c, const RunParams& rp, int mode) {
+void tangent_pairs_nsnm(mortar_ctx* c, const RunParams& rp) {
+  const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
+  if (seg && dual) launch_pairs_t<NS, NM, true, true>(c);
+  else if (seg) launch_pairs_t<NS, NM, true, false>(c);
+  else if (dual) launch_pairs_t<NS, NM, false, true>(c);
+  else launch_pairs_t<NS, NM, false, false>(c);
+}
+
+template <int NS, int NM>
+void tangent_rows_nsnm(mortar_ctx* c, const RunParams& rp, int mode) {
   const bool seg = rp.d_domain == 1, dual = rp.lm == 1;
   if (seg && dual) rows_t<NS, NM, true, true, false>(c, mode);
   else if (seg) rows_t<NS, NM, true, false, false>(c, mode);
   else if (dual) rows_t<NS, NM, false, true, true>(c, mode);
   else rows_t<NS, NM, false, false, true>(c, mode);
+}
+
+template void tangent_pairs_nsnm<MORTAR_PAIR_NS, MORTAR_PAIR_NM>(mortar_ctx*, const RunParams&);
+template void tangent_rows_nsnm<MORTAR_PAIR_NS, MORTAR_PAIR_NM>(mortar_ctx*, const RunParams&, int);
+#else   // the main part: element blocks, dispatch
+
+template <int NS, bool DUAL, bool ELEMD>
+void launch_elems_t(mortar_ctx* c) {
+  if (c->Es == 0) return;
+  k_tangent_elems<NS, DUAL, ELEMD><<<(unsigned)((c->Es + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(
+      c->xs.as<double>(), c->conn_s.as<int32_t>(), c->tan_ys.as<double>(), c->srec.as<double>(),
+      c->pair_off.as<int64_t>(), c->flag.as<uint8_t>(), c->tan_Op.as<double>(), c->Es, c->tan_Ke.as<double>(),
+      c->dstat.as<DevStatus>());
 }
 
 }  // namespace
@@ -854,10 +864,10 @@ bool tangent_needs_elems(const mortar_ctx* c) {
 }
 
 void launch_tangent_blocks(mortar_ctx* c, const RunParams& rp) {
-  if (c->nen_s == 4 && c->nen_m == 4) launch_pairs_nsnm<4, 4>(c, rp);
-  else if (c->nen_s == 4 && c->nen_m == 3) launch_pairs_nsnm<4, 3>(c, rp);
-  else if (c->nen_s == 3 && c->nen_m == 4) launch_pairs_nsnm<3, 4>(c, rp);
-  else launch_pairs_nsnm<3, 3>(c, rp);
+  if (c->nen_s == 4 && c->nen_m == 4) tangent_pairs_nsnm<4, 4>(c, rp);
+  else if (c->nen_s == 4 && c->nen_m == 3) tangent_pairs_nsnm<4, 3>(c, rp);
+  else if (c->nen_s == 3 && c->nen_m == 4) tangent_pairs_nsnm<3, 4>(c, rp);
+  else tangent_pairs_nsnm<3, 3>(c, rp);
   if (!tangent_needs_elems(c)) return;
   const bool elemd = rp.d_domain == 0, dual = rp.lm == 1;
   if (c->nen_s == 4) {
@@ -872,10 +882,11 @@ void launch_tangent_blocks(mortar_ctx* c, const RunParams& rp) {
 }
 
 void launch_tangent_rows(mortar_ctx* c, const RunParams& rp, int mode) {
-  if (c->nen_s == 4 && c->nen_m == 4) rows_nsnm<4, 4>(c, rp, mode);
-  else if (c->nen_s == 4 && c->nen_m == 3) rows_nsnm<4, 3>(c, rp, mode);
-  else if (c->nen_s == 3 && c->nen_m == 4) rows_nsnm<3, 4>(c, rp, mode);
-  else rows_nsnm<3, 3>(c, rp, mode);
+  if (c->nen_s == 4 && c->nen_m == 4) tangent_rows_nsnm<4, 4>(c, rp, mode);
+  else if (c->nen_s == 4 && c->nen_m == 3) tangent_rows_nsnm<4, 3>(c, rp, mode);
+  else if (c->nen_s == 3 && c->nen_m == 4) tangent_rows_nsnm<3, 4>(c, rp, mode);
+  else tangent_rows_nsnm<3, 3>(c, rp, mode);
 }
+#endif  // MORTAR_PAIR_NS
 
 }  // namespace mortar

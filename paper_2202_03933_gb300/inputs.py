@@ -154,6 +154,25 @@ def planar_noisy(ns: int, nm: int, lm: int, seed: int, name: str, noise: float =
                      info={"ns": ns, "nm": nm, "noise": noise, "seed": seed})
 
 
+def kite_master(ns: int, nm: int, d: float, lm: int = LM_STANDARD, name: str = "kite") -> Interface:
+    """ns x ns quad4 slave vs an nm x nm master grid whose interior nodes with
+    even i + j are moved by (d h_m, d h_m): every master quad keeps two opposite
+    corners in place and has the other two moved along the same diagonal, a
+    convex bilinear quad whose corner angle approaches 180 degrees as d -> 0.5
+    (strongly distorted but valid elements)."""
+    xs = grid_nodes(ns, ns)
+    cs = grid_quad4(ns, ns)
+    xm = grid_nodes(nm, nm)
+    n = nm + 1
+    i = np.arange(xm.shape[0]) % n
+    j = np.arange(xm.shape[0]) // n
+    sel = (i > 0) & (i < nm) & (j > 0) & (j < nm) & ((i + j) % 2 == 0)
+    xm[sel, 0] += d / nm
+    xm[sel, 1] += d / nm
+    return Interface(name, xs, cs, QUAD4, xm, grid_quad4(nm, nm), QUAD4, lm=lm, delta=1e-9,
+                     info={"ns": ns, "nm": nm, "kite_d": d})
+
+
 def planar_8x7() -> Interface:
     """8x8 vs 7x7 quad4, +-0.1 h_m in-plane master noise, standard LMs."""
     return planar_noisy(8, 7, LM_STANDARD, SEED_BASE + 1, "planar_8x7")

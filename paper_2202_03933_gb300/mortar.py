@@ -296,18 +296,24 @@ class Mortar:
     def set_timing(self, on: bool = True):
         call("mortar_set_timing", self.h, 1 if on else 0)
 
+    def set_watchdog(self, us: int = 0):
+        """Time budget of the persistent pair kernels in microseconds (0 = none)."""
+        call("mortar_set_watchdog", self.h, int(us))
+
     def set_launch(self, variant: int = 0, block_size: int = 0, chunk_pairs: int = 0, rounds: int = 0):
         call("mortar_set_launch", self.h, variant, block_size, chunk_pairs, rounds)
 
     def autotune(self, lam=None) -> dict:
         """Pick the fastest launch shape for this workload (see mortar_autotune)."""
-        v, r, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        v, r, b, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
         if lam is None:
-            call("mortar_autotune", self.h, None, 0, ctypes.byref(v), ctypes.byref(r), ctypes.byref(t))
+            call("mortar_autotune", self.h, None, 0, ctypes.byref(v), ctypes.byref(r), ctypes.byref(b),
+                 ctypes.byref(t))
         else:
             p, k, d = _ptr_in(lam, np.float64)
-            call("mortar_autotune", self.h, p, d, ctypes.byref(v), ctypes.byref(r), ctypes.byref(t))
-        return {"variant": v.value, "rounds": r.value, "ms": t.value}
+            call("mortar_autotune", self.h, p, d, ctypes.byref(v), ctypes.byref(r), ctypes.byref(b),
+                 ctypes.byref(t))
+        return {"variant": v.value, "rounds": r.value, "block": b.value, "ms": t.value}
 
 
 def evaluate(xs, conn_s, xm, conn_m, lm: int = LM_STANDARD, d_domain: int = D_ELEMENT, delta: float = 1e-9):

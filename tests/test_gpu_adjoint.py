@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2202_03933_gb300 import inputs
-from gpu_util import grad_term_scale
+from gpu_util import grad_parity, grad_sensitivity, grad_term_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +46,7 @@ def cases():
         ("nonplanar_dual", _nonplanar(inputs.planar_noisy(10, 9, 1, 61, "np")), 0),
         ("tri_slave", _swap(inputs.mixed_tri(12, 9, name="ts")), 0),
         ("tri_slave_seg_dual", _swap(inputs.mixed_tri(12, 9, lm=1, name="tsd")), 1),
+        ("kite_master_dual_seg", inputs.kite_master(16, 13, 0.45, lm=1), 1),
     ]
 
 
@@ -167,6 +168,68 @@ def test_full_size_mixed_adjoint(mt, orc):
     _grad_parity(gs, gm, rs, rm)
 
 
+def test_full_size_cylinder_adjoint(mt, orc):
+    """cylinder_200x173 (curved, dual LMs) with the adjoint in its graph: the
+    full gradient (lambda on every slave node) against the oracle's, at the
+    two-term scale of R16 (the slave and master terms nearly cancel on the
+    curved surface)."""
+    import os
+    itf = inputs.cylinder_patch()
+    lam = np.random.default_rng(13).uniform(-1, 1, itf.xs.shape)
+    m = mt.Mortar(lm=itf.lm, delta=itf.delta)
+    m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+    m.run_graph(lam)
+    m.run_graph(lam)
+    J, gs, gm = m.gradient()
+    s, mm = m.pairs()
+    o = orc.make_opts(lm=itf.lm, delta=itf.delta, n_threads=os.cpu_count() or 1)
+    Jr, rs, rm = orc.weighted_gap_grad(itf, lam, s, mm, o)
+    scale = grad_term_scale(orc, itf, lam, s, mm, o)
+    grad_parity(gs, gm, rs, rm, scale, lambda: grad_sensitivity(orc, itf, lam, s, mm, o))
+    assert abs(J - Jr) <= 1e-12 * (np.sum(np.abs(itf.xs * rs)) + np.sum(np.abs(itf.xm * rm)))
+
+
+def test_full_size_mixed_central_differences(mt):
+    """mixed_300x400 itself: the GPU gradient against central differences of
+    the GPU's J at step 1e-6 on 64 random coordinates (half slave, half master).
+
+    J = sum_j lam_j . r_j(X) and r_j depends on a coordinate X_i only through
+    the pairs that contain node i, so the difference quotient of J equals that
+    of J restricted to lam_j of the slave nodes within 3 slave element widths
+    of node i (in the plane); the restriction keeps the rounding of the
+    ~90,000 unaffected terms out of the quotient.  The gradient compared is
+    the one of the full J."""
+    itf = inputs.mixed_tri()
+    lam = np.random.default_rng(17).uniform(-1, 1, itf.xs.shape)
+    m = mt.Mortar(lm=0, delta=itf.delta)
+    m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+    J, gs, gm = m.weighted_gap_grad(lam)
+    scale = max(np.abs(gs).max(), np.abs(gm).max())
+    hs = 1.0 / itf.info["ns"]
+    rng = np.random.default_rng(19)
+    h = 1e-6
+    xs0, xm0 = itf.xs.copy(), itf.xm.copy()
+    worst = 0.0
+    for k in range(64):
+        side = "s" if k % 2 == 0 else "m"
+        X = xs0 if side == "s" else xm0
+        i = int(rng.integers(0, X.shape[0]))
+        c = int(rng.integers(0, 3))
+        near = np.hypot(xs0[:, 0] - X[i, 0], xs0[:, 1] - X[i, 1]) <= 3.0 * hs
+        lam_loc = np.where(near[:, None], lam, 0.0)
+        vals = []
+        for sgn in (1, -1):
+            xs, xm = xs0.copy(), xm0.copy()
+            (xs if side == "s" else xm)[i, c] += sgn * h
+            m.set_coordinates(xs, xm)
+            vals.append(m.weighted_gap_grad(lam_loc)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        g = (gs if side == "s" else gm)[i, c]
+        worst = max(worst, abs(fd - g) / scale)
+        assert abs(fd - g) <= 1e-6 * scale, (side, i, c, fd, g)
+    m.set_coordinates(xs0, xm0)
+
+
 def test_full_size_planar_2000_adjoint_sampled(mt, orc):
     """The benchmark workload with lambda nonzero on a scattered 0.5 % of slave
     nodes: the oracle then needs only the pairs of slave elements touching
@@ -190,8 +253,8 @@ def test_full_size_planar_2000_adjoint_sampled(mt, orc):
     assert abs(J - Jr) <= 1e-12 * np.abs(rs).max()
 
 
-@pytest.mark.parametrize("variant,rounds", [(1, 0), (0, 1), (0, 4)])
-def test_adjoint_launch_variants(mt, orc, variant, rounds):
+@pytest.mark.parametrize("variant,rounds,block", [(1, 0, 64), (1, 0, 256), (0, 1, 256), (0, 4, 64)])
+def test_adjoint_launch_variants(mt, orc, variant, rounds, block):
     """Both adjoint schedules give the oracle's gradient (bilinear and tri3
     masters, dual segment mode, warped slave)."""
     warped = inputs.planar_noisy(13, 11, 1, 46, "w")
@@ -205,7 +268,7 @@ def test_adjoint_launch_variants(mt, orc, variant, rounds):
         lam = np.random.default_rng(9).uniform(-1, 1, itf.xs.shape)
         m = mt.Mortar(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
         m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
-        m.set_launch(variant=variant, rounds=rounds)
+        m.set_launch(variant=variant, block_size=block, rounds=rounds)
         J, gs, gm = m.weighted_gap_grad(lam)
         s, mm = m.pairs()
         o = orc.make_opts(lm=itf.lm, d_domain=d_domain, delta=itf.delta, n_threads=8)

@@ -1,7 +1,7 @@
 """GPU parity of element-based integration (Sec. 1, Sec. 2.3) against the oracle.
 
 Same candidate pairs, same point ownership (first covering master in pair
-order), identical CSR patterns, values within 1e-12 (csr_parity), per-pair
+order), identical CSR patterns, values within 1e-12 (forward_parity), per-pair
 blocks within 1e-12; determinism and graph replay; sampled rows at the
 profiling size; the gradient and linearisation refuse element-based contexts.
 """
@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2202_03933_gb300 import inputs
-from gpu_util import blocks_parity, csr_parity
+from gpu_util import blocks_parity, forward_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +41,7 @@ def cases():
         ("tri_slave", _swap(inputs.mixed_tri(9, 7, name="ts")), 0, 8),
         ("tri_slave_seg_dual", _swap(inputs.mixed_tri(9, 7, lm=1, name="tsd")), 1, 6),
         ("noisy_slave_dual", _swap(inputs.planar_noisy(7, 9, 1, 43, "ns", noise=0.2)), 0, 8),
+        ("kite_master", inputs.kite_master(9, 7, 0.45), 0, 8),
     ]
 
 
@@ -59,8 +60,8 @@ def test_element_based_matches_oracle(mt, orc, name, itf, d_domain, n):
     blocks_parity(Mb, rMb)
     if d_domain == 1:
         blocks_parity(Db, rDb)
-    csr_parity(m.scipy(mt.MATRIX_M), M)
-    csr_parity(m.scipy(mt.MATRIX_D), D)
+    forward_parity(m.scipy(mt.MATRIX_D), m.scipy(mt.MATRIX_M), D, M,
+                   lambda x: orc.evaluate_element_based(x, n, o, pairs=(s, mm))[:2], itf)
     st = m.stats()
     assert st["n_nonempty"] == int(fl.sum()) and st["n_cells"] == 0
 
@@ -129,6 +130,7 @@ def test_element_based_batched(mt, orc):
     big = inputs.Interface("cat", xs, np.concatenate(cs).astype(np.int32), inputs.QUAD4, xm,
                            np.concatenate(cm).astype(np.int32), inputs.QUAD4, lm=0, delta=1e-9)
     s, mm = m.pairs()
-    D, M, _, _ = orc.evaluate_element_based(big, 5, orc.make_opts(lm=0, delta=1e-9), pairs=(s, mm))
-    csr_parity(m.scipy(mt.MATRIX_M), M)
-    csr_parity(m.scipy(mt.MATRIX_D), D)
+    o = orc.make_opts(lm=0, delta=1e-9)
+    D, M, _, _ = orc.evaluate_element_based(big, 5, o, pairs=(s, mm))
+    forward_parity(m.scipy(mt.MATRIX_D), m.scipy(mt.MATRIX_M), D, M,
+                   lambda x: orc.evaluate_element_based(x, 5, o, pairs=(s, mm))[:2], big)

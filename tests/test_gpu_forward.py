@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2202_03933_gb300 import inputs
-from gpu_util import blocks_parity, csr_parity
+from gpu_util import blocks_parity, forward_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +48,17 @@ def small_cases():
     ]
 
 
+def _dm(res):
+    return res.D, res.M
+
+
+def check_dm(mt, m, orc, itf, o, ref):
+    """D and M of context m against the oracle result ref (computed with
+    options o on ref's pair list)."""
+    return forward_parity(m.scipy(mt.MATRIX_D), m.scipy(mt.MATRIX_M), ref.D, ref.M,
+                          lambda x: _dm(orc.evaluate(x, o, pairs=(ref.s, ref.m))), itf)
+
+
 def run_gpu(mt, itf, d_domain, graph=False):
     m = mt.Mortar(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
     m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
@@ -71,8 +82,7 @@ def test_forward_parity_small(mt, orc, name, itf, d_domain):
     blocks_parity(Mb, ref.Mb)
     if d_domain == 1:
         blocks_parity(Db, ref.Db)
-    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
-    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    check_dm(mt, m, orc, itf, o, ref)
     st = m.stats()
     assert st["n_nonempty"] == ref.stats["nonempty"]
     assert st["n_gauss_points"] == ref.stats["gauss_points"]
@@ -98,9 +108,8 @@ def test_coordinate_update_reuses_context(mt, orc):
     itf2 = inputs.planar_noisy(12, 10, 0, 52, "upd2")
     m.set_coordinates(itf2.xs, itf2.xm)
     m.evaluate()
-    ref = orc.evaluate(itf2)
-    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
-    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
+    o = orc.make_opts(lm=itf2.lm, delta=itf2.delta)
+    check_dm(mt, m, orc, itf2, o, orc.evaluate(itf2, o))
 
 
 # ---------------------------------------------------------------- edge cases
@@ -131,8 +140,8 @@ def test_single_element_each(mt, orc):
     xm = inputs.grid_nodes(1, 1, 0.3, -0.2, 1.3, 0.8)
     itf = inputs.Interface("one", xs, cs, 4, xm, cs.copy(), 4)
     m = run_gpu(mt, itf, 1)
-    ref = orc.evaluate(itf, orc.make_opts(d_domain=1))
-    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    o = orc.make_opts(d_domain=1)
+    check_dm(mt, m, orc, itf, o, orc.evaluate(itf, o))
     assert abs(m.scipy(mt.MATRIX_M).sum() - 0.7 * 0.8) < 1e-15
 
 
@@ -140,10 +149,11 @@ def test_touching_only_pairs_are_empty(mt, orc):
     """Neighbouring elements that share only an edge: candidate pair, empty clip."""
     itf = inputs.matching(3, 0)[0]
     m = run_gpu(mt, itf, 0)
-    ref = orc.evaluate(itf)
+    o = orc.make_opts(lm=itf.lm, delta=itf.delta)
+    ref = orc.evaluate(itf, o)
     _, _, ne = m.pair_blocks()
     assert np.array_equal(ne, ref.nonempty) and (~ne).sum() > 0
-    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    check_dm(mt, m, orc, itf, o, ref)
 
 
 def test_bad_connectivity_rejected(mt):
@@ -202,8 +212,7 @@ def test_full_size_parity(mt, orc, cfg):
     m = run_gpu(mt, itf, 0, graph=True)
     s, mm = m.pairs()
     assert np.array_equal(s, ref.s) and np.array_equal(mm, ref.m)
-    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
-    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+    check_dm(mt, m, orc, itf, o, ref)
     if itf.lm == 1:
         D = m.scipy(mt.MATRIX_D)
         off = D - __import__("scipy.sparse", fromlist=["diags"]).diags(D.diagonal())
@@ -231,8 +240,7 @@ def test_full_size_planar_2000(mt, orc):
     Dr, Mr = _sampled_rows(orc, itf, s, mm, rows, o)
     D = m.scipy(mt.MATRIX_D)
     M = m.scipy(mt.MATRIX_M)
-    csr_parity(D[rows], Dr)
-    csr_parity(M[rows], Mr)
+    forward_parity(D[rows], M[rows], Dr, Mr, lambda x: _sampled_rows(orc, x, s, mm, rows, o), itf)
     # invariants at full size: unit square fully covered
     assert abs(D.sum() - 1.0) < 1e-12 and abs(M.sum() - 1.0) < 1e-12
     for c in (0, 1):
@@ -241,28 +249,8 @@ def test_full_size_planar_2000(mt, orc):
     assert abs(off).max() <= 1e-14 * D.diagonal().max()
 
 
-def test_batched_block_diagonal(mt, orc):
-    itfs = inputs.batched_512()[:40]
-    m = mt.Mortar()
-    m.set_batch(itfs)
-    m.run_graph()
-    m.run_graph()
-    D = m.scipy(mt.MATRIX_D)
-    M = m.scipy(mt.MATRIX_M)
-    sn, mn = m.offsets["slave_nodes"], m.offsets["master_nodes"]
-    for k, itf in enumerate(itfs):
-        ref = orc.evaluate(itf)
-        csr_parity(D[sn[k]:sn[k + 1], sn[k]:sn[k + 1]], ref.D)
-        csr_parity(M[sn[k]:sn[k + 1], mn[k]:mn[k + 1]], ref.M)
-    # nothing outside the diagonal blocks
-    rows = np.repeat(np.arange(M.shape[0]), np.diff(M.indptr))
-    blk_r = np.searchsorted(sn, rows, side="right") - 1
-    blk_c = np.searchsorted(mn, M.indices, side="right") - 1
-    assert np.array_equal(blk_r, blk_c)
-
-
-@pytest.mark.parametrize("variant,rounds", [(1, 0), (0, 1), (0, 2), (0, 4)])
-def test_launch_variants_agree(mt, orc, variant, rounds):
+@pytest.mark.parametrize("variant,rounds,block", [(1, 0, 64), (1, 0, 256), (0, 1, 64), (0, 2, 256), (0, 4, 128)])
+def test_launch_variants_agree(mt, orc, variant, rounds, block):
     """Every integration schedule gives the oracle's blocks (bilinear masters,
     tri3 masters, a non-affine warped slave, segment mode)."""
     cases = [(inputs.planar_noisy(41, 37, 1, 44, "v"), 1), (inputs.mixed_tri(33, 41, name="vt"), 0)]
@@ -275,6 +263,42 @@ def test_launch_variants_agree(mt, orc, variant, rounds):
         ref = orc.evaluate(itf, o)
         m = mt.Mortar(lm=itf.lm, d_domain=d_domain, delta=itf.delta)
         m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+        m.set_launch(variant=variant, block_size=block, rounds=rounds)
+        m.evaluate()
+        Mb, Db, ne = m.pair_blocks(with_D=d_domain == 1)
+        assert np.array_equal(ne, ref.nonempty)
+        blocks_parity(Mb, ref.Mb)
+        if d_domain == 1:
+            blocks_parity(Db, ref.Db)
+        check_dm(mt, m, orc, itf, o, ref)
+        assert m.stats()["n_newton_fail"] == 0
+
+
+def test_launch_shape_validation(mt):
+    """Shapes outside the documented set are refused (blocks above 256 threads,
+    blocks that are not whole warps, warp batches whose shared memory does not
+    fit one block)."""
+    m = mt.Mortar()
+    for args in ((0, 512, 0, 2), (1, 96 + 16, 0, 0), (0, 256, 0, 4), (0, 128, 0, 3)):
+        with pytest.raises(mt._native.MortarError, match="INVALID_ARG"):
+            m.set_launch(*args)
+    m.set_launch(0, 256, 0, 2)
+    m.set_launch(1, 256, 128, 0)
+
+
+@pytest.mark.parametrize("lm,d_domain", [(0, 0), (1, 1)])
+def test_distorted_master_quads(mt, orc, lm, d_domain):
+    """Strongly distorted but valid bilinear master quads (kite mesh, a corner
+    angle near 180 degrees): the FP32-seeded back-projection does not settle at
+    a fraction of the points there and continues with FP64 Newton.  Pair blocks
+    and D, M against the oracle in both schedules, and no Newton failure."""
+    itf = inputs.kite_master(20, 17, 0.45, lm=lm)
+    o = orc.make_opts(lm=lm, d_domain=d_domain, delta=itf.delta)
+    ref = orc.evaluate(itf, o)
+    assert ref.stats["newton_fail"] == 0
+    for variant, rounds in ((0, 2), (1, 0)):
+        m = mt.Mortar(lm=lm, d_domain=d_domain, delta=itf.delta)
+        m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
         m.set_launch(variant=variant, rounds=rounds)
         m.evaluate()
         Mb, Db, ne = m.pair_blocks(with_D=d_domain == 1)
@@ -282,7 +306,7 @@ def test_launch_variants_agree(mt, orc, variant, rounds):
         blocks_parity(Mb, ref.Mb)
         if d_domain == 1:
             blocks_parity(Db, ref.Db)
-        csr_parity(m.scipy(mt.MATRIX_M), ref.M)
+        check_dm(mt, m, orc, itf, o, ref)
         assert m.stats()["n_newton_fail"] == 0
 
 
@@ -293,11 +317,11 @@ def test_autotune_keeps_results(mt, orc):
     lam = np.random.default_rng(3).uniform(-1, 1, itf.xs.shape)
     pick = m.autotune(lam)
     assert pick["variant"] in (0, 1) and pick["rounds"] in (0, 1, 2, 4) and pick["ms"] > 0
+    assert pick["block"] in (64, 128, 256)
     m.run_graph(lam)
     m.run_graph(lam)
-    ref = orc.evaluate(itf)
-    csr_parity(m.scipy(mt.MATRIX_M), ref.M)
-    csr_parity(m.scipy(mt.MATRIX_D), ref.D)
+    o = orc.make_opts(lm=itf.lm, delta=itf.delta)
+    check_dm(mt, m, orc, itf, o, orc.evaluate(itf, o))
 
 
 def test_moving_interface_reevaluation(mt, orc):
@@ -321,8 +345,8 @@ def test_moving_interface_reevaluation(mt, orc):
         m.set_coordinates(None, torch.from_numpy(xm).cuda())
         m.run_graph(torch.from_numpy(lam).cuda())
         itf = inputs.Interface("mov", base.xs, base.conn_s, 4, xm, base.conn_m, 4, lm=1, delta=1e-9)
-        ref = orc.evaluate(itf)
+        o = orc.make_opts(lm=1, delta=1e-9)
+        ref = orc.evaluate(itf, o)
         s, mm = m.pairs()
         assert np.array_equal(s, ref.s) and np.array_equal(mm, ref.m), step
-        csr_parity(m.scipy(mt.MATRIX_M), ref.M)
-        csr_parity(m.scipy(mt.MATRIX_D), ref.D)
+        check_dm(mt, m, orc, itf, o, ref)
