@@ -53,8 +53,8 @@ UNIT = "pairs/s"
 # this build on planar_600x520 (same element types and density as the full
 # workload, so per-pair figures carry over); see profiles/.
 EXEC_PER_PAIR = {
-    "fused": {"flops": 12391.7, "dram_bytes": 2405.0},
-    "integrate": {"flops": None, "dram_bytes": None},
+    "fused": {"flops": 9397.0, "dram_bytes": 1130.0},
+    "integrate": {"flops": 3422.6, "dram_bytes": 236.0},
 }
 
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes

@@ -202,7 +202,7 @@ struct MapInverse {
   // updates.  Taken only when the FP32 iteration did not settle (strongly
   // distorted elements: a corner angle near 180 degrees makes the FP32
   // Jacobian too inaccurate for its 3e-7 step test).
-  __device__ __noinline__ bool newton64(double xu, double xv, double& xi, double& eta) const {
+  __device__ __forceinline__ bool newton64(double xu, double xv, double& xi, double& eta) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
     bool last = false;
     for (int it = 0; it < 20; ++it) {

@@ -277,18 +277,24 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_pairs(
 
 // ---------------------------------------------------------------- variant 0
 // Same functional, reorganised for the FP64 pipe:
-//  * the per-point reverse sweep only carries what depends on xi: with
-//    PX[c][b] = Lambda_c . X_b and PY[c][l] = Lambda_c . Y_l (per pair),
-//      t_c      = Lambda_c . q        = [seg] sum_b N_b PX[c][b] - sum_l Nm_l PY[c][l]
-//      f        = Lh . q              = sum_c N_c t_c
-//      dJ/dN_c  = W (t_c + [seg] sum_d N_d PX[d][c]),  dJ/dNm_l = -W sum_d N_d PY[d][l];
+//  * the per-point work is written in the monomial basis of the shape
+//    functions, N = T m with m = (1, xi, eta, xi eta) (quad4) or (1, xi, eta)
+//    (tri3).  With the monomial coefficients LM_i = sum_c T_s[c][i] Lambda_c,
+//    YM_j = sum_l T_m[l][j] Y_l and XM_j = sum_b T_s[b][j] X_b (per pair),
+//      f = Lh . q = [seg] m_s^T CX m_s - m_s^T CY m_m,
+//      CY[i][j] = LM_i . YM_j,  CX[i][j] = LM_i . XM_j,
+//    so a point needs v = CY m_m, u = CY^T m_s (and [seg] w = (CX + CX^T) m_s):
+//      f = [seg] m_s^T w / 2 - m_s^T v,
+//      W df/dxi_s = W (dm_s/dxi_s)^T (w - v),  W df/dxi_m = -W (dm_m/dxi_m)^T u;
 //  * the terms that hold the shape functions fixed come from the forward
-//    accumulators G = sum W N Nm^T and H = sum W N N^T at the end:
+//    accumulators G = sum W N Nm^T and H = sum W N N^T (summed in the nodal
+//    basis: non-negative terms keep small entries accurate) at the end:
 //      dJ/dY_l |direct = -sum_c G[c][l] Lambda_c,  dJ/dX_b |direct = sum_c H[c][b] Lambda_c,
 //      dJ/dLambda_c = sum_b H[c][b] X_b - sum_l G[c][l] Y_l,  J = sum_c Lambda_c . dJ/dLambda_c;
 //  * element maps are inverted as in the batched integration kernel (affine
 //    2x2 inverse, or FP32 Newton + one FP64 Newton step), and the
 //    implicit-function step uses the exact FP64 inverse Jacobian;
+//  * the clip is recorded as a compact vertex pool (ClipPool);
 //  * a warp sorts its batch of pairs by cell count before the sweep.
 template <int NS, int NM, bool SEG, bool DUAL, bool FWD>
 __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, const int32_t* __restrict__ pm,
@@ -297,30 +303,50 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
                                   const int32_t* __restrict__ conn_m, const double* __restrict__ lambda,
                                   double* __restrict__ gs_out, double* __restrict__ gm_out,
                                   double* __restrict__ ab_out, double* __restrict__ J_out,
-                                  const FwdOut& fo, AdjCounters& ctr) {
+                                  const FwdOut& fo, AdjCounters& ctr, double* __restrict__ csh, int cstride) {
+  constexpr int KS = NS, KM = NM;   // monomials per side (quad4: 4, tri3: 3)
+  // CY (and [seg] SX) live in this thread's slice of shared memory, entry k
+  // at csh[k * cstride] (interleaved across the block's threads: no bank
+  // conflicts); they are read at every quadrature point and would otherwise
+  // hold 32 (64) registers through the loop
+  auto CYs = [&](int i, int j) -> double& { return csh[(4 * i + j) * cstride]; };
+  auto SXs = [&](int i, int j) -> double& { return csh[(16 + 4 * i + j) * cstride]; };
   const int32_t s = ps[p], m = pm[p];
   const double* r = srec + (int64_t)SR_STRIDE * s;
-  double gX[4][3], gY[4][3];
-  for (int a = 0; a < 4; ++a)
-    for (int k = 0; k < 3; ++k) { gX[a][k] = 0.0; gY[a][k] = 0.0; }
-  V3 X[4], Y[4], lam[4], Lam[4], Lb[4];
-  for (int a = 0; a < 4; ++a) Lb[a] = v3(0, 0, 0);
-  double Jp = 0.0;
-  for (int a = 0; a < NS; ++a) {
-    const int64_t n = conn_s[(int64_t)NS * s + a];
-    X[a] = v3(xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]);
-    lam[a] = v3(lambda[3 * n], lambda[3 * n + 1], lambda[3 * n + 2]);
-  }
-  for (int l = 0; l < NM; ++l) {
-    const int64_t n = conn_m[(int64_t)NM * m + l];
-    Y[l] = v3(xm[3 * n], xm[3 * n + 1], xm[3 * n + 2]);
-  }
+  const int32_t* cs = conn_s + (int64_t)NS * s;
+  const int32_t* cm = conn_m + (int64_t)NM * m;
+  // Node coordinates and multipliers are read here for the set-up and read
+  // again (from L1/L2) after the quadrature loop: keeping them in registers
+  // across the loop would spill.
+  auto load_nodes = [&](V3* X, V3* Y, V3* lam) {
+    for (int a = 0; a < NS; ++a) {
+      const int64_t n = cs[a];
+      X[a] = v3(xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]);
+      lam[a] = v3(lambda[3 * n], lambda[3 * n + 1], lambda[3 * n + 2]);
+    }
+    for (int l = 0; l < NM; ++l) {
+      const int64_t n = cm[l];
+      Y[l] = v3(xm[3 * n], xm[3 * n + 1], xm[3 * n + 2]);
+    }
+  };
+  auto lm_weights = [&](const V3* lam, V3* Lam) {   // Lambda_c = sum_a A[a][c] lambda_a (dual), lambda_c
+    for (int c = 0; c < NS; ++c) {
+      if (DUAL) {
+        V3 acc = v3(0, 0, 0);
+        for (int a = 0; a < NS; ++a) acc = acc + r[SR_A + 4 * a + c] * lam[a];
+        Lam[c] = acc;
+      } else {
+        Lam[c] = lam[c];
+      }
+    }
+  };
   const V3 x0 = v3(r[SR_X0], r[SR_X0 + 1], r[SR_X0 + 2]);
   const V3 t1 = v3(r[SR_T1], r[SR_T1 + 1], r[SR_T1 + 2]);
   const V3 t2 = v3(r[SR_T2], r[SR_T2 + 1], r[SR_T2 + 2]);
   double mu[4], mv[4];
   for (int l = 0; l < NM; ++l) {
-    const double dx = Y[l].x - x0.x, dy = Y[l].y - x0.y, dz = Y[l].z - x0.z;
+    const int64_t n = cm[l];
+    const double dx = xm[3 * n] - x0.x, dy = xm[3 * n + 1] - x0.y, dz = xm[3 * n + 2] - x0.z;
     mu[l] = dx * t1.x + dy * t1.y + dz * t1.z;
     mv[l] = dx * t2.x + dy * t2.y + dz * t2.z;
   }
@@ -332,26 +358,38 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
   for (int l = 0; l < NM; ++l) ma2 += cross2(mu[l], mv[l], mu[(l + 1) % NM], mv[(l + 1) % NM]);
   const bool mrev = ma2 < 0.0;
   const bool srev = r[SR_REV] != 0.0;
-  // ---- forward clip with recorded stages and merge (same decisions as clip_polygon)
-  ClipRec<NS> cr;
-  const bool nonempty = cr.template run<NM>(r, mu, mv, mrev, ctr.clip_over);
-  const int nr = cr.nr;
+  // ---- forward clip recorded as a vertex pool, and merge (same decisions as clip_polygon)
+  ClipPool<NS, NM> cp;
+  const bool nonempty = cp.run(r, mu, mv, mrev, ctr.clip_over);
+  const int nr = cp.nr;
+  double Jp = 0.0;
+  V3 Lb[4];
   if (nonempty) {
-    for (int c = 0; c < NS; ++c) {
-      if (DUAL) {
-        V3 acc = v3(0, 0, 0);
-        for (int a = 0; a < NS; ++a) acc = acc + r[SR_A + 4 * a + c] * lam[a];
-        Lam[c] = acc;
-      } else {
-        Lam[c] = lam[c];
+    // monomial coefficients and the pair's bilinear forms
+    {
+      V3 X[4], Y[4], lam[4], Lam[4], LM[4], YM[4];
+      load_nodes(X, Y, lam);
+      lm_weights(lam, Lam);
+      nodal_to_mono<NS>(Lam, LM);
+      nodal_to_mono<NM>(Y, YM);
+#pragma unroll
+      for (int i = 0; i < KS; ++i)
+#pragma unroll
+        for (int j = 0; j < KM; ++j) CYs(i, j) = dot(LM[i], YM[j]);
+      if (SEG) {
+        V3 XM[4];
+        nodal_to_mono<NS>(X, XM);
+        double CX[4][4];
+#pragma unroll
+        for (int i = 0; i < KS; ++i)
+#pragma unroll
+          for (int j = 0; j < KS; ++j) CX[i][j] = dot(LM[i], XM[j]);
+#pragma unroll
+        for (int i = 0; i < KS; ++i)
+#pragma unroll
+          for (int j = 0; j < KS; ++j) SXs(i, j) = CX[i][j] + CX[j][i];
       }
     }
-    double PX[4][4], PY[4][4];
-    for (int c = 0; c < 4; ++c)
-      for (int b = 0; b < 4; ++b) {
-        PX[c][b] = (SEG && c < NS && b < NS) ? dot(Lam[c], X[b]) : 0.0;
-        PY[c][b] = (c < NS && b < NM) ? dot(Lam[c], Y[b]) : 0.0;
-      }
     MapInverse mi;
     mi.setup(mmap, NM == 3 || map_is_affine(mmap));
     MapInverse si;
@@ -362,22 +400,21 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
     } else {
       si.setup(smap, false);
     }
-    double Ru[kPolyA], Rv[kPolyA], Rbu[kPolyA], Rbv[kPolyA];
-    for (int k = 0; k < nr; ++k) {
-      Ru[k] = cr.pu(k);
-      Rv[k] = cr.pv(k);
-      Rbu[k] = 0.0;
-      Rbv[k] = 0.0;
-    }
+    // polygon vertex adjoints, kept at the vertices' pool slots
+    double Bu[ClipPool<NS, NM>::kSlots], Bv[ClipPool<NS, NM>::kSlots];
+    for (int k = 0; k < cp.nv; ++k) { Bu[k] = 0.0; Bv[k] = 0.0; }
     double cu = 0.0, cv = 0.0, cbu = 0.0, cbv = 0.0;
     int ncell = 1;
     if (nr > 3) {
       double su = 0.0, sv = 0.0;
-      for (int k = 0; k < nr; ++k) { su += Ru[k]; sv += Rv[k]; }
+      for (int k = 0; k < nr; ++k) { su += cp.u(k); sv += cp.v(k); }
       cu = su / (double)nr;
       cv = sv / (double)nr;
       ncell = nr;
     }
+    // forward accumulators G = sum W N_s N_m^T, H = sum W N_s N_s^T, summed
+    // from the nodal shape functions: all terms are non-negative, so small
+    // entries keep their relative accuracy (monomial moments would cancel)
     double G[4][4], H[4][4];
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) { G[a][b] = 0.0; H[a][b] = 0.0; }
@@ -386,11 +423,12 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
       int ib, iw;
       double au, av;
       if (nr == 3) {
-        au = Ru[0]; av = Rv[0]; ib = 1; iw = 2;
+        au = cp.u(0); av = cp.v(0); ib = 1; iw = 2;
       } else {
         au = cu; av = cv; ib = cI; iw = cI + 1 == nr ? 0 : cI + 1;
       }
-      const double e1u = Ru[ib] - au, e1v = Rv[ib] - av, e2u = Ru[iw] - au, e2v = Rv[iw] - av;
+      const int sb = cp.id(ib), sw = cp.id(iw);
+      const double e1u = cp.pu[sb] - au, e1v = cp.pv[sb] - av, e2u = cp.pu[sw] - au, e2v = cp.pv[sw] - av;
       const double cr = cross2(e1u, e1v, e2u, e2v);
       const double area = 0.5 * fabs(cr);
       double area_b = 0.0, e1bu = 0.0, e1bv = 0.0, e2bu = 0.0, e2bv = 0.0, abu = 0.0, abv = 0.0;
@@ -405,60 +443,88 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
         double xs1, xs2, xm1, xm2;
         if (!si.solve(xu, xv, xs1, xs2)) ctr.newton_fail++;
         if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
-        ShapeAD<NS> SA;
-        ShapeAD<NM> MA;
-        SA.eval(xs1, xs2);
-        MA.eval(xm1, xm2);
-        const double* Ns = SA.N;
-        const double* Nm = MA.N;
-        double t[4], f = 0.0;
+        const double xs12 = xs1 * xs2, xm12 = xm1 * xm2;
+        // v = CY m_m, u = CY^T m_s
+        double v[4], u[4];
 #pragma unroll
-        for (int c = 0; c < NS; ++c) {
-          double v = 0.0;
-          if (SEG)
+        for (int i = 0; i < KS; ++i) {
+          double t = fma(CYs(i, 2), xm2, fma(CYs(i, 1), xm1, CYs(i, 0)));
+          if (KM == 4) t = fma(CYs(i, 3), xm12, t);
+          v[i] = t;
+        }
 #pragma unroll
-            for (int b = 0; b < NS; ++b) v = fma(Ns[b], PX[c][b], v);
+        for (int j = 0; j < KM; ++j) {
+          double t = fma(CYs(2, j), xs2, fma(CYs(1, j), xs1, CYs(0, j)));
+          if (KS == 4) t = fma(CYs(3, j), xs12, t);
+          u[j] = t;
+        }
+        // g = [seg] (CX + CX^T) m_s - v;  f = [seg] m_s^T w / 2 - m_s^T v
+        double g[4], f;
+        {
+          double fv = fma(v[2], xs2, fma(v[1], xs1, v[0]));
+          if (KS == 4) fv = fma(v[3], xs12, fv);
+          if (SEG) {
+            double fw = 0.0;
 #pragma unroll
-          for (int l = 0; l < NM; ++l) v = fma(-Nm[l], PY[c][l], v);
-          t[c] = v;
-          f = fma(Ns[c], v, f);
+            for (int i = 0; i < KS; ++i) {
+              double t = fma(SXs(i, 2), xs2, fma(SXs(i, 1), xs1, SXs(i, 0)));
+              if (KS == 4) t = fma(SXs(i, 3), xs12, t);
+              g[i] = t - v[i];
+              fw = i == 0 ? t : fma(i == 1 ? xs1 : (i == 2 ? xs2 : xs12), t, fw);
+            }
+            f = fma(0.5, fw, -fv);
+          } else {
+#pragma unroll
+            for (int i = 0; i < KS; ++i) g[i] = -v[i];
+            f = -fv;
+          }
         }
         area_b = fma(w, f, area_b);
-        double Nsb[4], Nmb[4];
-#pragma unroll
-        for (int c = 0; c < NS; ++c) {
-          double v = t[c];
-          if (SEG)
-#pragma unroll
-            for (int d = 0; d < NS; ++d) v = fma(Ns[d], PX[d][c], v);
-          Nsb[c] = W * v;
-        }
-#pragma unroll
-        for (int l = 0; l < NM; ++l) {
-          double v = 0.0;
-#pragma unroll
-          for (int d = 0; d < NS; ++d) v = fma(Ns[d], PY[d][l], v);
-          Nmb[l] = -W * v;
-        }
-        // forward accumulators for the direct terms
-#pragma unroll
-        for (int c = 0; c < NS; ++c) {
-          const double wn = W * Ns[c];
-#pragma unroll
-          for (int l = 0; l < NM; ++l) G[c][l] = fma(wn, Nm[l], G[c][l]);
-          if (SEG)
-#pragma unroll
-            for (int b = 0; b < NS; ++b) H[c][b] = fma(wn, Ns[b], H[c][b]);
-        }
+        // W df/dxi on both sides
         double xsb0, xsb1, xmb0, xmb1;
-        SA.pull(Nsb, xsb0, xsb1);
-        MA.pull(Nmb, xmb0, xmb1);
+        if (KS == 4) {
+          xsb0 = W * fma(xs2, g[3], g[1]);
+          xsb1 = W * fma(xs1, g[3], g[2]);
+        } else {
+          xsb0 = W * g[1];
+          xsb1 = W * g[2];
+        }
+        if (KM == 4) {
+          xmb0 = -W * fma(xm2, u[3], u[1]);
+          xmb1 = -W * fma(xm1, u[3], u[2]);
+        } else {
+          xmb0 = -W * u[1];
+          xmb1 = -W * u[2];
+        }
+        // forward accumulators (nodal shape functions, W folded into N_s)
+        {
+          double WNs[4], Nm[4];
+          if constexpr (NS == 4) {
+            const double w4 = 0.25 * W;
+            const double qa = w4 * (1.0 - xs1), qb = w4 * (1.0 + xs1), c = 1.0 - xs2, d = 1.0 + xs2;
+            WNs[0] = qa * c; WNs[1] = qb * c; WNs[2] = qb * d; WNs[3] = qa * d;
+          } else {
+            WNs[0] = W * (1.0 - xs1 - xs2); WNs[1] = W * xs1; WNs[2] = W * xs2; WNs[3] = 0.0;
+          }
+          shape_fn<NM>(xm1, xm2, Nm);
+#pragma unroll
+          for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int l = 0; l < NM; ++l) G[a][l] = fma(WNs[a], Nm[l], G[a][l]);
+          if (SEG) {
+            double Ns[4];
+            shape_fn<NS>(xs1, xs2, Ns);
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+#pragma unroll
+              for (int b = 0; b < NS; ++b) H[a][b] = fma(WNs[a], Ns[b], H[a][b]);
+          }
+        }
         double a00, a01, a10, a11;
         si.jinv(xs1, xs2, a00, a01, a10, a11);
         const double msu = a00 * xsb0 + a10 * xsb1, msv = a01 * xsb0 + a11 * xsb1;   // J^-T xib
         mi.jinv(xm1, xm2, a00, a01, a10, a11);
         const double mmu = a00 * xmb0 + a10 * xmb1, mmv = a01 * xmb0 + a11 * xmb1;
-        const double xs12 = xs1 * xs2, xm12 = xm1 * xm2;
         smb[0] -= msu; smb[1] -= msv;
         smb[2] = fma(-xs1, msu, smb[2]); smb[3] = fma(-xs1, msv, smb[3]);
         smb[4] = fma(-xs2, msu, smb[4]); smb[5] = fma(-xs2, msv, smb[5]);
@@ -475,36 +541,16 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
       const double crb = 0.5 * (cr < 0.0 ? -area_b : area_b);
       e1bu += crb * e2v; e1bv -= crb * e2u;
       e2bu -= crb * e1v; e2bv += crb * e1u;
-      Rbu[ib] += e1bu; Rbv[ib] += e1bv;
-      Rbu[iw] += e2bu; Rbv[iw] += e2bv;
+      Bu[sb] += e1bu; Bv[sb] += e1bv;
+      Bu[sw] += e2bu; Bv[sw] += e2bv;
       abu -= e1bu + e2bu;
       abv -= e1bv + e2bv;
-      if (nr == 3) { Rbu[0] += abu; Rbv[0] += abv; } else { cbu += abu; cbv += abv; }
+      if (nr == 3) { const int s0 = cp.id(0); Bu[s0] += abu; Bv[s0] += abv; } else { cbu += abu; cbv += abv; }
     }
     if (nr > 3) {
       const double inv = 1.0 / (double)nr;
-      for (int k = 0; k < nr; ++k) { Rbu[k] += cbu * inv; Rbv[k] += cbv * inv; }
+      for (int k = 0; k < nr; ++k) { const int sk = cp.id(k); Bu[sk] += cbu * inv; Bv[sk] += cbv * inv; }
     }
-    // ---- direct terms and J from the forward accumulators
-    for (int c = 0; c < NS; ++c) {
-      V3 acc = v3(0, 0, 0);
-      if (SEG)
-        for (int b = 0; b < NS; ++b) acc = acc + H[c][b] * X[b];
-      for (int l = 0; l < NM; ++l) acc = acc - G[c][l] * Y[l];
-      Lb[c] = acc;
-      Jp += dot(Lam[c], acc);
-    }
-    for (int l = 0; l < NM; ++l) {
-      V3 acc = v3(0, 0, 0);
-      for (int c = 0; c < NS; ++c) acc = acc + G[c][l] * Lam[c];
-      gY[l][0] -= acc.x; gY[l][1] -= acc.y; gY[l][2] -= acc.z;
-    }
-    if (SEG)
-      for (int b = 0; b < NS; ++b) {
-        V3 acc = v3(0, 0, 0);
-        for (int c = 0; c < NS; ++c) acc = acc + H[c][b] * Lam[c];
-        gX[b][0] += acc.x; gX[b][1] += acc.y; gX[b][2] += acc.z;
-      }
     if (FWD) {   // fused forward: M = A G, D = A H of this pair
       ctr.nonempty++;
       double* mo = fo.Mblk + 16 * p;
@@ -535,29 +581,67 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
       }
       fo.flag[p] = 1;
     }
-    // ---- reverse merge and clipping stages, projection, auxiliary plane
+    // ---- reverse merge and clipping (vertex pool) and the element maps
     double sbu[4] = {0, 0, 0, 0}, sbv[4] = {0, 0, 0, 0}, mbu[4] = {0, 0, 0, 0}, mbv[4] = {0, 0, 0, 0};
-    cr.template reverse<NM>(r, Rbu, Rbv, srev, mrev, sbu, sbv, mbu, mbv);
+    cp.reverse(r, Bu, Bv, srev, mrev, sbu, sbv, mbu, mbv);
     map_coeff_reverse<NS>(smb, sbu, sbv);
     map_coeff_reverse<NM>(mmb, mbu, mbv);
+    // ---- direct terms and J from the forward accumulators, then the
+    //      reverse of the projection onto the auxiliary plane
+    V3 X[4], Y[4], lam[4], Lam[4];
+    load_nodes(X, Y, lam);
+    lm_weights(lam, Lam);
+    double gX[4][3], gY[4][3];
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) { gX[a][k] = 0.0; gY[a][k] = 0.0; }
+    for (int c = 0; c < NS; ++c) {
+      V3 acc = v3(0, 0, 0);
+      if (SEG)
+        for (int b = 0; b < NS; ++b) acc = acc + H[c][b] * X[b];
+      for (int l = 0; l < NM; ++l) acc = acc - G[c][l] * Y[l];
+      Lb[c] = acc;
+      Jp += dot(Lam[c], acc);
+    }
+    for (int l = 0; l < NM; ++l) {
+      V3 acc = v3(0, 0, 0);
+      for (int c = 0; c < NS; ++c) acc = acc + G[c][l] * Lam[c];
+      gY[l][0] -= acc.x; gY[l][1] -= acc.y; gY[l][2] -= acc.z;
+    }
+    if (SEG)
+      for (int b = 0; b < NS; ++b) {
+        V3 acc = v3(0, 0, 0);
+        for (int c = 0; c < NS; ++c) acc = acc + H[c][b] * Lam[c];
+        gX[b][0] += acc.x; gX[b][1] += acc.y; gX[b][2] += acc.z;
+      }
     const V3 n0 = v3(r[SR_N0], r[SR_N0 + 1], r[SR_N0 + 2]);
     plane_reverse<NS, NM>(X, Y, x0, t1, t2, n0, sbu, sbv, mbu, mbv, gX, gY);
-  }
-  double* go = gs_out + 12 * p;
-  double* gmo = gm_out + 12 * p;
-  for (int a = 0; a < 4; ++a)
-    for (int k = 0; k < 3; ++k) {
-      go[3 * a + k] = gX[a][k];
-      gmo[3 * a + k] = gY[a][k];
-    }
-  if (DUAL) {
-    double* ab = ab_out + 16 * p;
+    double* go = gs_out + 12 * p;
+    double* gmo = gm_out + 12 * p;
     for (int a = 0; a < 4; ++a)
-      for (int c = 0; c < 4; ++c)
-        ab[4 * a + c] = (nonempty && a < NS && c < NS) ? dot(lam[a], Lb[c]) : 0.0;
+      for (int k = 0; k < 3; ++k) {
+        go[3 * a + k] = gX[a][k];
+        gmo[3 * a + k] = gY[a][k];
+      }
+    if (DUAL) {
+      double* ab = ab_out + 16 * p;
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) ab[4 * a + c] = (a < NS && c < NS) ? dot(lam[a], Lb[c]) : 0.0;
+    }
+  } else {
+    double2* g1 = reinterpret_cast<double2*>(gs_out + 12 * p);
+    double2* g2 = reinterpret_cast<double2*>(gm_out + 12 * p);
+    for (int k = 0; k < 6; ++k) { g1[k] = make_double2(0.0, 0.0); g2[k] = make_double2(0.0, 0.0); }
+    if (DUAL) {
+      double2* a2 = reinterpret_cast<double2*>(ab_out + 16 * p);
+      for (int k = 0; k < 8; ++k) a2[k] = make_double2(0.0, 0.0);
+    }
   }
   J_out[p] = Jp;
 }
+
+// shared-memory coefficients per thread of the batched adjoint kernel: CY and [seg] SX
+template <bool SEG>
+constexpr int kAdjCoef = SEG ? 32 : 16;
 
 template <int NS, int NM, bool SEG, bool DUAL, bool FWD, int R>
 __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
@@ -569,6 +653,7 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
   cta_mark(cta_t, 0);
   constexpr int B = 32 * R;
   __shared__ uint8_t perm_s[kMaxPairBlock / 32][B];
+  extern __shared__ double adj_coef[];   // kAdjCoef doubles per thread, interleaved
   uint8_t* perm = perm_s[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -643,7 +728,8 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
       const int i = i0 + lane;
       if (i < n_live)
         adjoint_pair_fast<NS, NM, SEG, DUAL, FWD>(base + perm[i], ps, pm, srec, xs, xm, conn_s, conn_m, lambda,
-                                                  gs_out, gm_out, ab_out, J_out, fo, ctr);
+                                                  gs_out, gm_out, ab_out, J_out, fo, ctr, adj_coef + threadIdx.x,
+                                                  (int)blockDim.x);
     }
     __syncwarp();
   }
@@ -972,13 +1058,15 @@ void launch_batched_f(mortar_ctx* c, int rounds) {
   const FwdOut fo{c->Mblk.as<double>(), c->Dblk.as<double>(), c->flag.as<uint8_t>()};
   unsigned long long* cta_t = (FWD && c->timing && c->cta_t.p) ? c->cta_t.as<unsigned long long>() : nullptr;
   const int block = c->block_size > 0 ? c->block_size : 128;
+  const size_t shm = (size_t)block * kAdjCoef<SEG> * sizeof(double);
   auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);   // > 48 KB at 256 threads
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, shm);
     if (per_sm < 1) per_sm = 1;
     const unsigned grid = (unsigned)(c->n_sm * per_sm);
     if (cta_t) c->pair_grid = (int)grid;
-    kern<<<grid, block, 0, c->stream>>>(
+    kern<<<grid, block, shm, c->stream>>>(
         c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
         c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->lambda.as<double>(), c->pair_cap,
         c->gs_pair.as<double>(), c->gm_pair.as<double>(), c->abar_pair.as<double>(), c->J_pair.as<double>(), fo,

@@ -228,6 +228,192 @@ struct ClipRec {
   }
 };
 
+// Compact clip record: the same Sutherland-Hodgman clip and merge as
+// ClipRec (identical arithmetic and decisions), recorded as a pool of
+// vertices instead of whole stages.  Pool slots [0, NM) are the master
+// polygon's vertices (counter-clockwise), every later slot is an edge
+// intersection x = p + t (q - p) made at stage i from pool slots p and q; a
+// copied vertex keeps its slot.  The working polygon of a stage is a list of
+// 4-bit slot ids packed into 64 bits.  Reverse: slots are visited from the
+// last intersection down, so that each slot's adjoint is complete before it
+// is passed on to its two parents and to the clip edge.
+template <int NS, int NM>
+struct ClipPool {
+  static constexpr int kSlots = 12;   // master vertices + intersections (convex quads: <= 4 + 8)
+  double pu[kSlots], pv[kSlots], tt[kSlots];
+  uint16_t meta[kSlots];              // intersection: p | q << 4 | stage << 8
+  int nv = 0, nr = 0;
+  uint64_t poly = 0;                  // merged polygon: slot ids, 4 bits each
+
+  __device__ __forceinline__ int id(int k) const { return (int)((poly >> (4 * k)) & 15); }
+  __device__ __forceinline__ double u(int k) const { return pu[id(k)]; }
+  __device__ __forceinline__ double v(int k) const { return pv[id(k)]; }
+
+  __device__ __forceinline__ bool run(const double* __restrict__ r, const double* mu, const double* mv, bool mrev,
+                                      unsigned long long& clip_over) {
+    const double eps_in = r[SR_EPSIN];
+    const long long eps_bits = __double_as_longlong(eps_in >= 0.0 ? eps_in : 0.0);
+    uint64_t cur = 0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      const int l = mrev ? NM - 1 - k : k;
+      pu[k] = mu[l];
+      pv[k] = mv[l];
+      cur |= (uint64_t)k << (4 * k);
+    }
+    nv = NM;
+    int n = NM;
+    bool over = false;
+    for (int i = 0; i < NS && n > 0; ++i) {
+      const int i1 = i + 1 == NS ? 0 : i + 1;
+      const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
+      const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
+      const int id0 = (int)(cur & 15);
+      const double d0 = cross2(eu, ev, pu[id0] - au, pv[id0] - av);
+      const int s0 = band_side(d0, eps_bits);
+      double dp = d0;
+      int sp = s0, idp = id0;
+      uint64_t nxt = 0;
+      int o = 0;
+      for (int k = 0; k < n; ++k) {
+        const int k1 = k + 1 == n ? 0 : k + 1;
+        const int idq = (int)((cur >> (4 * k1)) & 15);
+        double dq;
+        int sq;
+        if (k1 == 0) {
+          dq = d0;
+          sq = s0;
+        } else {
+          dq = cross2(eu, ev, pu[idq] - au, pv[idq] - av);
+          sq = band_side(dq, eps_bits);
+        }
+        if ((sp == 1 && sq == -1) || (sp == -1 && sq == 1)) {   // dp, dq beyond the band on both sides
+          const double t = dp / (dp - dq);
+          if (nv < kSlots && o < 16) {
+            pu[nv] = pu[idp] + t * (pu[idq] - pu[idp]);
+            pv[nv] = pv[idp] + t * (pv[idq] - pv[idp]);
+            tt[nv] = t;
+            meta[nv] = (uint16_t)(idp | (idq << 4) | (i << 8));
+            nxt |= (uint64_t)nv << (4 * o);
+            ++nv;
+            ++o;
+          } else {
+            over = true;
+          }
+        }
+        if (sq == 0 || sq == 1) {   // dq >= -eps_in
+          if (o < 16) {
+            nxt |= (uint64_t)idq << (4 * o);
+            ++o;
+          } else {
+            over = true;
+          }
+        }
+        dp = dq;
+        sp = sq;
+        idp = idq;
+      }
+      cur = nxt;
+      n = o;
+    }
+    if (over) {   // cannot happen for convex elements; reported, pair dropped
+      clip_over++;
+      nr = 0;
+      return false;
+    }
+    // merge consecutive (cyclic) vertices closer than eps_merge: a selection
+    const double em2 = r[SR_EPSM2];
+    nr = 0;
+    poly = 0;
+    int last_id = -1, first_id = -1;
+    for (int k = 0; k < n; ++k) {
+      const int q = (int)((cur >> (4 * k)) & 15);
+      if (nr > 0) {
+        const double du = pu[q] - pu[last_id], dv = pv[q] - pv[last_id];
+        if (du * du + dv * dv < em2) continue;
+      } else {
+        first_id = q;
+      }
+      poly |= (uint64_t)q << (4 * nr);
+      last_id = q;
+      ++nr;
+    }
+    while (nr > 1) {
+      const int q = id(nr - 1);
+      const double du = pu[q] - pu[first_id], dv = pv[q] - pv[first_id];
+      if (du * du + dv * dv < em2) {
+        --nr;
+        poly &= ~((uint64_t)15 << (4 * nr));
+      } else {
+        break;
+      }
+    }
+    double pa2 = 0.0;
+    for (int k = 0; k < nr; ++k) {
+      const int a = id(k), b = id(k + 1 == nr ? 0 : k + 1);
+      pa2 += cross2(pu[a], pv[a], pu[b], pv[b]);
+    }
+    return eps_in >= 0.0 && nr >= 3 && !(0.5 * fabs(pa2) < r[SR_EPSA]);
+  }
+
+  // Reverse of merge and clip.  Bu, Bv (kSlots, caller-owned) hold on entry
+  // the adjoints of the merged polygon's vertices ADDED at their slots (all
+  // other slots zero); the in-plane adjoints of the slave window vertices
+  // (element node order) and of the master nodes are ADDED to sbu, sbv, mbu, mbv.
+  __device__ __forceinline__ void reverse(const double* __restrict__ r, double* Bu, double* Bv, bool srev,
+                                          bool mrev, double* sbu, double* sbv, double* mbu, double* mbv) const {
+    double Wbu[NS], Wbv[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) { Wbu[k] = 0.0; Wbv[k] = 0.0; }
+    for (int w = nv - 1; w >= NM; --w) {
+      const double gbu = Bu[w], gbv = Bv[w];
+      const int p = meta[w] & 15, q = (meta[w] >> 4) & 15, i = meta[w] >> 8;
+      const int i1 = i + 1 == NS ? 0 : i + 1;
+      const double au = r[SR_PS + 2 * i], av = r[SR_PS + 2 * i + 1];
+      const double eu = r[SR_PS + 2 * i1] - au, ev = r[SR_PS + 2 * i1 + 1] - av;
+      // intersection x = p + t (q - p), t = d_p / (d_p - d_q),
+      // d = eu (y_v - a_v) - ev (y_u - a_u) for y = p, q
+      const double tk = tt[w];
+      const double pu_ = pu[p], pv_ = pv[p], qu = pu[q], qv = pv[q];
+      const double tb = gbu * (qu - pu_) + gbv * (qv - pv_);
+      const double dp = cross2(eu, ev, pu_ - au, pv_ - av);
+      const double dq = cross2(eu, ev, qu - au, qv - av);
+      const double den = dp - dq;
+      const double i2 = 1.0 / (den * den);
+      const double dpb = -tb * dq * i2, dqb = tb * dp * i2;
+      Bu[p] += (1.0 - tk) * gbu - ev * dpb;
+      Bv[p] += (1.0 - tk) * gbv + eu * dpb;
+      Bu[q] += tk * gbu - ev * dqb;
+      Bv[q] += tk * gbv + eu * dqb;
+      const double abu2 = ev * (dpb + dqb), abv2 = -eu * (dpb + dqb);
+      const double ebu = (pv_ - av) * dpb + (qv - av) * dqb;
+      const double ebv = -(pu_ - au) * dpb - (qu - au) * dqb;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {   // window vertices i and i + 1 (registers, no indexed array)
+        const int s1 = s + 1 == NS ? 0 : s + 1;
+        if (s == i) {
+          Wbu[s] += abu2 - ebu;
+          Wbv[s] += abv2 - ebv;
+          Wbu[s1] += ebu;
+          Wbv[s1] += ebv;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int a = srev ? NS - 1 - k : k;
+      sbu[a] += Wbu[k];
+      sbv[a] += Wbv[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+      const int l = mrev ? NM - 1 - k : k;
+      mbu[l] += Bu[k];
+      mbv[l] += Bv[k];
+    }
+  }
+};
+
 // Reverse of the projection u = (P - x0).t1, v = (P - x0).t2 of every node of
 // the pair and of the auxiliary plane (x0 = element centre, n0 = unit normal
 // there, t1 = normalised projected first edge, t2 = n0 x t1) as functions of
@@ -296,6 +482,29 @@ __device__ __forceinline__ void plane_reverse(const V3* X, const V3* Y, V3 x0, V
   }
   for (int a = 0; a < NS; ++a) {
     gX[a][0] += Xb[a].x; gX[a][1] += Xb[a].y; gX[a][2] += Xb[a].z;
+  }
+}
+
+// Monomial form of the element shape functions, N(xi) = T m(xi): quad4
+// m = (1, xi, eta, xi eta) and row a of T is (1, xi_a, eta_a, xi_a eta_a) / 4
+// with the corners (xi_a, eta_a) = (-1,-1), (1,-1), (1,1), (-1,1); tri3
+// m = (1, xi, eta) and N = (1 - xi - eta, xi, eta).  A bilinear form
+// N_s^T P N_m of nodal quantities equals m_s^T (T_s^T P T_m) m_m, which a
+// quadrature point evaluates without forming N.
+
+// out_i = sum_a T[a][i] in_a: monomial coefficients of the nodal field `in`.
+template <int NEN>
+__device__ __forceinline__ void nodal_to_mono(const V3* in, V3* out) {
+  if constexpr (NEN == 4) {
+    const V3 s02 = in[0] + in[2], s13 = in[1] + in[3], d20 = in[2] - in[0], d13 = in[1] - in[3];
+    out[0] = 0.25 * (s02 + s13);
+    out[1] = 0.25 * (d20 + d13);
+    out[2] = 0.25 * (d20 - d13);
+    out[3] = 0.25 * (s02 - s13);
+  } else {
+    out[0] = in[0];
+    out[1] = in[1] - in[0];
+    out[2] = in[2] - in[0];
   }
 }
 
