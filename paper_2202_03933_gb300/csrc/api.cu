@@ -11,9 +11,23 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "context.h"
 
 using namespace mortar;
+
+namespace {
+// NVTX range for tracing tools (Nsight Systems, ncu --nvtx): a named host
+// range around every public call and each phase of an enqueued run.  Without
+// an attached tool the push / pop are no-ops.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 namespace mortar {
 
@@ -143,24 +157,32 @@ void enqueue_run(mortar_ctx* c, const Phases& ph) {
   cudaMemsetAsync(c->dstat.p, 0, sizeof(DevStatus), st);
   c->pair_grid = 0;
   if (c->timing) record_event(c->ev[0], st);
-  launch_slave_precompute(c, rp);
-  launch_master_boxes(c, rp);
-  launch_grid_params(c, rp);
-  launch_bin_masters(c);
-  launch_candidates(c);
+  {
+    NvtxRange nv("mortar:search");
+    launch_slave_precompute(c, rp);
+    launch_master_boxes(c, rp);
+    launch_grid_params(c, rp);
+    launch_bin_masters(c);
+    launch_candidates(c);
+  }
   if (c->timing) record_event(c->ev[1], st);
   // with the adjoint, the batched adjoint pair kernel also produces the
   // forward blocks (one pass over the pairs instead of two)
   const bool fused = ph.adjoint && ph.integrate && adjoint_fuses_forward(c);
-  if (fused) launch_adjoint_pairs(c, rp, true);
-  else if (ph.integrate) launch_integrate(c, rp);
+  {
+    NvtxRange nv(fused ? "mortar:pairs(forward+adjoint)" : "mortar:pairs(forward)");
+    if (fused) launch_adjoint_pairs(c, rp, true);
+    else if (ph.integrate) launch_integrate(c, rp);
+  }
   if (c->timing) record_event(c->ev[2], st);
   if (ph.assemble) {
+    NvtxRange nv("mortar:assemble");
     launch_assemble(c, rp);
     launch_finalize_status(c);
   }
   if (c->timing) record_event(c->ev[3], st);
   if (ph.adjoint) {
+    NvtxRange nv("mortar:adjoint");
     if (!fused) launch_adjoint_pairs(c, rp, false);
     if (c->timing) record_event(c->ev[5], st);
     launch_adjoint_rest(c, rp);
@@ -474,6 +496,7 @@ void mortar_destroy(mortar_ctx* c) {
 int mortar_set_interface(mortar_ctx* c, const double* xs, int64_t Ns, const int32_t* conn_s, int64_t Es,
                          int32_t type_s, const double* xm, int64_t Nm, const int32_t* conn_m, int64_t Em,
                          int32_t type_m, int32_t on_device) {
+  NvtxRange nv_call("mortar_set_interface");
   if (Ns < 0 || Es < 0 || Nm < 0 || Em < 0) return MORTAR_ERR_INVALID_ARG;
   const int64_t sn[2] = {0, Ns}, se[2] = {0, Es}, mn[2] = {0, Nm}, me[2] = {0, Em};
   return set_common(c, 1, sn, se, mn, me, xs, conn_s, type_s, xm, conn_m, type_m, on_device);
@@ -482,6 +505,7 @@ int mortar_set_interface(mortar_ctx* c, const double* xs, int64_t Ns, const int3
 int mortar_set_batch(mortar_ctx* c, int32_t n_if, const int64_t* sn, const int64_t* se, const int64_t* mn,
                      const int64_t* me, const double* xs, const int32_t* conn_s, int32_t type_s, const double* xm,
                      const int32_t* conn_m, int32_t type_m, int32_t on_device) {
+  NvtxRange nv_call("mortar_set_batch");
   if (!sn || !se || !mn || !me) return MORTAR_ERR_INVALID_ARG;
   return set_common(c, n_if, sn, se, mn, me, xs, conn_s, type_s, xm, conn_m, type_m, on_device);
 }
@@ -495,6 +519,7 @@ int mortar_set_coordinates(mortar_ctx* c, const double* xs, const double* xm, in
 }
 
 int mortar_search(mortar_ctx* c, int64_t* n_pairs) {
+  NvtxRange nv_call("mortar_search");
   if (!c) return MORTAR_ERR_INVALID_ARG;
   Phases ph;
   ph.integrate = ph.assemble = false;
@@ -514,6 +539,7 @@ int mortar_get_pairs(mortar_ctx* c, int32_t* s_ids, int32_t* m_ids, int64_t capa
 }
 
 int mortar_evaluate(mortar_ctx* c) {
+  NvtxRange nv_call("mortar_evaluate");
   if (!c) return MORTAR_ERR_INVALID_ARG;
   Phases ph;
   return run(c, ph);
@@ -530,6 +556,7 @@ int mortar_csr_size(mortar_ctx* c, int32_t which, int64_t* nrows, int64_t* ncols
 
 int mortar_csr_copy(mortar_ctx* c, int32_t which, int64_t* rowptr, int32_t* colidx, double* vals,
                     int64_t capacity_nnz, int32_t on_device) {
+  NvtxRange nv_call("mortar_csr_copy");
   if (!c || (which != 0 && which != 1)) return MORTAR_ERR_INVALID_ARG;
   if (!c->eval_valid) return MORTAR_ERR_STATE;
   const int64_t nnz = which == 0 ? c->nnz_D : c->nnz_M;
@@ -560,6 +587,7 @@ int mortar_get_pair_blocks(mortar_ctx* c, double* M_blocks, double* D_blocks, ui
 
 int mortar_weighted_gap_grad(mortar_ctx* c, const double* lambda, double* J, double* grad_xs, double* grad_xm,
                              int32_t on_device) {
+  NvtxRange nv_call("mortar_weighted_gap_grad");
   if (!c || !lambda) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
   MORTAR_TRY(buf_reserve(c->lambda, (size_t)std::max<int64_t>(c->Ns, 1) * 24));
@@ -574,6 +602,7 @@ int mortar_weighted_gap_grad(mortar_ctx* c, const double* lambda, double* J, dou
 
 int mortar_tangent(mortar_ctx* c, const double* ys, const double* ym, int32_t add_direct, int32_t on_device,
                    int64_t* nnzb) {
+  NvtxRange nv_call("mortar_tangent");
   if (!c || !ys || !ym) return MORTAR_ERR_INVALID_ARG;
   if (c->opt.integration != MORTAR_INTEGRATE_SEGMENT) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
@@ -629,6 +658,7 @@ int mortar_tangent(mortar_ctx* c, const double* ys, const double* ym, int32_t ad
 
 int mortar_contact_terms(mortar_ctx* c, const double* lambda_n, double cpen, double* normals, double* gap,
                          uint8_t* active, double* ncp, int32_t on_device) {
+  NvtxRange nv_call("mortar_contact_terms");
   if (!c) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
   if (lambda_n && !(cpen > 0.0)) return MORTAR_ERR_INVALID_ARG;
@@ -669,6 +699,7 @@ int mortar_tangent_copy(mortar_ctx* c, int64_t* rowptr, int32_t* colidx, double*
 }
 
 int mortar_get_gradient(mortar_ctx* c, double* J, double* grad_xs, double* grad_xm, int32_t on_device) {
+  NvtxRange nv_call("mortar_get_gradient");
   if (!c) return MORTAR_ERR_INVALID_ARG;
   if (!c->grad_valid) return MORTAR_ERR_STATE;
   if (J) *J = c->hstat->J;
@@ -678,6 +709,7 @@ int mortar_get_gradient(mortar_ctx* c, double* J, double* grad_xs, double* grad_
 }
 
 int mortar_run_graph(mortar_ctx* c, const double* lambda, int32_t on_device) {
+  NvtxRange nv_call("mortar_run_graph");
   if (!c) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
   Phases ph;
@@ -778,6 +810,7 @@ int mortar_set_launch(mortar_ctx* c, int32_t variant, int32_t block_size, int32_
 
 int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int32_t* variant, int32_t* rounds,
                     int32_t* block_size, float* best_ms) {
+  NvtxRange nv_call("mortar_autotune");
   if (!c) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
   Phases ph;

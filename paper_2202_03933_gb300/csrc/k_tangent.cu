@@ -74,24 +74,18 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   const int lane = threadIdx.x & 31;
   const int32_t s = g.ps[p], m = g.pm[p];
   const double* r = g.srec + (int64_t)SR_STRIDE * s;
-  V3 X[4], Y[4];
+  const int32_t* cs = g.conn_s + (int64_t)NS * s;
+  const int32_t* cm = g.conn_m + (int64_t)NM * m;
   double yS[4] = {0, 0, 0, 0}, yM[4] = {0, 0, 0, 0};
-  for (int a = 0; a < NS; ++a) {
-    const int64_t n = g.conn_s[(int64_t)NS * s + a];
-    X[a] = v3(g.xs[3 * n], g.xs[3 * n + 1], g.xs[3 * n + 2]);
-    yS[a] = g.ys[3 * n + cp];
-  }
-  for (int l = 0; l < NM; ++l) {
-    const int64_t n = g.conn_m[(int64_t)NM * m + l];
-    Y[l] = v3(g.xm[3 * n], g.xm[3 * n + 1], g.xm[3 * n + 2]);
-    yM[l] = g.ym[3 * n + cp];
-  }
+  for (int a = 0; a < NS; ++a) yS[a] = g.ys[3 * (int64_t)cs[a] + cp];
+  for (int l = 0; l < NM; ++l) yM[l] = g.ym[3 * (int64_t)cm[l] + cp];
   const V3 x0 = v3(r[SR_X0], r[SR_X0 + 1], r[SR_X0 + 2]);
   const V3 t1 = v3(r[SR_T1], r[SR_T1 + 1], r[SR_T1 + 2]);
   const V3 t2 = v3(r[SR_T2], r[SR_T2 + 1], r[SR_T2 + 2]);
   double mu[4], mv[4];
   for (int l = 0; l < NM; ++l) {
-    const double dx = Y[l].x - x0.x, dy = Y[l].y - x0.y, dz = Y[l].z - x0.z;
+    const int64_t n = cm[l];
+    const double dx = g.xm[3 * n] - x0.x, dy = g.xm[3 * n + 1] - x0.y, dz = g.xm[3 * n + 2] - x0.z;
     mu[l] = dx * t1.x + dy * t1.y + dz * t1.z;
     mv[l] = dx * t2.x + dy * t2.y + dz * t2.z;
   }
@@ -103,9 +97,9 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   for (int l = 0; l < NM; ++l) ma2 += cross2(mu[l], mv[l], mu[(l + 1) % NM], mv[(l + 1) % NM]);
   const bool mrev = ma2 < 0.0;
   const bool srev = r[SR_REV] != 0.0;
-  ClipRec<NS> clip;
+  ClipPool<NS, NM> clip;   // compact record: master corners + intersections
   unsigned long long clip_dummy = 0;
-  const bool nonempty = clip.template run<NM>(r, mu, mv, mrev, live ? clip_over : clip_dummy);
+  const bool nonempty = clip.run(r, mu, mv, mrev, live ? clip_over : clip_dummy);
   double* kout = g.Kp + 288 * p + 24 * cp;   // row a at + 72 a
   const int nr = nonempty ? clip.nr : 0;
   MapInverse mi;
@@ -118,17 +112,16 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   } else {
     si.setup(smap, false);
   }
-  double Ru[kPolyA], Rv[kPolyA], Rbu[4][kPolyA], Rbv[4][kPolyA];
-  for (int k = 0; k < nr; ++k) {
-    Ru[k] = clip.pu(k);
-    Rv[k] = clip.pv(k);
+  // per-seed adjoints of the polygon vertices, kept at the vertices' pool slots
+  constexpr int kSlots = ClipPool<NS, NM>::kSlots;
+  double Rbu[4][kSlots], Rbv[4][kSlots];
+  for (int k = 0; k < clip.nv; ++k)
     for (int e = 0; e < NS; ++e) { Rbu[e][k] = 0.0; Rbv[e][k] = 0.0; }
-  }
   double cu = 0.0, cv = 0.0;
   int ncell = nr >= 3 ? 1 : 0;
   if (nr > 3) {
     double su = 0.0, sv = 0.0;
-    for (int k = 0; k < nr; ++k) { su += Ru[k]; sv += Rv[k]; }
+    for (int k = 0; k < nr; ++k) { su += clip.u(k); sv += clip.v(k); }
     cu = su / (double)nr;
     cv = sv / (double)nr;
     ncell = nr;
@@ -140,17 +133,17 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   const int gbase = 3 * (lane / 3);
   for (int cI = 0; cI < ncell_w; ++cI) {
     const bool cell_ok = cI < ncell;
-    int ib = 0, iw = 0;
+    int ib = 0, iw = 0;   // pool slots of the cell's two polygon vertices
     double au = 0.0, av = 0.0;
     if (cell_ok) {
       if (nr == 3) {
-        au = Ru[0]; av = Rv[0]; ib = 1; iw = 2;
+        au = clip.u(0); av = clip.v(0); ib = clip.id(1); iw = clip.id(2);
       } else {
-        au = cu; av = cv; ib = cI; iw = cI + 1 == nr ? 0 : cI + 1;
+        au = cu; av = cv; ib = clip.id(cI); iw = clip.id(cI + 1 == nr ? 0 : cI + 1);
       }
     }
-    const double e1u = cell_ok ? Ru[ib] - au : 0.0, e1v = cell_ok ? Rv[ib] - av : 0.0;
-    const double e2u = cell_ok ? Ru[iw] - au : 0.0, e2v = cell_ok ? Rv[iw] - av : 0.0;
+    const double e1u = cell_ok ? clip.pu[ib] - au : 0.0, e1v = cell_ok ? clip.pv[ib] - av : 0.0;
+    const double e2u = cell_ok ? clip.pu[iw] - au : 0.0, e2v = cell_ok ? clip.pv[iw] - av : 0.0;
     const double crs = cross2(e1u, e1v, e2u, e2v);
     const double area = 0.5 * fabs(crs);
     double arb[4], e1bu[4], e1bv[4], e2bu[4], e2bv[4], xbu_c[4], xbv_c[4];
@@ -271,7 +264,12 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
         Rbu[e][ib] += e1bu[e]; Rbv[e][ib] += e1bv[e];
         Rbu[e][iw] += e2bu[e]; Rbv[e][iw] += e2bv[e];
         const double abu = xbu_c[e] - (e1bu[e] + e2bu[e]), abv = xbv_c[e] - (e1bv[e] + e2bv[e]);
-        if (nr == 3) { Rbu[e][0] += abu; Rbv[e][0] += abv; } else { cbu[e] += abu; cbv[e] += abv; }
+        if (nr == 3) {
+          const int s0 = clip.id(0);
+          Rbu[e][s0] += abu; Rbv[e][s0] += abv;
+        } else {
+          cbu[e] += abu; cbv[e] += abv;
+        }
       }
     }
   }
@@ -286,14 +284,28 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   if (nr > 3) {
     const double inv = 1.0 / (double)nr;
     for (int e = 0; e < NS; ++e)
-      for (int k = 0; k < nr; ++k) { Rbu[e][k] += cbu[e] * inv; Rbv[e][k] += cbv[e] * inv; }
+      for (int k = 0; k < nr; ++k) {
+        const int sk = clip.id(k);
+        Rbu[e][sk] += cbu[e] * inv; Rbv[e][sk] += cbv[e] * inv;
+      }
   }
-  // ---- per seed: clip and merge, map coefficients, projection and plane
+  // ---- per seed: clip and merge, map coefficients, projection and plane;
+  //      node coordinates read again here (L1/L2) rather than held through
+  //      the quadrature loop
   const V3 n0 = v3(r[SR_N0], r[SR_N0 + 1], r[SR_N0 + 2]);
-  double Ks[4][24];
+  V3 X[4], Y[4];
+  for (int a = 0; a < NS; ++a) {
+    const int64_t n = cs[a];
+    X[a] = v3(g.xs[3 * n], g.xs[3 * n + 1], g.xs[3 * n + 2]);
+  }
+  for (int l = 0; l < NM; ++l) {
+    const int64_t n = cm[l];
+    Y[l] = v3(g.xm[3 * n], g.xm[3 * n + 1], g.xm[3 * n + 2]);
+  }
+  double Ks[DUAL ? 4 : 1][24];   // seed rows, combined through A at the end (dual LMs)
   for (int e = 0; e < NS; ++e) {
     double sbu[4] = {0, 0, 0, 0}, sbv[4] = {0, 0, 0, 0}, mbu[4] = {0, 0, 0, 0}, mbv[4] = {0, 0, 0, 0};
-    clip.template reverse<NM>(r, Rbu[e], Rbv[e], srev, mrev, sbu, sbv, mbu, mbv);
+    clip.reverse(r, Rbu[e], Rbv[e], srev, mrev, sbu, sbv, mbu, mbv);
     double smb[8], mmb[8];
     for (int k = 0; k < 8; ++k) {
       smb[k] = acc[(16 * e + k) * kTanThreads];
@@ -305,23 +317,32 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
     for (int a = 0; a < 4; ++a)
       for (int d = 0; d < 3; ++d) { gX[a][d] = 0.0; gY[a][d] = 0.0; }
     plane_reverse<NS, NM>(X, Y, x0, t1, t2, n0, sbu, sbv, mbu, mbv, gX, gY);
-    for (int a = 0; a < 4; ++a)
-      for (int d = 0; d < 3; ++d) {
-        Ks[e][3 * a + d] = gX[a][d];
-        Ks[e][12 + 3 * a + d] = gY[a][d];
-      }
-  }
-  for (int a = 0; a < 4; ++a)
-    for (int k = 0; k < 24; ++k) {
-      double v = 0.0;
-      if (a < NS) {
-        if (DUAL)
-          for (int e = 0; e < NS; ++e) v = fma(r[SR_A + 4 * a + e], Ks[e][k], v);
-        else
-          v = Ks[a][k];
-      }
-      kout[72 * a + k] = v;
+    if (DUAL) {
+      for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 3; ++d) {
+          Ks[DUAL ? e : 0][3 * a + d] = gX[a][d];
+          Ks[DUAL ? e : 0][12 + 3 * a + d] = gY[a][d];
+        }
+    } else {   // standard LMs: seed e is row e
+      for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 3; ++d) {
+          kout[72 * e + 3 * a + d] = gX[a][d];
+          kout[72 * e + 12 + 3 * a + d] = gY[a][d];
+        }
     }
+  }
+  if (DUAL) {
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 24; ++k) {
+        double v = 0.0;
+        if (a < NS)
+          for (int e = 0; e < NS; ++e) v = fma(r[SR_A + 4 * a + e], Ks[e][k], v);
+        kout[72 * a + k] = v;
+      }
+  } else {
+    for (int a = NS; a < 4; ++a)
+      for (int k = 0; k < 24; ++k) kout[72 * a + k] = 0.0;
+  }
   if (DUAL)
     for (int e = 0; e < 4; ++e) g.Op[12 * p + 3 * e + cp] = e < NS ? O[e] : 0.0;
 }
