@@ -793,9 +793,7 @@ int mortar_set_watchdog(mortar_ctx* c, int32_t watchdog_us) {
 
 int mortar_set_launch(mortar_ctx* c, int32_t variant, int32_t block_size, int32_t chunk_pairs, int32_t rounds) {
   if (!c || variant < 0 || variant > 1 || block_size < 0 || block_size > kMaxPairBlock || (block_size % 32) != 0 ||
-      chunk_pairs < 0 || (rounds != 0 && rounds != 1 && rounds != 2 && rounds != 4))
-    return MORTAR_ERR_INVALID_ARG;
-  if (variant == 0 && !integrate_batched_fits(rounds > 0 ? rounds : 2, block_size > 0 ? block_size : 128))
+      chunk_pairs < 0 || (rounds != 0 && rounds != 1 && rounds != 2 && rounds != 4 && rounds != 8 && rounds != 16))
     return MORTAR_ERR_INVALID_ARG;
   c->variant = variant;
   c->block_size = block_size;
@@ -825,9 +823,11 @@ int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int3
   // 32 or 128 pairs per work-counter fetch
   struct Cand { int32_t variant, rounds, block, chunk; };
   std::vector<Cand> cands;
-  for (int32_t r : {1, 2, 4})
+  // (8 and 16 rounds only for the adjoint pair kernel: the forward-only
+  // integration kernel runs at most 4, see integrate_rounds)
+  for (int32_t r : {1, 2, 4, 8, 16})
     for (int32_t b : {64, 128, 256})
-      if (integrate_batched_fits(r, b)) cands.push_back({0, r, b, 0});   // the shape serves both kernels
+      if (ph.adjoint ? true : (r <= 4 && integrate_batched_fits(r, b))) cands.push_back({0, r, b, 0});
   for (int32_t b : {64, 128, 256})
     for (int32_t k : {32, 128}) cands.push_back({1, 0, b, k});
   const bool timing = c->timing;

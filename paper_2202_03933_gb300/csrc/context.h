@@ -139,6 +139,7 @@ void launch_candidates(mortar_ctx* c);
 // k_integrate.cu
 void launch_integrate(mortar_ctx* c, const RunParams& rp);
 bool integrate_batched_fits(int rounds, int block);   // shared memory of the batched kernel fits
+int integrate_rounds(int rounds, int block);          // rounds the integration kernel uses for a setting
 
 // k_contact.cu
 void launch_contact_terms(mortar_ctx* c, bool with_ncp, double cpen);   // normals, gap (+ active, ncp)

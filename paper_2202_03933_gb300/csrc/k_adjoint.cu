@@ -24,6 +24,7 @@
 // point atomics), and J is reduced with a fixed tree: results are bitwise
 // reproducible.
 #include <algorithm>
+#include <type_traits>
 
 #include "clip.cuh"
 #include "context.h"
@@ -652,28 +653,41 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
     double* __restrict__ J_out, FwdOut fo, DevStatus* st, unsigned long long* cta_t, int32_t watchdog_us) {
   cta_mark(cta_t, 0);
   constexpr int B = 32 * R;
-  __shared__ uint8_t perm_s[kMaxPairBlock / 32][B];
+  using PermT = typename std::conditional<(B > 256), uint16_t, uint8_t>::type;
+  __shared__ PermT perm_s[kMaxPairBlock / 32][B];
+  __shared__ uint8_t key_s[kMaxPairBlock / 32][B];
   extern __shared__ double adj_coef[];   // kAdjCoef doubles per thread, interleaved
-  uint8_t* perm = perm_s[threadIdx.x >> 5];
+  PermT* perm = perm_s[threadIdx.x >> 5];
+  uint8_t* keys = key_s[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   AdjCounters ctr;
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
+  // near the end of the queue a warp takes 32 pairs at a time, so that the
+  // last batches do not leave most warps idle
+  const int64_t tail = (int64_t)B * 2 * gridDim.x * (blockDim.x >> 5);
   const Watchdog wd(watchdog_us);
   for (;;) {   // bounded: the shared counter only grows
     if (wd.expired(&st->timeout)) break;
     int64_t base = 0;
-    if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr2, (unsigned long long)B);
+    int fetch = B;
+    if (lane == 0) {
+      const unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(&st->work_ctr2);
+      if ((int64_t)seen + tail > n) fetch = 32;
+      base = (int64_t)atomicAdd(&st->work_ctr2, (unsigned long long)fetch);
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
+    fetch = __shfl_sync(0xffffffffu, fetch, 0);
     if (base >= n) break;
+    const int64_t lim = min(n, base + (int64_t)fetch);
+    const int rounds = (fetch + 31) >> 5;
     // phase A: cell count of each pair (clip without recording); empty pairs done here
-    int key[R];
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
+#pragma unroll 1
+    for (int rr = 0; rr < rounds; ++rr) {
       const int64_t p = base + rr * 32 + lane;
       int nr = 0;
-      if (p < n) {
+      if (p < lim) {
         const double* r = srec + (int64_t)SR_STRIDE * ps[p];
         PlaneMap mm;
         double Pu[kPolyS], Pv[kPolyS];
@@ -703,25 +717,25 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
           }
         }
       }
-      key[rr] = nr == 0 ? 0 : (nr == 3 ? 1 : nr);
+      keys[rr * 32 + lane] = (uint8_t)(nr == 0 ? 0 : (nr == 3 ? 1 : nr));
     }
-    int pos[R];
+    __syncwarp();
+    // counting sort of the batch by cell count, descending (ballots per value)
     int basecnt = 0;
 #pragma unroll 1
     for (int v = kPolyS; v >= 1; --v) {
       int before = 0;
-#pragma unroll
-      for (int rr = 0; rr < R; ++rr) {
-        const unsigned mk = __ballot_sync(0xffffffffu, key[rr] == v);
-        if (key[rr] == v) pos[rr] = basecnt + before + __popc(mk & lt_mask);
+#pragma unroll 1
+      for (int rr = 0; rr < rounds; ++rr) {
+        const int slot = rr * 32 + lane;
+        const bool hit = keys[slot] == v;
+        const unsigned mk = __ballot_sync(0xffffffffu, hit);
+        if (hit) perm[basecnt + before + __popc(mk & lt_mask)] = (PermT)slot;
         before += __popc(mk);
       }
       basecnt += before;
     }
     const int n_live = basecnt;
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr)
-      if (key[rr] > 0) perm[pos[rr]] = (uint8_t)(rr * 32 + lane);
     __syncwarp();
     // phase B: full adjoint of each non-empty pair, rounds of similar cell counts
     for (int i0 = 0; i0 < n_live; i0 += 32) {
@@ -1074,7 +1088,9 @@ void launch_batched_f(mortar_ctx* c, int rounds) {
   };
   if (rounds <= 1) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 1>);
   else if (rounds == 2) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 2>);
-  else go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 4>);
+  else if (rounds == 4) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 4>);
+  else if (rounds == 8) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 8>);
+  else go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 16>);
 }
 
 // The warp-batched adjoint always produces the forward blocks as well (the

@@ -245,12 +245,21 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_integrate_batched(
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
   const unsigned lt_mask = (1u << lane) - 1u;
   const Watchdog wd(rp.watchdog_us);
+  // near the end of the queue a warp takes 32 pairs at a time
+  const int64_t tail = (int64_t)B * 2 * gridDim.x * (blockDim.x >> 5);
   for (;;) {   // bounded: the shared counter only grows
     if (wd.expired(&st->timeout)) break;
     int64_t base = 0;
-    if (lane == 0) base = (int64_t)atomicAdd(&st->work_ctr, (unsigned long long)B);
+    int fetch = B;
+    if (lane == 0) {
+      const unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(&st->work_ctr);
+      if ((int64_t)seen + tail > n) fetch = 32;
+      base = (int64_t)atomicAdd(&st->work_ctr, (unsigned long long)fetch);
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
+    fetch = __shfl_sync(0xffffffffu, fetch, 0);
     if (base >= n) break;
+    const int64_t lim = min(n, base + (int64_t)fetch);
     // ---- phase A: clip one pair per lane, results to shared memory
     int key[R];
 #pragma unroll
@@ -258,7 +267,7 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_integrate_batched(
       const int slot = rr * 32 + lane;
       const int64_t p = base + slot;
       int nr = 0;
-      if (p < n) {
+      if (p < lim) {
         const int32_t s = ps[p];
         const double* r = srec + (int64_t)SR_STRIDE * s;
         PlaneMap mm;
@@ -462,6 +471,14 @@ bool integrate_batched_fits(int rounds, int block) {
   return block >= 32 && block <= kMaxPairBlock && (size_t)(block / 32) * per_warp <= kMaxDynSmem;
 }
 
+int integrate_rounds(int rounds, int block) {
+  // the integration kernel keeps each batch's polygons in shared memory:
+  // at most 4 rounds (128 pairs per warp), fewer where 8 warps would not fit
+  int r = rounds <= 1 ? 1 : (rounds == 2 ? 2 : 4);
+  while (r > 1 && !integrate_batched_fits(r, block)) r >>= 1;
+  return r;
+}
+
 void launch_integrate_raw(const IntegrateArgs& a, const RunParams& rp, int nen_s, int nen_m, int n_sm) {
   launch_dispatch(a, rp, nen_s, nen_m, n_sm, 0, 128, 32, 2);
 }
@@ -482,7 +499,7 @@ void launch_integrate(mortar_ctx* c, const RunParams& rp) {
   }
   const int block = c->block_size > 0 ? c->block_size : 128;
   const int chunk = c->chunk_pairs > 0 ? c->chunk_pairs : 32;
-  const int rounds = c->rounds > 0 ? c->rounds : 2;
+  const int rounds = integrate_rounds(c->rounds > 0 ? c->rounds : 2, block);
   launch_dispatch(a, rp, c->nen_s, c->nen_m, c->n_sm, c->variant, block, chunk, rounds);
 }
 #endif  // MORTAR_PAIR_NS

@@ -253,7 +253,8 @@ def test_full_size_planar_2000_adjoint_sampled(mt, orc):
     assert abs(J - Jr) <= 1e-12 * np.abs(rs).max()
 
 
-@pytest.mark.parametrize("variant,rounds,block", [(1, 0, 64), (1, 0, 256), (0, 1, 256), (0, 4, 64)])
+@pytest.mark.parametrize("variant,rounds,block", [(1, 0, 64), (1, 0, 256), (0, 1, 256), (0, 4, 64), (0, 8, 128),
+                                                  (0, 16, 256)])
 def test_adjoint_launch_variants(mt, orc, variant, rounds, block):
     """Both adjoint schedules give the oracle's gradient (bilinear and tri3
     masters, dual segment mode, warped slave)."""
