@@ -19,6 +19,10 @@ Parity status per function (how each is pinned is in ``tests/test_oracle_*.py``)
       form beyond those invariants
   weighted_gap_grad                  -- pinned (finite differences, Euler
       homogeneity, translation invariance)
+  quadratic_element_D / quadratic_pair_blocks (tri6, quad8 slaves) -- pinned
+      (shape-function identities, element D against an independent
+      high-order rule, slave area, linear-field reproduction, row sums, the
+      overlap area, sub-elements coinciding with master elements)
   element_based_blocks / evaluate_element_based -- pinned (exact slave area
       and linear-field reproduction on full coverage, matching meshes, a
       brute-force point location over all master elements, convergence to the
@@ -115,6 +119,13 @@ def _load():
             lib.oracle_tri_rule.argtypes = [i32, P, i32]
             lib.oracle_invert_map.restype = ctypes.c_int
             lib.oracle_invert_map.argtypes = [i32, P, P, ctypes.POINTER(Opts), P]
+            lib.oracle_quadratic_element_D.restype = ctypes.c_int
+            lib.oracle_quadratic_element_D.argtypes = [P, P, i64, i32, P]
+            lib.oracle_quadratic_pair_blocks.restype = ctypes.c_int
+            lib.oracle_quadratic_pair_blocks.argtypes = [P, P, i32, P, P, i32, ctypes.POINTER(Opts),
+                                                         P, P, i64, P, P, P]
+            lib.oracle_quadratic_shape.restype = ctypes.c_int
+            lib.oracle_quadratic_shape.argtypes = [i32, f64, f64, P, P]
             _lib = lib
     return _lib
 
@@ -274,6 +285,49 @@ class Result:
     stats: dict
 
 
+QUADRATIC = (6, 8)   # tri6, quad8 slave elements
+
+
+def shape_quadratic(nen: int, xi: float, eta: float):
+    """Quadratic shape functions (tri6: 6, quad8: 8) and their parameter
+    derivatives (nen x 2) at one point."""
+    lib = _load()
+    N = np.zeros(8)
+    dN = np.zeros(16)
+    if lib.oracle_quadratic_shape(int(nen), float(xi), float(eta), _p(N), _p(dN)) != 0:
+        raise ValueError("nen must be 6 or 8")
+    return N[:nen].copy(), dN.reshape(8, 2)[:nen].copy()
+
+
+def quadratic_element_D(itf):
+    """Element-domain D blocks (Es, 8, 8) of a quadratic slave mesh, standard LMs."""
+    lib = _load()
+    xs, cs, _, _ = _mesh_arrays(itf)
+    E = cs.shape[0]
+    De = np.zeros((max(E, 1), 64))
+    if lib.oracle_quadratic_element_D(_p(xs), _p(cs), E, cs.shape[1], _p(De)) != 0:
+        raise ValueError("slave elements must be tri6 or quad8")
+    return De[:E].reshape(E, 8, 8)
+
+
+def quadratic_pair_blocks(itf, s, m, opts: Opts | None = None):
+    """Per-pair M blocks (P, 8, 4) of a quadratic slave mesh (segment-based on
+    the four linear sub-elements), nonempty flags and counters."""
+    lib = _load()
+    o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
+    xs, cs, xm, cm = _mesh_arrays(itf)
+    s = np.ascontiguousarray(s, np.int32)
+    m = np.ascontiguousarray(m, np.int32)
+    P = s.shape[0]
+    Mb = np.zeros((max(P, 1), 32))
+    ne = np.zeros(max(P, 1), np.uint8)
+    st = np.zeros(7, np.int64)
+    if lib.oracle_quadratic_pair_blocks(_p(xs), _p(cs), cs.shape[1], _p(xm), _p(cm), cm.shape[1],
+                                        ctypes.byref(o), _p(s), _p(m), P, _p(Mb), _p(ne), _p(st)) != 0:
+        raise ValueError("slave elements must be tri6 or quad8")
+    return Mb[:P].reshape(P, 8, 4), ne[:P].astype(bool), dict(zip(STAT_NAMES, (int(x) for x in st)))
+
+
 def evaluate(itf, opts: Opts | None = None, search: str = "binned", pairs=None) -> Result:
     """Search + per-pair integration + assembly, all on the CPU."""
     o = opts if opts is not None else make_opts(lm=itf.lm, delta=itf.delta)
@@ -283,6 +337,14 @@ def evaluate(itf, opts: Opts | None = None, search: str = "binned", pairs=None) 
         s, m = search_bruteforce(itf, o.delta)
     else:
         s, m = search_binned(itf, o.delta)
+    if np.asarray(itf.conn_s).shape[1] in QUADRATIC:
+        # quadratic slave elements: standard LMs and element-domain D only
+        if o.lm != 0 or o.d_domain != 0:
+            raise ValueError("quadratic slave elements: standard LMs and element-domain D only")
+        De = quadratic_element_D(itf)
+        Mb, ne, st = quadratic_pair_blocks(itf, s, m, o)
+        D, M = assemble(itf, s, m, Mb, None, ne, De, 0, 0)
+        return Result(s, m, Mb, None, ne, None, De, D, M, st)
     A, De = element_blocks(itf, o.lm)
     Mb, Db, ne, st = pair_blocks(itf, s, m, o)
     D, M = assemble(itf, s, m, Mb, Db, ne, De, o.d_domain, o.lm)

@@ -410,15 +410,18 @@ T polygon_signed_area2(const std::vector<V2<T>>& P) {  // twice the signed area
   return s;
 }
 
+template <class T> struct Cell { V2<T> a, b, c; };
+
+// Steps (1)-(4) of Algorithm 1 for one slave/master pair: projection onto the
+// slave element's auxiliary plane, clipping, merge, triangulation.  Writes the
+// projected slave and master polygons (element node order) and the cells;
+// returns false (no cells) when the pair contributes nothing.
 template <class T>
-void integrate_pair(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const Opts& o,
-                    PairOut<T>& out, Stats& st) {
+bool pair_cells(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const Opts& o, Stats& st, V2<T> ps[4],
+                V2<T> pm[4], std::vector<Cell<T>>& cells, int& nverts) {
   const int nen_s = S.nen;
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) { out.M[a][b] = T(0.0); out.D[a][b] = T(0.0); }
-  out.nonempty = false;
-  out.nverts = 0;
-  st.pairs++;
+  cells.clear();
+  nverts = 0;
 
   // tolerances from the real slave geometry (diameter, projected area)
   double h_s = 0.0;
@@ -432,7 +435,6 @@ void integrate_pair(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const O
   const double eps_merge = o.merge_tol_rel * h_s;
 
   // (1) project all nodes onto the auxiliary plane; in-plane coordinates
-  V2<T> ps[4], pm[4];
   for (int a = 0; a < nen_s; ++a) {
     V3<T> d = sub(S.X[a], S.x0);
     ps[a] = {dot(d, S.t1), dot(d, S.t2)};
@@ -481,15 +483,12 @@ void integrate_pair(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const O
   for (const V2<T>& v : poly)
     if (P.empty() || !close(v, P.back())) P.push_back(v);
   while (P.size() > 1 && close(P.back(), P.front())) P.pop_back();
-  if (P.size() < 3) return;
-  if (0.5 * std::fabs(val(polygon_signed_area2(P))) < eps_area) return;
-  out.nonempty = true;
-  out.nverts = (int)P.size();
+  if (P.size() < 3) return false;
+  if (0.5 * std::fabs(val(polygon_signed_area2(P))) < eps_area) return false;
+  nverts = (int)P.size();
   st.nonempty++;
 
   // (4) triangulate into integration cells
-  struct Cell { V2<T> a, b, c; };
-  std::vector<Cell> cells;
   const size_t nv = P.size();
   if (nv == 3) {
     cells.push_back({P[0], P[1], P[2]});
@@ -503,10 +502,26 @@ void integrate_pair(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const O
     for (size_t i = 0; i < nv; ++i) cells.push_back({c, P[i], P[(i + 1) % nv]});
   }
   st.cells += (int64_t)cells.size();
+  return true;
+}
+
+template <class T>
+void integrate_pair(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const Opts& o,
+                    PairOut<T>& out, Stats& st) {
+  const int nen_s = S.nen;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) { out.M[a][b] = T(0.0); out.D[a][b] = T(0.0); }
+  out.nonempty = false;
+  out.nverts = 0;
+  st.pairs++;
+  V2<T> ps[4], pm[4];
+  std::vector<Cell<T>> cells;
+  if (!pair_cells<T>(S, Xm, nen_m, o, st, ps, pm, cells, out.nverts)) return;
+  out.nonempty = true;
 
   // (5) quadrature on each cell with back-projection to both elements
   const std::vector<TriPoint> rule = o.tri_rule == 25 ? rule_tri_duffy(5) : rule_tri7();
-  for (const Cell& C : cells) {
+  for (const Cell<T>& C : cells) {
     T ar2 = cross2(sub2(C.b, C.a), sub2(C.c, C.a));
     T area = 0.5 * tabs(ar2);
     for (const TriPoint& q : rule) {
@@ -531,6 +546,168 @@ void integrate_pair(const SlaveData<T>& S, const V3<T> Xm[4], int nen_m, const O
       st.gauss_points++;
     }
   }
+}
+
+// --------------------------------------------------------------------------
+// quadratic slave elements (tri6, quad8), standard Lagrange multipliers
+// --------------------------------------------------------------------------
+// quad8 (serendipity): corners 0..3 at (-1,-1), (1,-1), (1,1), (-1,1), mid-side
+// nodes 4..7 at (0,-1), (1,0), (0,1), (-1,0):
+//   corner:   N = (1 + xi xi_a)(1 + eta eta_a)(xi xi_a + eta eta_a - 1) / 4,
+//   xi_a = 0: N = (1 - xi^2)(1 + eta eta_a) / 2,  eta_a = 0: N = (1 + xi xi_a)(1 - eta^2) / 2.
+// tri6: corners 0..2 at (0,0), (1,0), (0,1), mid-side nodes 3 (edge 0-1),
+// 4 (edge 1-2), 5 (edge 2-0); with L = (1 - xi - eta, xi, eta):
+//   corner i: N = L_i (2 L_i - 1),  mid-side (i, j): N = 4 L_i L_j.
+static const double kQ8Node[8][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}, {0, -1}, {1, 0}, {0, 1}, {-1, 0}};
+
+inline void shape_quadratic(int nen, double xi, double eta, double N[8], double dN[8][2]) {
+  if (nen == 8) {
+    for (int a = 0; a < 8; ++a) {
+      const double xa = kQ8Node[a][0], ea = kQ8Node[a][1];
+      if (a < 4) {
+        N[a] = 0.25 * (1.0 + xi * xa) * (1.0 + eta * ea) * (xi * xa + eta * ea - 1.0);
+        dN[a][0] = 0.25 * xa * (1.0 + eta * ea) * (2.0 * xi * xa + eta * ea);
+        dN[a][1] = 0.25 * ea * (1.0 + xi * xa) * (xi * xa + 2.0 * eta * ea);
+      } else if (xa == 0.0) {
+        N[a] = 0.5 * (1.0 - xi * xi) * (1.0 + eta * ea);
+        dN[a][0] = -xi * (1.0 + eta * ea);
+        dN[a][1] = 0.5 * ea * (1.0 - xi * xi);
+      } else {
+        N[a] = 0.5 * (1.0 + xi * xa) * (1.0 - eta * eta);
+        dN[a][0] = 0.5 * xa * (1.0 - eta * eta);
+        dN[a][1] = -eta * (1.0 + xi * xa);
+      }
+    }
+  } else {
+    const double L[3] = {1.0 - xi - eta, xi, eta};
+    const double dL[3][2] = {{-1.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}};
+    for (int i = 0; i < 3; ++i) {
+      N[i] = L[i] * (2.0 * L[i] - 1.0);
+      dN[i][0] = (4.0 * L[i] - 1.0) * dL[i][0];
+      dN[i][1] = (4.0 * L[i] - 1.0) * dL[i][1];
+    }
+    const int edge[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+    for (int k = 0; k < 3; ++k) {
+      const int i = edge[k][0], j = edge[k][1];
+      N[3 + k] = 4.0 * L[i] * L[j];
+      dN[3 + k][0] = 4.0 * (L[j] * dL[i][0] + L[i] * dL[j][0]);
+      dN[3 + k][1] = 4.0 * (L[j] * dL[i][1] + L[i] * dL[j][1]);
+    }
+    for (int a = 6; a < 8; ++a) { N[a] = 0.0; dN[a][0] = 0.0; dN[a][1] = 0.0; }
+  }
+}
+
+// The four linear sub-elements of a quadratic element: their corners (parent
+// local nodes; -1 = the quad8 centre xi = eta = 0) and the corners' parent
+// parameter coordinates, counter-clockwise like the parent.  quad8 -> four
+// quad4 (corner, mid-side, centre, mid-side); tri6 -> four tri3 (three corner
+// triangles and the middle one).
+struct SubElement { int nen; int node[4]; double ref[4][2]; };
+
+inline void sub_elements(int nen_p, SubElement sub[4]) {
+  if (nen_p == 8) {
+    const SubElement q[4] = {
+        {4, {0, 4, -1, 7}, {{-1, -1}, {0, -1}, {0, 0}, {-1, 0}}},
+        {4, {4, 1, 5, -1}, {{0, -1}, {1, -1}, {1, 0}, {0, 0}}},
+        {4, {-1, 5, 2, 6}, {{0, 0}, {1, 0}, {1, 1}, {0, 1}}},
+        {4, {7, -1, 6, 3}, {{-1, 0}, {0, 0}, {0, 1}, {-1, 1}}}};
+    for (int k = 0; k < 4; ++k) sub[k] = q[k];
+  } else {
+    const SubElement t[4] = {
+        {3, {0, 3, 5, 0}, {{0, 0}, {0.5, 0}, {0, 0.5}, {0, 0}}},
+        {3, {3, 1, 4, 0}, {{0.5, 0}, {1, 0}, {0.5, 0.5}, {0, 0}}},
+        {3, {5, 4, 2, 0}, {{0, 0.5}, {0.5, 0.5}, {0, 1}, {0, 0}}},
+        {3, {3, 4, 5, 0}, {{0.5, 0}, {0.5, 0.5}, {0, 0.5}, {0, 0}}}};
+    for (int k = 0; k < 4; ++k) sub[k] = t[k];
+  }
+}
+
+// Element-domain D of a quadratic element, standard LMs (Eq.
+// DiscreteWeakFormInterfaceFlux over the whole element): De[a][b] =
+// sum_q w_q J(xi_q) N_a N_b with the 3x3 Gauss-Legendre rule (quad8) or the
+// 7-point rule (tri6), exact for flat elements (N_a N_b of degree <= 4 per
+// direction).
+inline void element_D_quadratic(int nen, const V3<double> X[8], double De[8][8]) {
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) De[a][b] = 0.0;
+  for (const ElemPoint& q : element_rule(nen == 8 ? 4 : 3)) {
+    double N[8], dN[8][2];
+    shape_quadratic(nen, q.xi, q.eta, N, dN);
+    V3<double> g1{0.0, 0.0, 0.0}, g2 = g1;
+    for (int a = 0; a < nen; ++a) {
+      g1 = {g1.x + dN[a][0] * X[a].x, g1.y + dN[a][0] * X[a].y, g1.z + dN[a][0] * X[a].z};
+      g2 = {g2.x + dN[a][1] * X[a].x, g2.y + dN[a][1] * X[a].y, g2.z + dN[a][1] * X[a].z};
+    }
+    const V3<double> n = cross(g1, g2);
+    const double wj = q.w * std::sqrt(dot(n, n));
+    for (int a = 0; a < nen; ++a)
+      for (int b = 0; b < nen; ++b) De[a][b] += wj * N[a] * N[b];
+  }
+}
+
+// One quadratic slave element against one master element: steps (1)-(4) of
+// Algorithm 1 on each linear sub-element (the piecewise flat approximation of
+// the slave surface, Sec. 2.3), the 7-point rule on every cell, and at every
+// point the sub-element parameters mapped to the parent's, where the
+// quadratic shape functions are evaluated:
+//   M[a][l] += W N_a(xi_parent) N_l(xi_m).
+inline void integrate_pair_quadratic(int nen_p, const V3<double> Xp[8], const V3<double> Xm[4], int nen_m,
+                                     const Opts& o, double M[8][4], bool& nonempty, Stats& st) {
+  for (int a = 0; a < 8; ++a)
+    for (int l = 0; l < 4; ++l) M[a][l] = 0.0;
+  nonempty = false;
+  st.pairs++;
+  SubElement sub[4];
+  sub_elements(nen_p, sub);
+  V3<double> xc{0.0, 0.0, 0.0};
+  if (nen_p == 8) {   // the centre point of the quad8
+    double N[8], dN[8][2];
+    shape_quadratic(8, 0.0, 0.0, N, dN);
+    for (int a = 0; a < 8; ++a) xc = {xc.x + N[a] * Xp[a].x, xc.y + N[a] * Xp[a].y, xc.z + N[a] * Xp[a].z};
+  }
+  const std::vector<TriPoint> rule = rule_tri7();
+  for (int k = 0; k < 4; ++k) {
+    const SubElement& se = sub[k];
+    SlaveData<double> S;
+    S.nen = se.nen;
+    for (int j = 0; j < 4; ++j) S.X[j] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < se.nen; ++j) S.X[j] = se.node[j] < 0 ? xc : Xp[se.node[j]];
+    slave_frame<double>(S);
+    Stats sk;
+    V2<double> ps[4], pm[4];
+    std::vector<Cell<double>> cells;
+    int nv = 0;
+    if (!pair_cells<double>(S, Xm, nen_m, o, sk, ps, pm, cells, nv)) {
+      st.clip_overflow += sk.clip_overflow;
+      continue;
+    }
+    nonempty = true;
+    st.cells += sk.cells;
+    st.clip_overflow += sk.clip_overflow;
+    for (const Cell<double>& C : cells) {
+      const double area = 0.5 * std::fabs(cross2(sub2(C.b, C.a), sub2(C.c, C.a)));
+      for (const TriPoint& q : rule) {
+        V2<double> xg{q.l0 * C.a.u + q.l1 * C.b.u + q.l2 * C.c.u, q.l0 * C.a.v + q.l1 * C.b.v + q.l2 * C.c.v};
+        const double W = q.w * area;
+        double xs[2], xm[2];
+        invert_map<double>(se.nen, ps, xg, o, xs, st);
+        invert_map<double>(nen_m, pm, xg, o, xm, st);
+        double Nsub[4], Nm[4];
+        shape<double>(se.nen, xs[0], xs[1], Nsub);
+        shape<double>(nen_m, xm[0], xm[1], Nm);
+        double xp = 0.0, ep = 0.0;   // parent parameters (an affine map of the sub-element's)
+        for (int j = 0; j < se.nen; ++j) { xp += Nsub[j] * se.ref[j][0]; ep += Nsub[j] * se.ref[j][1]; }
+        double Np[8], dNp[8][2];
+        shape_quadratic(nen_p, xp, ep, Np, dNp);
+        for (int a = 0; a < nen_p; ++a) {
+          const double wn = W * Np[a];
+          for (int l = 0; l < nen_m; ++l) M[a][l] += wn * Nm[l];
+        }
+        st.gauss_points++;
+      }
+    }
+  }
+  if (nonempty) st.nonempty++;
 }
 
 // --------------------------------------------------------------------------
@@ -1148,4 +1325,76 @@ int oracle_invert_map(int32_t nen, const double* p, const double* x, const Opts*
   return st.newton_fail == 0 ? 1 : 0;
 }
 
+
+// Quadratic slave elements (tri6, quad8; standard LMs, element-domain D):
+// element D blocks (Es x 64, row-major 8 x 8) ...
+int oracle_quadratic_element_D(const double* xs, const int32_t* cs, int64_t Es, int32_t nen, double* De) {
+  if (nen != 6 && nen != 8) return -1;
+  for (int64_t e = 0; e < Es; ++e) {
+    V3<double> X[8];
+    for (int a = 0; a < 8; ++a) X[a] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < nen; ++a) {
+      const double* p = xs + 3 * (int64_t)cs[(int64_t)nen * e + a];
+      X[a] = {p[0], p[1], p[2]};
+    }
+    double D[8][8];
+    element_D_quadratic(nen, X, D);
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) De[64 * e + 8 * a + b] = D[a][b];
+  }
+  return 0;
+}
+
+// ... and per-pair M blocks (P x 32, row-major 8 x 4), nonempty flags, counters.
+int oracle_quadratic_pair_blocks(const double* xs, const int32_t* cs, int32_t nen_s, const double* xm,
+                                 const int32_t* cm, int32_t nen_m, const Opts* o, const int32_t* ps,
+                                 const int32_t* pm, int64_t P, double* M_out, uint8_t* nonempty, int64_t* stats) {
+  if (nen_s != 6 && nen_s != 8) return -1;
+  for (int k = 0; k < 7; ++k) stats[k] = 0;
+  int nt = o->n_threads > 0 ? o->n_threads : 1;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+  {
+    Stats st;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 256)
+#endif
+    for (int64_t p = 0; p < P; ++p) {
+      V3<double> Xp[8], Xm[4];
+      for (int a = 0; a < 8; ++a) Xp[a] = {0.0, 0.0, 0.0};
+      for (int a = 0; a < nen_s; ++a) {
+        const double* q = xs + 3 * (int64_t)cs[(int64_t)nen_s * ps[p] + a];
+        Xp[a] = {q[0], q[1], q[2]};
+      }
+      for (int l = 0; l < 4; ++l) Xm[l] = {0.0, 0.0, 0.0};
+      for (int l = 0; l < nen_m; ++l) {
+        const double* q = xm + 3 * (int64_t)cm[(int64_t)nen_m * pm[p] + l];
+        Xm[l] = {q[0], q[1], q[2]};
+      }
+      double M[8][4];
+      bool ne = false;
+      integrate_pair_quadratic(nen_s, Xp, Xm, nen_m, *o, M, ne, st);
+      for (int a = 0; a < 8; ++a)
+        for (int l = 0; l < 4; ++l) M_out[32 * p + 4 * a + l] = M[a][l];
+      nonempty[p] = ne ? 1 : 0;
+    }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+    add_stats(stats, st);
+  }
+  (void)nt;
+  return 0;
+}
+
+// Quadratic shape functions and their parameter derivatives at one point
+// (N: 8, dN: 16 row-major [a][xi, eta]; tri6 fills 6).
+int oracle_quadratic_shape(int32_t nen, double xi, double eta, double* N, double* dN) {
+  if (nen != 6 && nen != 8) return -1;
+  double n[8], d[8][2];
+  shape_quadratic(nen, xi, eta, n, d);
+  for (int a = 0; a < 8; ++a) { N[a] = n[a]; dN[2 * a] = d[a][0]; dN[2 * a + 1] = d[a][1]; }
+  return 0;
+}
 }  // extern "C"

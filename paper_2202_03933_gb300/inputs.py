@@ -173,6 +173,78 @@ def kite_master(ns: int, nm: int, d: float, lm: int = LM_STANDARD, name: str = "
                      info={"ns": ns, "nm": nm, "kite_d": d})
 
 
+QUAD8, TRI6 = 8, 6
+
+
+def quadratic_grid(n: int, kind: str):
+    """Parameter-plane nodes (uv in [0,1]^2, z = 0) and connectivity of an n x n
+    quad8 mesh, or of its tri6 split (each quad cut along the diagonal from its
+    first to its third corner).  Node ids: corners j (n+1) + i, then the
+    mid-points of the horizontal edges, of the vertical edges and (tri6) of the
+    diagonals.  quad8 order: 4 corners counter-clockwise, then the mid-sides of
+    edges 0-1, 1-2, 2-3, 3-0; tri6: 3 corners, then edges 0-1, 1-2, 2-0."""
+    h = 1.0 / n
+    corners = grid_nodes(n, n)
+    i, j = np.meshgrid(np.arange(n), np.arange(n + 1), indexing="xy")
+    hmid = np.stack([(i.ravel() + 0.5) * h, j.ravel() * h, np.zeros(i.size)], 1)
+    i, j = np.meshgrid(np.arange(n + 1), np.arange(n), indexing="xy")
+    vmid = np.stack([i.ravel() * h, (j.ravel() + 0.5) * h, np.zeros(i.size)], 1)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    dmid = np.stack([(i.ravel() + 0.5) * h, (j.ravel() + 0.5) * h, np.zeros(i.size)], 1)
+    nc, nh, nv = corners.shape[0], hmid.shape[0], vmid.shape[0]
+    i = i.ravel()
+    j = j.ravel()
+    c00 = j * (n + 1) + i
+    c10, c11, c01 = c00 + 1, c00 + n + 2, c00 + n + 1
+    hb, ht = nc + j * n + i, nc + (j + 1) * n + i
+    vl, vr = nc + nh + j * (n + 1) + i, nc + nh + j * (n + 1) + i + 1
+    if kind == "quad8":
+        x = np.concatenate([corners, hmid, vmid])
+        conn = np.stack([c00, c10, c11, c01, hb, vr, ht, vl], 1)
+    elif kind == "tri6":
+        x = np.concatenate([corners, hmid, vmid, dmid])
+        dg = nc + nh + nv + j * n + i
+        lower = np.stack([c00, c10, c11, hb, vr, dg], 1)
+        upper = np.stack([c00, c11, c01, dg, ht, vl], 1)
+        conn = np.empty((2 * lower.shape[0], 6), dtype=np.int64)
+        conn[0::2] = lower
+        conn[1::2] = upper
+    else:
+        raise ValueError(kind)
+    return x, conn.astype(np.int32)
+
+
+def quadratic_planar(ns: int, nm: int, kind: str = "quad8", seed: int = SEED_BASE + 21,
+                     noise: float = 0.1, warp: float = 0.0, name: str = "quadratic") -> Interface:
+    """ns x ns quad8 (or tri6) slave mesh on the unit square against an nm x nm
+    quad4 master with the in-plane node noise of planar_noisy.  warp > 0 moves
+    every slave node (mid-sides included) in-plane by warp * h_s * sin(pi x)
+    sin(pi y) along (1, 1): curved element edges, boundary unchanged."""
+    xs, cs = quadratic_grid(ns, kind)
+    if warp:
+        f = warp / ns * np.sin(np.pi * xs[:, 0]) * np.sin(np.pi * xs[:, 1])
+        xs = xs.copy()
+        xs[:, 0] += f
+        xs[:, 1] += f
+    m = planar_noisy(2, nm, LM_STANDARD, seed, name, noise=noise)
+    return Interface(name, xs, cs, QUAD8 if kind == "quad8" else TRI6, m.xm, m.conn_m, QUAD4, lm=LM_STANDARD,
+                     delta=1e-9, info={"ns": ns, "nm": nm, "kind": kind, "noise": noise, "warp": warp})
+
+
+def quadratic_cylinder(ns: int = 24, nm: int = 21, kind: str = "quad8", seed: int = SEED_BASE + 22,
+                       name: str = "quadratic_cylinder") -> Interface:
+    """Curved quadratic slave elements: the quad8 (tri6) mesh of the 90 degree
+    cylinder patch r = 1, z in [0, 2] with every node (mid-sides included) on
+    the cylinder, against the chord-quad4 master of cylinder_patch."""
+    xs, cs = quadratic_grid(ns, kind)
+    th = 0.5 * math.pi * xs[:, 0]
+    z = 2.0 * xs[:, 1]
+    xs = np.stack([np.cos(th), np.sin(th), z], 1)
+    cyl = cylinder_patch(4, nm, LM_STANDARD, seed, name)
+    return Interface(name, xs, cs, QUAD8 if kind == "quad8" else TRI6, cyl.xm, cyl.conn_m, QUAD4, lm=LM_STANDARD,
+                     delta=0.05 / ns, info={"ns": ns, "nm": nm, "kind": kind})
+
+
 def planar_8x7() -> Interface:
     """8x8 vs 7x7 quad4, +-0.1 h_m in-plane master noise, standard LMs."""
     return planar_noisy(8, 7, LM_STANDARD, SEED_BASE + 1, "planar_8x7")
