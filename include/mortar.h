@@ -60,7 +60,20 @@ typedef enum mortar_status {
   MORTAR_ERR_NOT_BUILT = -9    /* functionality not available in this build */
 } mortar_status;
 
-enum { MORTAR_TRI3 = 3, MORTAR_QUAD4 = 4 };
+/* Element types (number of nodes).  Linear: tri3, quad4 (both sides).
+ * Quadratic (slave side only; Sec. 2.3 admits higher-order interpolation):
+ * tri6 = corners 0-2 at (0,0), (1,0), (0,1), mid-side nodes 3 (edge 0-1),
+ * 4 (edge 1-2), 5 (edge 2-0); quad8 (serendipity) = corners 0-3 at (-1,-1),
+ * (1,-1), (1,1), (-1,1), mid-side nodes 4-7 at (0,-1), (1,0), (0,1), (-1,0).
+ * A quadratic slave element is integrated on its piecewise flat
+ * approximation (four linear sub-elements, each clipped against the master
+ * element), with the quadratic shape functions evaluated at the parent
+ * parameters of every quadrature point.  Quadratic slave elements support the
+ * forward path only: standard multipliers, element-domain D, segment-based
+ * integration, no facing test (other options: MORTAR_ERR_INVALID_ARG at
+ * mortar_set_interface / mortar_set_batch); the adjoint, the linearisation,
+ * the contact terms and the autotuner return MORTAR_ERR_INVALID_ARG. */
+enum { MORTAR_TRI3 = 3, MORTAR_QUAD4 = 4, MORTAR_TRI6 = 6, MORTAR_QUAD8 = 8 };
 enum { MORTAR_LM_STANDARD = 0, MORTAR_LM_DUAL = 1 };
 /* Domain of D: ELEMENT integrates D over the whole slave element (the
  * definition in Eq. DiscreteWeakFormInterfaceFlux, so sum(D) is the slave
@@ -145,8 +158,8 @@ int mortar_create(mortar_ctx** ctx, const mortar_options* o, void* stream);
 void mortar_destroy(mortar_ctx* ctx);
 
 /* Define one interface (Eq. AnsatzDiscretization: slave and master node
- * coordinates and connectivity).  type_s / type_m: MORTAR_QUAD4 or
- * MORTAR_TRI3.  Copies the data; node ids are checked against the node
+ * coordinates and connectivity).  type_s: MORTAR_QUAD4, MORTAR_TRI3,
+ * MORTAR_QUAD8 or MORTAR_TRI6; type_m: MORTAR_QUAD4 or MORTAR_TRI3.  Copies the data; node ids are checked against the node
  * counts (MORTAR_ERR_INVALID_ARG).  Empty meshes are allowed. */
 int mortar_set_interface(mortar_ctx* ctx,
                          const double* xs, int64_t n_slave_nodes,
@@ -203,7 +216,9 @@ int mortar_csr_copy(mortar_ctx* ctx, int32_t which, int64_t* rowptr, int32_t* co
 /* Per-pair blocks of the last evaluation, in pair order: M_blocks and D_blocks
  * are (n_pairs x 16) FP64, row a = slave local node, column = master (or
  * slave) local node, 4x4 padded with zeros; nonempty is n_pairs bytes.
- * D_blocks is filled only in segment mode (may be NULL). */
+ * D_blocks is filled only in segment mode (may be NULL).  Quadratic slave
+ * elements: M_blocks is (n_pairs x 32), 8 x 4 rows of slave local nodes
+ * padded with zeros, and D_blocks must be NULL. */
 int mortar_get_pair_blocks(mortar_ctx* ctx, double* M_blocks, double* D_blocks, uint8_t* nonempty,
                            int64_t capacity, int32_t on_device);
 

@@ -107,7 +107,7 @@ int alloc_pair_buffers(mortar_ctx* c, int64_t cap) {
   const size_t n = (size_t)std::max<int64_t>(cap, 1);
   MORTAR_TRY(buf_reserve(c->pairs_s, n * 4));
   MORTAR_TRY(buf_reserve(c->pairs_m, n * 4));
-  MORTAR_TRY(buf_reserve(c->Mblk, n * 16 * 8));
+  MORTAR_TRY(buf_reserve(c->Mblk, n * mblk_stride(c) * 8));
   if (c->opt.d_domain == MORTAR_D_SEGMENT) MORTAR_TRY(buf_reserve(c->Dblk, n * 16 * 8));
   MORTAR_TRY(buf_reserve(c->flag, n));
   c->pair_cap = cap;
@@ -272,7 +272,7 @@ int run_status(const DevStatus& h, const Phases& ph) {
 
 int run(mortar_ctx* c, const Phases& ph) {
   if (!c->have_interface) return MORTAR_ERR_STATE;
-  if (ph.adjoint && c->opt.integration != MORTAR_INTEGRATE_SEGMENT) return MORTAR_ERR_INVALID_ARG;
+  if (ph.adjoint && (c->opt.integration != MORTAR_INTEGRATE_SEGMENT || quadratic_slave(c))) return MORTAR_ERR_INVALID_ARG;
   c->stats.reruns = 0;
   for (int attempt = 0; attempt < 4; ++attempt) {
     if (ph.adjoint) MORTAR_TRY(prepare_adjoint_buffers(c));
@@ -295,7 +295,14 @@ int set_common(mortar_ctx* c, int32_t n_if, const int64_t* sn_off, const int64_t
                const int64_t* me_off, const double* xs, const int32_t* conn_s, int32_t type_s, const double* xm,
                const int32_t* conn_m, int32_t type_m, int32_t on_device) {
   if (!c || n_if < 1) return MORTAR_ERR_INVALID_ARG;
-  if ((type_s != MORTAR_QUAD4 && type_s != MORTAR_TRI3) || (type_m != MORTAR_QUAD4 && type_m != MORTAR_TRI3))
+  const bool quad_s = type_s == MORTAR_TRI6 || type_s == MORTAR_QUAD8;
+  if ((type_s != MORTAR_QUAD4 && type_s != MORTAR_TRI3 && !quad_s) ||
+      (type_m != MORTAR_QUAD4 && type_m != MORTAR_TRI3))
+    return MORTAR_ERR_INVALID_ARG;
+  // quadratic slave elements: standard multipliers, element-domain D,
+  // segment-based integration, no facing test (the forward path only)
+  if (quad_s && (c->opt.lm != MORTAR_LM_STANDARD || c->opt.d_domain != MORTAR_D_ELEMENT ||
+                 c->opt.integration != MORTAR_INTEGRATE_SEGMENT || c->opt.facing_test != 0))
     return MORTAR_ERR_INVALID_ARG;
   for (int i = 0; i < n_if; ++i)
     if (sn_off[i + 1] < sn_off[i] || se_off[i + 1] < se_off[i] || mn_off[i + 1] < mn_off[i] ||
@@ -361,8 +368,9 @@ int set_common(mortar_ctx* c, int32_t n_if, const int64_t* sn_off, const int64_t
   cudaMemcpyAsync(c->chunk_ptr.p, cptr.data(), (n_if + 1) * 4, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(c->bin_cap_off.p, capoff.data(), (n_if + 1) * 8, cudaMemcpyHostToDevice, st);
   // per-element workspaces
-  MORTAR_TRY(buf_reserve(c->srec, Es * SR_STRIDE * 8));
-  MORTAR_TRY(buf_reserve(c->De, Es * 16 * 8));
+  // quadratic slave elements: four sub-element records and an 8 x 8 D block each
+  MORTAR_TRY(buf_reserve(c->srec, Es * (quad_s ? 4 : 1) * SR_STRIDE * 8));
+  MORTAR_TRY(buf_reserve(c->De, Es * (quad_s ? 64 : 16) * 8));
   MORTAR_TRY(buf_reserve(c->box_s, Es * 8 * 8));
   MORTAR_TRY(buf_reserve(c->box_m, Em * 8 * 8));
   if (c->opt.facing_test) MORTAR_TRY(buf_reserve(c->nrm_m, Em * 3 * 8));
@@ -384,7 +392,8 @@ int set_common(mortar_ctx* c, int32_t n_if, const int64_t* sn_off, const int64_t
   MORTAR_TRY(buf_reserve(c->n2e_m_ent, Em * type_m * 8));
   const int64_t scan_n = std::max<int64_t>({c->bin_cap, c->Es, c->Ns, c->Nm, c->Em, 1});
   MORTAR_TRY(buf_reserve(c->scan_tmp, (size_t)scan_temp_words(scan_n) * 8));
-  if (c->pair_cap < 8 * c->Es + 1024) MORTAR_TRY(alloc_pair_buffers(c, 8 * c->Es + 1024));
+  if (c->pair_cap < 8 * c->Es + 1024 || c->Mblk.bytes < (size_t)c->pair_cap * mblk_stride(c) * 8)
+    MORTAR_TRY(alloc_pair_buffers(c, std::max<int64_t>(c->pair_cap, 8 * c->Es + 1024)));
   if (c->nnz_cap_D < 9 * c->Ns + 64 || c->nnz_cap_M < 16 * c->Ns + 64)
     MORTAR_TRY(alloc_csr_buffers(c, std::max(c->nnz_cap_D, 9 * c->Ns + 64), std::max(c->nnz_cap_M, 16 * c->Ns + 64)));
   // validation
@@ -576,7 +585,7 @@ int mortar_get_pair_blocks(mortar_ctx* c, double* M_blocks, double* D_blocks, ui
   if (!c->eval_valid) return MORTAR_ERR_STATE;
   if (capacity < c->n_pairs) return MORTAR_ERR_CAPACITY;
   const size_t P = (size_t)c->n_pairs;
-  if (M_blocks) MORTAR_TRY(copy_out(M_blocks, c->Mblk.p, P * 128, on_device, c->stream));
+  if (M_blocks) MORTAR_TRY(copy_out(M_blocks, c->Mblk.p, P * mblk_stride(c) * 8, on_device, c->stream));
   if (D_blocks) {
     if (c->opt.d_domain != MORTAR_D_SEGMENT) return MORTAR_ERR_STATE;
     MORTAR_TRY(copy_out(D_blocks, c->Dblk.p, P * 128, on_device, c->stream));
@@ -606,6 +615,7 @@ int mortar_tangent(mortar_ctx* c, const double* ys, const double* ym, int32_t ad
   if (!c || !ys || !ym) return MORTAR_ERR_INVALID_ARG;
   if (c->opt.integration != MORTAR_INTEGRATE_SEGMENT) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
+  if (quadratic_slave(c)) return MORTAR_ERR_INVALID_ARG;
   MORTAR_TRY(buf_reserve(c->tan_ys, (size_t)std::max<int64_t>(c->Ns, 1) * 24));
   MORTAR_TRY(buf_reserve(c->tan_ym, (size_t)std::max<int64_t>(c->Nm, 1) * 24));
   MORTAR_TRY(copy_in(c->tan_ys.p, ys, (size_t)c->Ns * 24, on_device, c->stream));
@@ -662,6 +672,7 @@ int mortar_contact_terms(mortar_ctx* c, const double* lambda_n, double cpen, dou
   if (!c) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
   if (lambda_n && !(cpen > 0.0)) return MORTAR_ERR_INVALID_ARG;
+  if (quadratic_slave(c)) return MORTAR_ERR_INVALID_ARG;
   int r0 = MORTAR_OK;
   if (!c->eval_valid) {
     Phases ph;
@@ -811,14 +822,15 @@ int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int3
   NvtxRange nv_call("mortar_autotune");
   if (!c) return MORTAR_ERR_INVALID_ARG;
   if (!c->have_interface) return MORTAR_ERR_STATE;
+  if (quadratic_slave(c)) return MORTAR_ERR_INVALID_ARG;   // one launch shape: nothing to tune
   Phases ph;
   ph.adjoint = lambda != nullptr;
   if (lambda) {
     MORTAR_TRY(buf_reserve(c->lambda, (size_t)std::max<int64_t>(c->Ns, 1) * 24));
     MORTAR_TRY(copy_in(c->lambda.p, lambda, (size_t)c->Ns * 24, on_device, c->stream));
   }
-  // candidate launch shapes: the warp-batched kernels with 32, 64 or 128
-  // pairs per warp batch (rounds 1, 2, 4) and 2, 4 or 8 warps per block, and
+  // candidate launch shapes: the warp-batched kernels with 32 R pairs per
+  // warp batch (R = rounds 1, 2, 4, 8, 16) and 2, 4 or 8 warps per block, and
   // the one-pair-per-thread kernels with 64, 128 or 256 threads per block and
   // 32 or 128 pairs per work-counter fetch
   struct Cand { int32_t variant, rounds, block, chunk; };

@@ -166,6 +166,13 @@ void launch_tangent_rows(mortar_ctx* c, const RunParams& rp, int mode);   // 0: 
 
 RunParams run_params(const mortar_ctx* c);
 
+// Quadratic slave elements (tri6, quad8): forward path only, 8 x 4 pair blocks.
+inline bool quadratic_slave(const mortar_ctx* c) { return c->nen_s > 4; }
+inline int mblk_stride(const mortar_ctx* c) { return quadratic_slave(c) ? 32 : 16; }
+
+// k_quadratic.cu
+void launch_integrate_quadratic(mortar_ctx* c, const RunParams& rp);
+
 // Per element-type combination (slave NS, master NM nodes) parts of the pair
 // kernels.  Each is built as an object of its own from the same source file
 // with MORTAR_PAIR_NS / MORTAR_PAIR_NM defined, so the large kernel templates

@@ -552,6 +552,8 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
       const double inv = 1.0 / (double)nr;
       for (int k = 0; k < nr; ++k) { const int sk = cp.id(k); Bu[sk] += cbu * inv; Bv[sk] += cbv * inv; }
     }
+    // Outputs go out with streaming (evict-first) stores: each is written once
+    // and read by a later kernel, and L2 keeps the threads' stack lines instead.
     if (FWD) {   // fused forward: M = A G, D = A H of this pair
       ctr.nonempty++;
       double* mo = fo.Mblk + 16 * p;
@@ -564,7 +566,7 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
             else
               v = G[a][l];
           }
-          mo[4 * a + l] = v;
+          __stcs(mo + 4 * a + l, v);
         }
       if (SEG) {
         double* dout = fo.Dblk + 16 * p;
@@ -577,10 +579,10 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
               else
                 v = H[a][b];
             }
-            dout[4 * a + b] = v;
+            __stcs(dout + 4 * a + b, v);
           }
       }
-      fo.flag[p] = 1;
+      __stcs(fo.flag + p, (uint8_t)1);
     }
     // ---- reverse merge and clipping (vertex pool) and the element maps
     double sbu[4] = {0, 0, 0, 0}, sbv[4] = {0, 0, 0, 0}, mbu[4] = {0, 0, 0, 0}, mbv[4] = {0, 0, 0, 0};
@@ -620,24 +622,24 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
     double* gmo = gm_out + 12 * p;
     for (int a = 0; a < 4; ++a)
       for (int k = 0; k < 3; ++k) {
-        go[3 * a + k] = gX[a][k];
-        gmo[3 * a + k] = gY[a][k];
+        __stcs(go + 3 * a + k, gX[a][k]);
+        __stcs(gmo + 3 * a + k, gY[a][k]);
       }
     if (DUAL) {
       double* ab = ab_out + 16 * p;
       for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 4; ++c) ab[4 * a + c] = (a < NS && c < NS) ? dot(lam[a], Lb[c]) : 0.0;
+        for (int c = 0; c < 4; ++c) __stcs(ab + 4 * a + c, (a < NS && c < NS) ? dot(lam[a], Lb[c]) : 0.0);
     }
   } else {
     double2* g1 = reinterpret_cast<double2*>(gs_out + 12 * p);
     double2* g2 = reinterpret_cast<double2*>(gm_out + 12 * p);
-    for (int k = 0; k < 6; ++k) { g1[k] = make_double2(0.0, 0.0); g2[k] = make_double2(0.0, 0.0); }
+    for (int k = 0; k < 6; ++k) { __stcs(g1 + k, make_double2(0.0, 0.0)); __stcs(g2 + k, make_double2(0.0, 0.0)); }
     if (DUAL) {
       double2* a2 = reinterpret_cast<double2*>(ab_out + 16 * p);
-      for (int k = 0; k < 8; ++k) a2[k] = make_double2(0.0, 0.0);
+      for (int k = 0; k < 8; ++k) __stcs(a2 + k, make_double2(0.0, 0.0));
     }
   }
-  J_out[p] = Jp;
+  __stcs(J_out + p, Jp);
 }
 
 // shared-memory coefficients per thread of the batched adjoint kernel: CY and [seg] SX
@@ -697,23 +699,23 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
           double2* g1 = reinterpret_cast<double2*>(gs_out + 12 * p);
           double2* g2 = reinterpret_cast<double2*>(gm_out + 12 * p);
 #pragma unroll
-          for (int k = 0; k < 6; ++k) { g1[k] = make_double2(0.0, 0.0); g2[k] = make_double2(0.0, 0.0); }
+          for (int k = 0; k < 6; ++k) { __stcs(g1 + k, make_double2(0.0, 0.0)); __stcs(g2 + k, make_double2(0.0, 0.0)); }
           if (DUAL) {
             double2* a2 = reinterpret_cast<double2*>(ab_out + 16 * p);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) a2[k] = make_double2(0.0, 0.0);
+            for (int k = 0; k < 8; ++k) __stcs(a2 + k, make_double2(0.0, 0.0));
           }
-          J_out[p] = 0.0;
+          __stcs(J_out + p, 0.0);
           if (FWD) {
             double2* mo = reinterpret_cast<double2*>(fo.Mblk + 16 * p);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) mo[k] = make_double2(0.0, 0.0);
+            for (int k = 0; k < 8; ++k) __stcs(mo + k, make_double2(0.0, 0.0));
             if (SEG) {
               double2* dd = reinterpret_cast<double2*>(fo.Dblk + 16 * p);
 #pragma unroll
-              for (int k = 0; k < 8; ++k) dd[k] = make_double2(0.0, 0.0);
+              for (int k = 0; k < 8; ++k) __stcs(dd + k, make_double2(0.0, 0.0));
             }
-            fo.flag[p] = 0;
+            __stcs(fo.flag + p, (uint8_t)0);
           }
         }
       }

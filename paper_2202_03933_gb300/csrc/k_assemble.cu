@@ -23,8 +23,12 @@ template <int NEN>
 __global__ void k_adj_count(const int32_t* __restrict__ conn, int64_t E, int32_t* __restrict__ cnt) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  for (int a = 0; a < NEN; ++a) atomicAdd(&cnt[conn[NEN * e + a]], 1);
+  for (int a = 0; a < NEN; ++a) atomicAdd(&cnt[conn[(int64_t)NEN * e + a]], 1);
 }
+
+// Entry of the adjacency: element e, local node a, as e << kLocalBits(NEN) | a.
+template <int NEN>
+constexpr int kLocalBits = NEN > 4 ? 3 : 2;
 
 template <int NEN>
 __global__ void k_adj_fill(const int32_t* __restrict__ conn, int64_t E, const int64_t* __restrict__ ptr,
@@ -32,9 +36,9 @@ __global__ void k_adj_fill(const int32_t* __restrict__ conn, int64_t E, const in
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   for (int a = 0; a < NEN; ++a) {
-    const int32_t n = conn[NEN * e + a];
+    const int32_t n = conn[(int64_t)NEN * e + a];
     const int32_t slot = atomicSub(&cnt[n], 1) - 1;
-    ent[ptr[n] + slot] = e * 4 + a;
+    ent[ptr[n] + slot] = (e << kLocalBits<NEN>) | a;
   }
 }
 
@@ -51,8 +55,11 @@ __global__ void k_adj_sort(const int64_t* __restrict__ ptr, int64_t N, int64_t* 
 }
 
 // Entry source of one row.  WHICH: 0 = element-domain D, 1 = segment D, 2 = M.
+// Blocks: linear slave elements 4 x 4 (16 per element or pair); quadratic
+// slave elements 8 x 8 element D (64) and 8 x 4 pair M (32).
 template <int WHICH, int NS, int NM>
 struct RowSource {
+  static constexpr int kRowW = NS > 4 ? 8 : 4;   // slave-side block row width
   const int64_t* n2e_ptr;
   const int64_t* n2e_ent;
   const int64_t* pair_off;
@@ -68,13 +75,14 @@ struct RowSource {
     const int64_t q0 = n2e_ptr[j], q1 = n2e_ptr[j + 1];
     for (int64_t q = q0; q < q1; ++q) {
       const int64_t ee = n2e_ent[q];
-      const int64_t e = ee >> 2;
-      const int a = (int)(ee & 3);
+      const int64_t e = ee >> kLocalBits<NS>;
+      const int a = (int)(ee & ((1 << kLocalBits<NS>) - 1));
       if (WHICH == 0) {
+        const double* de = blk + (int64_t)kRowW * kRowW * e + kRowW * a;
         if (diag_only)
-          f(conn_s[NS * e + a], blk[16 * e + 4 * a + a]);
+          f(conn_s[NS * e + a], de[a]);
         else
-          for (int b = 0; b < NS; ++b) f(conn_s[NS * e + b], blk[16 * e + 4 * a + b]);
+          for (int b = 0; b < NS; ++b) f(conn_s[NS * e + b], de[b]);
       } else {
         const int64_t p0 = pair_off[e], p1 = pair_off[e + 1];
         for (int64_t p = p0; p < p1; ++p) {
@@ -83,7 +91,7 @@ struct RowSource {
             for (int b = 0; b < NS; ++b) f(conn_s[NS * e + b], blk[16 * p + 4 * a + b]);
           } else {
             const int64_t m = pm[p];
-            for (int l = 0; l < NM; ++l) f(conn_m[NM * m + l], blk[16 * p + 4 * a + l]);
+            for (int l = 0; l < NM; ++l) f(conn_m[NM * m + l], blk[4 * kRowW * p + 4 * a + l]);
           }
         }
       }
@@ -230,7 +238,7 @@ void assemble_t(mortar_ctx* c, const double* blkD) {
 
 template <int NS, int NM>
 void assemble_nsnm(mortar_ctx* c, const RunParams& rp) {
-  if (rp.d_domain == 1) assemble_t<1, NS, NM>(c, c->Dblk.as<double>());
+  if (NS <= 4 && rp.d_domain == 1) assemble_t<1, NS, NM>(c, c->Dblk.as<double>());
   else assemble_t<0, NS, NM>(c, c->De.as<double>());
 }
 
@@ -249,12 +257,17 @@ void launch_topology(mortar_ctx* c) {
     const unsigned ge = (unsigned)((E + kThreads - 1) / kThreads);
     if (E > 0) {
       if (nen == 4) k_adj_count<4><<<ge, kThreads, 0, c->stream>>>(conn, E, cnt);
-      else k_adj_count<3><<<ge, kThreads, 0, c->stream>>>(conn, E, cnt);
+      else if (nen == 3) k_adj_count<3><<<ge, kThreads, 0, c->stream>>>(conn, E, cnt);
+      else if (nen == 8) k_adj_count<8><<<ge, kThreads, 0, c->stream>>>(conn, E, cnt);
+      else k_adj_count<6><<<ge, kThreads, 0, c->stream>>>(conn, E, cnt);
     }
     launch_exclusive_scan_i32(cnt, ptr.as<int64_t>(), nullptr, N, c->scan_tmp.as<int64_t>(), c->stream);
     if (E > 0) {
-      if (nen == 4) k_adj_fill<4><<<ge, kThreads, 0, c->stream>>>(conn, E, ptr.as<int64_t>(), cnt, ent.as<int64_t>());
-      else k_adj_fill<3><<<ge, kThreads, 0, c->stream>>>(conn, E, ptr.as<int64_t>(), cnt, ent.as<int64_t>());
+      int64_t* en = ent.as<int64_t>();
+      if (nen == 4) k_adj_fill<4><<<ge, kThreads, 0, c->stream>>>(conn, E, ptr.as<int64_t>(), cnt, en);
+      else if (nen == 3) k_adj_fill<3><<<ge, kThreads, 0, c->stream>>>(conn, E, ptr.as<int64_t>(), cnt, en);
+      else if (nen == 8) k_adj_fill<8><<<ge, kThreads, 0, c->stream>>>(conn, E, ptr.as<int64_t>(), cnt, en);
+      else k_adj_fill<6><<<ge, kThreads, 0, c->stream>>>(conn, E, ptr.as<int64_t>(), cnt, en);
     }
     if (N > 0)
       k_adj_sort<<<(unsigned)((N + kThreads - 1) / kThreads), kThreads, 0, c->stream>>>(ptr.as<int64_t>(), N,
@@ -263,7 +276,11 @@ void launch_topology(mortar_ctx* c) {
 }
 
 void launch_assemble(mortar_ctx* c, const RunParams& rp) {
-  if (c->nen_s == 4 && c->nen_m == 4) assemble_nsnm<4, 4>(c, rp);
+  if (c->nen_s == 8 && c->nen_m == 4) assemble_nsnm<8, 4>(c, rp);
+  else if (c->nen_s == 8) assemble_nsnm<8, 3>(c, rp);
+  else if (c->nen_s == 6 && c->nen_m == 4) assemble_nsnm<6, 4>(c, rp);
+  else if (c->nen_s == 6) assemble_nsnm<6, 3>(c, rp);
+  else if (c->nen_s == 4 && c->nen_m == 4) assemble_nsnm<4, 4>(c, rp);
   else if (c->nen_s == 4 && c->nen_m == 3) assemble_nsnm<4, 3>(c, rp);
   else if (c->nen_s == 3 && c->nen_m == 4) assemble_nsnm<3, 4>(c, rp);
   else assemble_nsnm<3, 3>(c, rp);

@@ -484,6 +484,10 @@ void launch_integrate_raw(const IntegrateArgs& a, const RunParams& rp, int nen_s
 }
 
 void launch_integrate(mortar_ctx* c, const RunParams& rp) {
+  if (quadratic_slave(c)) {
+    launch_integrate_quadratic(c, rp);
+    return;
+  }
   if (rp.integration == 1) {
     c->pair_grid = 0;
     launch_integrate_element_based(c, rp);

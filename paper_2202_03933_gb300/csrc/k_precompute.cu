@@ -15,6 +15,7 @@
 #include <cfloat>
 
 #include "context.h"
+#include "quadratic.cuh"
 
 namespace mortar {
 
@@ -69,6 +70,98 @@ __device__ __forceinline__ void elem_point(int k, double& xi, double& eta, doubl
   }
 }
 
+// Auxiliary plane and clip window of one linear element (or linear
+// sub-element of a quadratic one) with nodes X: writes the record fields x0,
+// t1, t2, n0, the projected map, the window polygon, the tolerances, the
+// orientation flag, the inverse of the affine part and the affine flag, marks
+// a degenerate element (eps_in < 0); returns |g1 x g2| at the centre and the
+// diameter h, and the centre tangents g1, g2.
+template <int NS>
+__device__ __forceinline__ void slave_record(const V3* X, const RunParams& rp, double* r, double& ln, double& h,
+                                             V3& g1, V3& g2, bool& degenerate) {
+  // ---- auxiliary plane at the element centre
+  V3 x0;
+  if constexpr (NS == 4) {
+    x0 = {0.25 * ((X[0].x + X[1].x) + (X[2].x + X[3].x)), 0.25 * ((X[0].y + X[1].y) + (X[2].y + X[3].y)),
+          0.25 * ((X[0].z + X[1].z) + (X[2].z + X[3].z))};
+    g1 = {0.25 * ((X[1].x - X[0].x) + (X[2].x - X[3].x)), 0.25 * ((X[1].y - X[0].y) + (X[2].y - X[3].y)),
+          0.25 * ((X[1].z - X[0].z) + (X[2].z - X[3].z))};
+    g2 = {0.25 * ((X[2].x - X[1].x) + (X[3].x - X[0].x)), 0.25 * ((X[2].y - X[1].y) + (X[3].y - X[0].y)),
+          0.25 * ((X[2].z - X[1].z) + (X[3].z - X[0].z))};
+  } else {
+    const double t = 1.0 / 3.0;
+    x0 = {t * (X[0].x + X[1].x + X[2].x), t * (X[0].y + X[1].y + X[2].y), t * (X[0].z + X[1].z + X[2].z)};
+    g1 = sub(X[1], X[0]);
+    g2 = sub(X[2], X[0]);
+  }
+  V3 n = cross(g1, g2);
+  ln = sqrt(dot(n, n));
+  const V3 n0 = {n.x / ln, n.y / ln, n.z / ln};
+  const V3 ed = sub(X[1], X[0]);
+  const double en = dot(ed, n0);
+  const V3 ep = {ed.x - en * n0.x, ed.y - en * n0.y, ed.z - en * n0.z};
+  const double le = sqrt(dot(ep, ep));
+  const V3 t1 = {ep.x / le, ep.y / le, ep.z / le};
+  const V3 t2 = cross(n0, t1);
+  r[SR_X0] = x0.x; r[SR_X0 + 1] = x0.y; r[SR_X0 + 2] = x0.z;
+  r[SR_T1] = t1.x; r[SR_T1 + 1] = t1.y; r[SR_T1 + 2] = t1.z;
+  r[SR_T2] = t2.x; r[SR_T2 + 1] = t2.y; r[SR_T2 + 2] = t2.z;
+  r[SR_N0] = n0.x; r[SR_N0 + 1] = n0.y; r[SR_N0 + 2] = n0.z;
+  // ---- projected slave polygon
+  double pu[4] = {0, 0, 0, 0}, pv[4] = {0, 0, 0, 0};
+  for (int a = 0; a < NS; ++a) {
+    const V3 d = sub(X[a], x0);
+    pu[a] = dot(d, t1);
+    pv[a] = dot(d, t2);
+  }
+  const PlaneMap pm = plane_map<NS>(pu, pv);
+  r[SR_C + 0] = pm.c0u; r[SR_C + 1] = pm.c0v; r[SR_C + 2] = pm.c1u; r[SR_C + 3] = pm.c1v;
+  r[SR_C + 4] = pm.c2u; r[SR_C + 5] = pm.c2v; r[SR_C + 6] = pm.c3u; r[SR_C + 7] = pm.c3v;
+  double area2 = 0.0;
+  for (int a = 0; a < NS; ++a) area2 += cross2(pu[a], pv[a], pu[(a + 1) % NS], pv[(a + 1) % NS]);
+  for (int a = 0; a < NS; ++a) {
+    const int src = area2 < 0.0 ? NS - 1 - a : a;
+    r[SR_PS + 2 * a] = pu[src];
+    r[SR_PS + 2 * a + 1] = pv[src];
+  }
+  if (NS == 3) { r[SR_PS + 6] = 0.0; r[SR_PS + 7] = 0.0; }
+  r[SR_REV] = area2 < 0.0 ? 1.0 : 0.0;
+  {
+    const double det = pm.c1u * pm.c2v - pm.c2u * pm.c1v;
+    const double id = 1.0 / det;
+    r[SR_BINV + 0] = pm.c2v * id;
+    r[SR_BINV + 1] = -pm.c2u * id;
+    r[SR_BINV + 2] = -pm.c1v * id;
+    r[SR_BINV + 3] = pm.c1u * id;
+    r[SR_AFF] = (NS == 3 || map_is_affine(pm)) ? 1.0 : 0.0;
+    r[SR_AFF + 1] = 0.0; r[SR_AFF + 2] = 0.0; r[SR_AFF + 3] = 0.0;
+  }
+  // ---- tolerances: diameter and projected area
+  double h2 = 0.0;
+  for (int a = 0; a < NS; ++a)
+    for (int b = a + 1; b < NS; ++b) {
+      const V3 d = sub(X[a], X[b]);
+      h2 = fmax(h2, dot(d, d));
+    }
+  h = sqrt(h2);
+  const double em = rp.merge_tol_rel * h;
+  r[SR_EPSIN] = rp.clip_tol_rel * h * h;
+  r[SR_EPSM2] = em * em;
+  r[SR_EPSA] = rp.area_tol_rel * (0.5 * fabs(area2));
+  // an inverted (folded) quad4: its projected corners do not form a convex
+  // polygon of one orientation, and its Jacobian changes sign inside
+  bool folded = false;
+  if constexpr (NS == 4) {
+    for (int a = 0; a < 4; ++a) {
+      const int a1 = (a + 1) & 3, a2 = (a + 2) & 3;
+      const double c = cross2(pu[a1] - pu[a], pv[a1] - pv[a], pu[a2] - pu[a1], pv[a2] - pv[a1]);
+      folded |= !(c * area2 > 0.0);
+    }
+  }
+  degenerate = !(ln > 0.0) || !(le > 0.0) || !(fabs(area2) > 0.0) || !isfinite(h) || folded;
+  if (degenerate) r[SR_EPSIN] = -1.0;   // marks the element; its pairs integrate to nothing
+}
+
 // An element with a non-finite node coordinate gets an all-NaN box: every
 // box-overlap test (closed <= compares) is false for it, so it has no pairs,
 // and the grid's min / max reductions (fmin / fmax) skip it.
@@ -90,88 +183,10 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
       X[a] = {xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]};
       bad |= !(isfinite(X[a].x) && isfinite(X[a].y) && isfinite(X[a].z));
     }
-    // ---- auxiliary plane at the element centre
-    V3 x0, g1, g2;
-    if constexpr (NS == 4) {
-      x0 = {0.25 * ((X[0].x + X[1].x) + (X[2].x + X[3].x)), 0.25 * ((X[0].y + X[1].y) + (X[2].y + X[3].y)),
-            0.25 * ((X[0].z + X[1].z) + (X[2].z + X[3].z))};
-      g1 = {0.25 * ((X[1].x - X[0].x) + (X[2].x - X[3].x)), 0.25 * ((X[1].y - X[0].y) + (X[2].y - X[3].y)),
-            0.25 * ((X[1].z - X[0].z) + (X[2].z - X[3].z))};
-      g2 = {0.25 * ((X[2].x - X[1].x) + (X[3].x - X[0].x)), 0.25 * ((X[2].y - X[1].y) + (X[3].y - X[0].y)),
-            0.25 * ((X[2].z - X[1].z) + (X[3].z - X[0].z))};
-    } else {
-      const double t = 1.0 / 3.0;
-      x0 = {t * (X[0].x + X[1].x + X[2].x), t * (X[0].y + X[1].y + X[2].y), t * (X[0].z + X[1].z + X[2].z)};
-      g1 = sub(X[1], X[0]);
-      g2 = sub(X[2], X[0]);
-    }
-    V3 n = cross(g1, g2);
-    const double ln = sqrt(dot(n, n));
-    const V3 n0 = {n.x / ln, n.y / ln, n.z / ln};
-    const V3 ed = sub(X[1], X[0]);
-    const double en = dot(ed, n0);
-    const V3 ep = {ed.x - en * n0.x, ed.y - en * n0.y, ed.z - en * n0.z};
-    const double le = sqrt(dot(ep, ep));
-    const V3 t1 = {ep.x / le, ep.y / le, ep.z / le};
-    const V3 t2 = cross(n0, t1);
     double* r = srec + (int64_t)SR_STRIDE * e;
-    r[SR_X0] = x0.x; r[SR_X0 + 1] = x0.y; r[SR_X0 + 2] = x0.z;
-    r[SR_T1] = t1.x; r[SR_T1 + 1] = t1.y; r[SR_T1 + 2] = t1.z;
-    r[SR_T2] = t2.x; r[SR_T2 + 1] = t2.y; r[SR_T2 + 2] = t2.z;
-    r[SR_N0] = n0.x; r[SR_N0 + 1] = n0.y; r[SR_N0 + 2] = n0.z;
-    // ---- projected slave polygon
-    double pu[4] = {0, 0, 0, 0}, pv[4] = {0, 0, 0, 0};
-    for (int a = 0; a < NS; ++a) {
-      const V3 d = sub(X[a], x0);
-      pu[a] = dot(d, t1);
-      pv[a] = dot(d, t2);
-    }
-    const PlaneMap pm = plane_map<NS>(pu, pv);
-    r[SR_C + 0] = pm.c0u; r[SR_C + 1] = pm.c0v; r[SR_C + 2] = pm.c1u; r[SR_C + 3] = pm.c1v;
-    r[SR_C + 4] = pm.c2u; r[SR_C + 5] = pm.c2v; r[SR_C + 6] = pm.c3u; r[SR_C + 7] = pm.c3v;
-    double area2 = 0.0;
-    for (int a = 0; a < NS; ++a) area2 += cross2(pu[a], pv[a], pu[(a + 1) % NS], pv[(a + 1) % NS]);
-    for (int a = 0; a < NS; ++a) {
-      const int src = area2 < 0.0 ? NS - 1 - a : a;
-      r[SR_PS + 2 * a] = pu[src];
-      r[SR_PS + 2 * a + 1] = pv[src];
-    }
-    if (NS == 3) { r[SR_PS + 6] = 0.0; r[SR_PS + 7] = 0.0; }
-    r[SR_REV] = area2 < 0.0 ? 1.0 : 0.0;
-    {
-      const double det = pm.c1u * pm.c2v - pm.c2u * pm.c1v;
-      const double id = 1.0 / det;
-      r[SR_BINV + 0] = pm.c2v * id;
-      r[SR_BINV + 1] = -pm.c2u * id;
-      r[SR_BINV + 2] = -pm.c1v * id;
-      r[SR_BINV + 3] = pm.c1u * id;
-      r[SR_AFF] = (NS == 3 || map_is_affine(pm)) ? 1.0 : 0.0;
-      r[SR_AFF + 1] = 0.0; r[SR_AFF + 2] = 0.0; r[SR_AFF + 3] = 0.0;
-    }
-    // ---- tolerances: diameter and projected area
-    double h2 = 0.0;
-    for (int a = 0; a < NS; ++a)
-      for (int b = a + 1; b < NS; ++b) {
-        const V3 d = sub(X[a], X[b]);
-        h2 = fmax(h2, dot(d, d));
-      }
-    const double h = sqrt(h2);
-    const double em = rp.merge_tol_rel * h;
-    r[SR_EPSIN] = rp.clip_tol_rel * h * h;
-    r[SR_EPSM2] = em * em;
-    r[SR_EPSA] = rp.area_tol_rel * (0.5 * fabs(area2));
-    // an inverted (folded) quad4: its projected corners do not form a convex
-    // polygon of one orientation, and its Jacobian changes sign inside
-    bool folded = false;
-    if constexpr (NS == 4) {
-      for (int a = 0; a < 4; ++a) {
-        const int a1 = (a + 1) & 3, a2 = (a + 2) & 3;
-        const double c = cross2(pu[a1] - pu[a], pv[a1] - pv[a], pu[a2] - pu[a1], pv[a2] - pv[a1]);
-        folded |= !(c * area2 > 0.0);
-      }
-    }
-    degenerate = !(ln > 0.0) || !(le > 0.0) || !(fabs(area2) > 0.0) || !isfinite(h) || folded;
-    if (degenerate) r[SR_EPSIN] = -1.0;   // marks the element; its pairs integrate to nothing
+    double ln = 0.0, h = 0.0;
+    V3 g1, g2;
+    slave_record<NS>(X, rp, r, ln, h, g1, g2, degenerate);
     // ---- element integrals Me[a][b] = int N_a N_b, Dh[a] = int N_a (surface measure)
     // An element whose bilinear term is negligible (parallelogram, any tri3) has a
     // constant surface Jacobian J0, and then Me = J0 Mref, Dh = J0 dref exactly.
@@ -287,6 +302,104 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     if (bad) {
       set_nan_box(b);
       r[SR_EPSIN] = -1.0;
+      degenerate = true;
+    }
+  }
+  block_count_add(&st->degenerate, degenerate ? 1ull : 0ull);
+  block_count_add(&st->nonfinite, bad ? 1ull : 0ull);
+}
+
+// Quadratic slave element (tri6, quad8; standard LMs): the records of its
+// four linear sub-elements (record 4 e + k; the piecewise flat approximation
+// of the slave surface, Sec. 2.3, whose clip windows and auxiliary planes the
+// pairs use), the element-domain D with the quadratic isoparametric Jacobian
+// (3x3 Gauss-Legendre on quad8, the 7-point rule on tri6; 8 x 8 block per
+// element) and the search box over all its nodes.
+template <int NP>
+__global__ void __launch_bounds__(kThreads) k_slave_precompute_quadratic(
+    const double* __restrict__ xs, const int32_t* __restrict__ conn, int64_t Es, RunParams rp,
+    double* __restrict__ srec, double* __restrict__ De, double* __restrict__ box, DevStatus* st) {
+  constexpr int NSUB = NP == 8 ? 4 : 3;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool degenerate = false, bad = false;
+  if (e < Es) {
+    V3 X[8];
+    for (int a = 0; a < NP; ++a) {
+      const int64_t n = conn[(int64_t)NP * e + a];
+      X[a] = {xs[3 * n], xs[3 * n + 1], xs[3 * n + 2]};
+      bad |= !(isfinite(X[a].x) && isfinite(X[a].y) && isfinite(X[a].z));
+    }
+    V3 xc = {0.0, 0.0, 0.0};
+    if constexpr (NP == 8) {   // x(0, 0): corners weigh -1/4, mid-sides 1/2
+      for (int a = 0; a < 8; ++a) {
+        const double w = a < 4 ? -0.25 : 0.5;
+        xc = {xc.x + w * X[a].x, xc.y + w * X[a].y, xc.z + w * X[a].z};
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      V3 Xs[4];
+#pragma unroll
+      for (int j = 0; j < NSUB; ++j) {
+        const int a = sub_node<NP>(k, j);
+        Xs[j] = a < 0 ? xc : X[a];
+      }
+      double* r = srec + (int64_t)SR_STRIDE * (4 * e + k);
+      double ln = 0.0, h = 0.0;
+      V3 g1, g2;
+      bool dg = false;
+      slave_record<NSUB>(Xs, rp, r, ln, h, g1, g2, dg);
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) r[SR_A + 4 * a + b] = a == b ? 1.0 : 0.0;
+      degenerate |= dg;
+      if (bad) r[SR_EPSIN] = -1.0;
+    }
+    // element-domain D, standard LMs: De[a][b] = sum_q w J N_a N_b
+    double D[8][8];
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) D[a][b] = 0.0;
+    constexpr int nq = NP == 8 ? 9 : 7;
+    for (int q = 0; q < nq; ++q) {
+      double xi, eta, w;
+      elem_point<NP == 8 ? 4 : 3>(q, xi, eta, w);
+      double N[8], dN[8][2];
+      shape_quadratic<NP>(xi, eta, N);
+      shape_quadratic_grad<NP>(xi, eta, dN);
+      V3 g1 = {0.0, 0.0, 0.0}, g2 = g1;
+      for (int a = 0; a < NP; ++a) {
+        g1 = {g1.x + dN[a][0] * X[a].x, g1.y + dN[a][0] * X[a].y, g1.z + dN[a][0] * X[a].z};
+        g2 = {g2.x + dN[a][1] * X[a].x, g2.y + dN[a][1] * X[a].y, g2.z + dN[a][1] * X[a].z};
+      }
+      const V3 nq3 = cross(g1, g2);
+      const double wj = w * sqrt(dot(nq3, nq3));
+      for (int a = 0; a < NP; ++a)
+        for (int b = 0; b < NP; ++b) D[a][b] += wj * N[a] * N[b];
+    }
+    double* d = De + 64 * e;
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) d[8 * a + b] = D[a][b];
+    // search box (delta-inflated) and diameter over all nodes
+    double lo[3] = {X[0].x, X[0].y, X[0].z}, hi[3] = {X[0].x, X[0].y, X[0].z};
+    for (int a = 1; a < NP; ++a) {
+      lo[0] = fmin(lo[0], X[a].x); hi[0] = fmax(hi[0], X[a].x);
+      lo[1] = fmin(lo[1], X[a].y); hi[1] = fmax(hi[1], X[a].y);
+      lo[2] = fmin(lo[2], X[a].z); hi[2] = fmax(hi[2], X[a].z);
+    }
+    double h2 = 0.0;
+    for (int a = 0; a < NP; ++a)
+      for (int b = a + 1; b < NP; ++b) {
+        const V3 dd = sub(X[a], X[b]);
+        h2 = fmax(h2, dot(dd, dd));
+      }
+    double* b = box + 8 * e;
+    for (int k = 0; k < 3; ++k) {
+      b[k] = lo[k] - rp.delta;
+      b[3 + k] = hi[k] + rp.delta;
+    }
+    b[6] = sqrt(h2);
+    b[7] = 0.0;
+    if (bad) {
+      set_nan_box(b);
       degenerate = true;
     }
   }
@@ -498,6 +611,12 @@ void launch_slave_precompute(mortar_ctx* c, const RunParams& rp) {
   if (c->Es == 0) return;
   const unsigned g = (unsigned)((c->Es + kThreads - 1) / kThreads);
   DevStatus* st = c->dstat.as<DevStatus>();
+  if (c->nen_s == 8 || c->nen_s == 6) {
+    auto kern = c->nen_s == 8 ? k_slave_precompute_quadratic<8> : k_slave_precompute_quadratic<6>;
+    kern<<<g, kThreads, 0, c->stream>>>(c->xs.as<double>(), c->conn_s.as<int32_t>(), c->Es, rp, c->srec.as<double>(),
+                                        c->De.as<double>(), c->box_s.as<double>(), st);
+    return;
+  }
   if (c->nen_s == 4)
     k_slave_precompute<4><<<g, kThreads, 0, c->stream>>>(c->xs.as<double>(), c->conn_s.as<int32_t>(), c->Es, rp,
                                                           c->srec.as<double>(), c->De.as<double>(),

@@ -100,7 +100,9 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   ClipPool<NS, NM> clip;   // compact record: master corners + intersections
   unsigned long long clip_dummy = 0;
   const bool nonempty = clip.run(r, mu, mv, mrev, live ? clip_over : clip_dummy);
-  double* kout = g.Kp + 288 * p + 24 * cp;   // row a at + 72 a
+  // row a at + 72 a; written with streaming (evict-first) stores, so that L2
+  // keeps the threads' stack lines rather than these write-once blocks
+  double* kout = g.Kp + 288 * p + 24 * cp;
   const int nr = nonempty ? clip.nr : 0;
   MapInverse mi;
   mi.setup(mmap, NM == 3 || map_is_affine(mmap));
@@ -276,9 +278,9 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   if (!live) return;
   if (!nonempty) {   // not reached for pairs the count pass found non-empty; blocks stay defined
     for (int a = 0; a < 4; ++a)
-      for (int k = 0; k < 24; ++k) kout[72 * a + k] = 0.0;
+      for (int k = 0; k < 24; ++k) __stcs(kout + 72 * a + k, 0.0);
     if (DUAL)
-      for (int e = 0; e < 4; ++e) g.Op[12 * p + 3 * e + cp] = 0.0;
+      for (int e = 0; e < 4; ++e) __stcs(g.Op + 12 * p + 3 * e + cp, 0.0);
     return;
   }
   if (nr > 3) {
@@ -326,8 +328,8 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
     } else {   // standard LMs: seed e is row e
       for (int a = 0; a < 4; ++a)
         for (int d = 0; d < 3; ++d) {
-          kout[72 * e + 3 * a + d] = gX[a][d];
-          kout[72 * e + 12 + 3 * a + d] = gY[a][d];
+          __stcs(kout + 72 * e + 3 * a + d, gX[a][d]);
+          __stcs(kout + 72 * e + 12 + 3 * a + d, gY[a][d]);
         }
     }
   }
@@ -337,14 +339,14 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
         double v = 0.0;
         if (a < NS)
           for (int e = 0; e < NS; ++e) v = fma(r[SR_A + 4 * a + e], Ks[e][k], v);
-        kout[72 * a + k] = v;
+        __stcs(kout + 72 * a + k, v);
       }
   } else {
     for (int a = NS; a < 4; ++a)
-      for (int k = 0; k < 24; ++k) kout[72 * a + k] = 0.0;
+      for (int k = 0; k < 24; ++k) __stcs(kout + 72 * a + k, 0.0);
   }
   if (DUAL)
-    for (int e = 0; e < 4; ++e) g.Op[12 * p + 3 * e + cp] = e < NS ? O[e] : 0.0;
+    for (int e = 0; e < 4; ++e) __stcs(g.Op + 12 * p + 3 * e + cp, e < NS ? O[e] : 0.0);
 }
 
 // Persistent kernel over warp batches of 32 R pairs, each sorted by cell count

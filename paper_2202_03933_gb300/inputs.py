@@ -81,8 +81,8 @@ class Interface:
     """One slave/master pair of surface meshes (inputs only)."""
     name: str
     xs: np.ndarray          # (Ns, 3) float64 slave node coordinates
-    conn_s: np.ndarray      # (Es, 4 or 3) int32 slave connectivity (0-based)
-    type_s: int             # QUAD4 or TRI3
+    conn_s: np.ndarray      # (Es, 4, 3, 8 or 6) int32 slave connectivity (0-based)
+    type_s: int             # QUAD4, TRI3, QUAD8 or TRI6
     xm: np.ndarray          # (Nm, 3) float64 master node coordinates
     conn_m: np.ndarray      # (Em, 4 or 3) int32 master connectivity
     type_m: int

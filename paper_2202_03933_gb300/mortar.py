@@ -19,6 +19,8 @@ from ._native import MortarError, Options, Stats, call, lib  # noqa: F401
 
 QUAD4 = 4
 TRI3 = 3
+QUAD8 = 8   # quadratic slave elements (forward path only)
+TRI6 = 6
 LM_STANDARD = 0
 LM_DUAL = 1
 D_ELEMENT = 0
@@ -90,6 +92,7 @@ class Mortar:
              ctypes.c_void_p(stream or 0))
         self.h = h
         self.Ns = self.Nm = self.Es = self.Em = 0
+        self.type_s = QUAD4
 
     def close(self):
         if getattr(self, "h", None):
@@ -112,6 +115,7 @@ class Mortar:
         self.Es, self.Em = int(kcs.shape[0]), int(kcm.shape[0])
         ts = type_s or int(kcs.shape[1])
         tm = type_m or int(kcm.shape[1])
+        self.type_s = ts
         call("mortar_set_interface", self.h, px, self.Ns, pcs, self.Es, ts, pm, self.Nm, pcm, self.Em, tm, dx)
         return self
 
@@ -129,6 +133,7 @@ class Mortar:
             mn.append(mn[-1] + itf.xm.shape[0])
             me.append(me[-1] + itf.conn_m.shape[0])
         ts, tm = interfaces[0].type_s, interfaces[0].type_m
+        self.type_s = ts
         arrs = [np.ascontiguousarray(np.concatenate(xs)), np.ascontiguousarray(np.concatenate(cs), np.int32),
                 np.ascontiguousarray(np.concatenate(xm)), np.ascontiguousarray(np.concatenate(cm), np.int32)]
         offs = [np.asarray(o, np.int64) for o in (sn, se, mn, me)]
@@ -280,8 +285,11 @@ class Mortar:
         return torch.sparse_csr_tensor(rp, ci[:nnz].to(torch.int64), va[:nnz], size=(nr, nc))
 
     def pair_blocks(self, with_D: bool = False):
+        """Per-pair blocks (n_pairs, 4, 4) -- (n_pairs, 8, 4) for quadratic slave
+        elements -- the segment-mode D blocks if with_D, and the nonempty flags."""
         n = self.stats()["n_pairs"]
-        M = np.empty((max(n, 1), 4, 4))
+        rows = 8 if getattr(self, "type_s", QUAD4) in (TRI6, QUAD8) else 4
+        M = np.empty((max(n, 1), rows, 4))
         D = np.empty((max(n, 1), 4, 4)) if with_D else None
         f = np.empty(max(n, 1), np.uint8)
         call("mortar_get_pair_blocks", self.h, M.ctypes.data_as(ctypes.c_void_p),
