@@ -171,7 +171,7 @@ def bsr_parity(G, R, tol=1e-12):
     return float(rel.max())
 
 
-def grad_sensitivity(orc, itf, lam, s, m, o, trials=2, seed=0):
+def grad_sensitivity(orc, itf, lam, s, m, o, trials=4, seed=0):
     """Per-entry rounding sensitivity of the oracle's weighted-gap gradient:
     the largest change of each entry when every input coordinate is perturbed
     by one unit in the last place (random signs), over ``trials``."""
@@ -204,7 +204,11 @@ def grad_parity(gs, gm, rs, rm, scale, sens_fn=None, tol=1e-12):
     ss, sm = sens_fn()
     ok_s = dif_s <= np.maximum(tol * scale, SENS_FACTOR * ss)
     ok_m = dif_m <= np.maximum(tol * scale, SENS_FACTOR * sm)
+    big_s, big_m = dif_s > tol * scale, dif_m > tol * scale
+    ratio = max((dif_s[big_s] / np.maximum(ss[big_s], 1e-300)).max(initial=0.0),
+                (dif_m[big_m] / np.maximum(sm[big_m], 1e-300)).max(initial=0.0))
     assert ok_s.all() and ok_m.all(), (
         f"gradient rel err {err:.3e}; beyond the oracle's sensitivity at "
-        f"{int((~ok_s).sum()) + int((~ok_m).sum())} entries")
+        f"{int((~ok_s).sum()) + int((~ok_m).sum())} entries (largest deviation / sensitivity {ratio:.1f}, "
+        f"deviations {np.concatenate([dif_s[~ok_s], dif_m[~ok_m]]) / scale} of the scale)")
     return err

@@ -254,7 +254,7 @@ def test_full_size_planar_2000_adjoint_sampled(mt, orc):
 
 
 @pytest.mark.parametrize("variant,rounds,block", [(1, 0, 64), (1, 0, 256), (0, 1, 256), (0, 4, 64), (0, 8, 128),
-                                                  (0, 16, 256)])
+                                                  (0, 16, 256), (0, 32, 64), (0, 32, 256)])
 def test_adjoint_launch_variants(mt, orc, variant, rounds, block):
     """Both adjoint schedules give the oracle's gradient (bilinear and tri3
     masters, dual segment mode, warped slave)."""
