@@ -53,8 +53,8 @@ UNIT = "pairs/s"
 # this build on planar_600x520 (same element types and density as the full
 # workload, so per-pair figures carry over); see profiles/.
 EXEC_PER_PAIR = {
-    "fused": {"flops": 9397.0, "dram_bytes": 1130.0},
-    "integrate": {"flops": 3422.6, "dram_bytes": 236.0},
+    "fused": {"flops": 9391.0, "dram_bytes": 913.0},
+    "integrate": {"flops": 3579.0, "dram_bytes": 237.0},
 }
 
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes
@@ -474,20 +474,27 @@ def run_ours(args, world, rank, local):
     try:
         if "forward" not in sections:
             raise _Skip()
+        # a context of its own, autotuned for the forward pass (the integration
+        # kernel's best launch shape differs from the fused kernel's)
+        mf = mortar.Mortar(lm=itf.lm, delta=itf.delta, stream=stream.cuda_stream)
+        mf.set_interface(xs, cs, xm, cm)
+        pick_f = mf.autotune()
+        mf.set_timing(True)
         for _ in range(3):
-            m.run_graph()
+            mf.run_graph()
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t_fi = []
         g0.record(stream)
         for _ in range(args.steps):
-            m.run_graph()
-            t_fi.append(m.stats()["ms_integrate"])
+            mf.run_graph()
+            t_fi.append(mf.stats()["ms_integrate"])
         g1.record(stream)
         torch.cuda.synchronize()
         ms_f = g0.elapsed_time(g1) / args.steps
+        mf.close()
         fwd = {"ms_per_step": round(ms_f, 4), "pairs_per_s": world * n_pairs / (ms_f / 1e3),
-               "ms_integrate": round(med(t_fi), 4)}
+               "ms_integrate": round(med(t_fi), 4), "autotune": pick_f}
         exf = EXEC_PER_PAIR["integrate"]
         if exf["flops"] and args.workload.startswith("planar_") and itf.lm == 1:
             a = exf["flops"] * n_pairs / (med(t_fi) / 1e3) / 1e12

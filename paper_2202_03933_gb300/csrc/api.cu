@@ -804,7 +804,8 @@ int mortar_set_watchdog(mortar_ctx* c, int32_t watchdog_us) {
 
 int mortar_set_launch(mortar_ctx* c, int32_t variant, int32_t block_size, int32_t chunk_pairs, int32_t rounds) {
   if (!c || variant < 0 || variant > 1 || block_size < 0 || block_size > kMaxPairBlock || (block_size % 32) != 0 ||
-      chunk_pairs < 0 || (rounds != 0 && rounds != 1 && rounds != 2 && rounds != 4 && rounds != 8 && rounds != 16))
+      chunk_pairs < 0 ||
+      (rounds != 0 && rounds != 1 && rounds != 2 && rounds != 4 && rounds != 8 && rounds != 16 && rounds != 32))
     return MORTAR_ERR_INVALID_ARG;
   c->variant = variant;
   c->block_size = block_size;
@@ -830,14 +831,14 @@ int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int3
     MORTAR_TRY(copy_in(c->lambda.p, lambda, (size_t)c->Ns * 24, on_device, c->stream));
   }
   // candidate launch shapes: the warp-batched kernels with 32 R pairs per
-  // warp batch (R = rounds 1, 2, 4, 8, 16) and 2, 4 or 8 warps per block, and
+  // warp batch (R = rounds 1, 2, 4, 8, 16, 32) and 2, 4 or 8 warps per block, and
   // the one-pair-per-thread kernels with 64, 128 or 256 threads per block and
   // 32 or 128 pairs per work-counter fetch
   struct Cand { int32_t variant, rounds, block, chunk; };
   std::vector<Cand> cands;
-  // (8 and 16 rounds only for the adjoint pair kernel: the forward-only
+  // (8 to 32 rounds only for the adjoint pair kernel: the forward-only
   // integration kernel runs at most 4, see integrate_rounds)
-  for (int32_t r : {1, 2, 4, 8, 16})
+  for (int32_t r : {1, 2, 4, 8, 16, 32})
     for (int32_t b : {64, 128, 256})
       if (ph.adjoint ? true : (r <= 4 && integrate_batched_fits(r, b))) cands.push_back({0, r, b, 0});
   for (int32_t b : {64, 128, 256})

@@ -106,6 +106,91 @@ __device__ __forceinline__ int clip_polygon(const double* __restrict__ r, const 
   return nr;
 }
 
+// Vertex count of a pair's clipped and merged polygon, computed in FP32 with
+// the steps of clip_polygon (0 when the FP32 polygon is empty).  Used only as
+// the key that groups pairs of similar cost: the FP64 clip decides what a
+// pair contributes.  Coordinates are O(element size) apart, so FP32 keeps
+// them to ~1e-4 of an element; near-degenerate pairs may get another count.
+template <int NS, int NM>
+__device__ __forceinline__ int clip_count_f32(const double* __restrict__ r, const double* __restrict__ xm,
+                                              const int32_t* __restrict__ conn_m, int32_t m) {
+  const double eps_in = r[SR_EPSIN];
+  if (!(eps_in >= 0.0)) return 0;
+  const float ein = f32_trunc(eps_in);
+  const float x0x = f32_trunc(r[SR_X0]), x0y = f32_trunc(r[SR_X0 + 1]), x0z = f32_trunc(r[SR_X0 + 2]);
+  const float t1x = f32_trunc(r[SR_T1]), t1y = f32_trunc(r[SR_T1 + 1]), t1z = f32_trunc(r[SR_T1 + 2]);
+  const float t2x = f32_trunc(r[SR_T2]), t2y = f32_trunc(r[SR_T2 + 1]), t2z = f32_trunc(r[SR_T2 + 2]);
+  constexpr int CAP = 12;
+  float Wu[CAP], Wv[CAP], Qu[CAP], Qv[CAP], d[CAP];
+  float mu[4], mv[4];
+#pragma unroll
+  for (int l = 0; l < NM; ++l) {
+    const int64_t n = conn_m[(int64_t)NM * m + l];
+    const float dx = f32_trunc(xm[3 * n]) - x0x, dy = f32_trunc(xm[3 * n + 1]) - x0y,
+                dz = f32_trunc(xm[3 * n + 2]) - x0z;
+    mu[l] = fmaf(dz, t1z, fmaf(dy, t1y, dx * t1x));
+    mv[l] = fmaf(dz, t2z, fmaf(dy, t2y, dx * t2x));
+  }
+  float ma2 = 0.0f;
+#pragma unroll
+  for (int l = 0; l < NM; ++l) {
+    const int l1 = (l + 1) % NM;
+    ma2 += mu[l] * mv[l1] - mv[l] * mu[l1];
+  }
+#pragma unroll
+  for (int l = 0; l < NM; ++l) {
+    const int src = ma2 < 0.0f ? NM - 1 - l : l;
+    Wu[l] = mu[src];
+    Wv[l] = mv[src];
+  }
+  int n = NM;
+  for (int i = 0; i < NS && n > 0; ++i) {
+    const int i1 = i + 1 == NS ? 0 : i + 1;
+    const float au = f32_trunc(r[SR_PS + 2 * i]), av = f32_trunc(r[SR_PS + 2 * i + 1]);
+    const float eu = f32_trunc(r[SR_PS + 2 * i1]) - au, ev = f32_trunc(r[SR_PS + 2 * i1 + 1]) - av;
+    for (int k = 0; k < n; ++k) d[k] = eu * (Wv[k] - av) - ev * (Wu[k] - au);
+    int o = 0;
+    for (int k = 0; k < n; ++k) {
+      const int k1 = k + 1 == n ? 0 : k + 1;
+      const float dp = d[k], dq = d[k1];
+      if ((dp > ein && dq < -ein) || (dp < -ein && dq > ein)) {
+        const float t = dp / (dp - dq);
+        if (o < CAP) { Qu[o] = fmaf(t, Wu[k1] - Wu[k], Wu[k]); Qv[o] = fmaf(t, Wv[k1] - Wv[k], Wv[k]); }
+        ++o;
+      }
+      if (dq >= -ein) {
+        if (o < CAP) { Qu[o] = Wu[k1]; Qv[o] = Wv[k1]; }
+        ++o;
+      }
+    }
+    if (o > CAP) o = CAP;
+    for (int k = 0; k < o; ++k) { Wu[k] = Qu[k]; Wv[k] = Qv[k]; }
+    n = o;
+  }
+  const float em2 = f32_trunc(r[SR_EPSM2]);
+  int nr = 0;
+  for (int k = 0; k < n; ++k) {
+    if (nr > 0) {
+      const float du = Wu[k] - Wu[nr - 1], dv = Wv[k] - Wv[nr - 1];
+      if (du * du + dv * dv < em2) continue;
+    }
+    Wu[nr] = Wu[k];
+    Wv[nr] = Wv[k];
+    ++nr;
+  }
+  while (nr > 1) {
+    const float du = Wu[nr - 1] - Wu[0], dv = Wv[nr - 1] - Wv[0];
+    if (du * du + dv * dv < em2) --nr; else break;
+  }
+  float pa2 = 0.0f;
+  for (int k = 0; k < nr; ++k) {
+    const int k1 = k + 1 == nr ? 0 : k + 1;
+    pa2 += Wu[k] * Wv[k1] - Wv[k] * Wu[k1];
+  }
+  if (nr < 3 || 0.5f * fabsf(pa2) < f32_trunc(r[SR_EPSA])) return 0;
+  return nr;
+}
+
 // Inverse of an element map in the plane for many query points: affine maps
 // by a 2x2 inverse, bilinear ones by FP32 Newton on coordinates scaled by a
 // power of two (error e0 ~ 1e-7 in xi), then one FP64 Newton step with the
@@ -144,7 +229,7 @@ struct MapInverse {
   // then one Newton-Raphson reciprocal iteration r <- r + r (1 - d r) in FP64,
   // which squares the seed's relative error (~1e-7 -> ~1e-14).
   __device__ __forceinline__ double inv_det(double det) const {
-    double id = (double)__frcp_rn((float)(det * sc2)) * sc2;
+    double id = f64_of_f32(__frcp_rn((float)(det * sc2))) * sc2;
     const double e = fma(-det, id, 1.0);
     return fma(id, e, id);
   }
@@ -166,7 +251,7 @@ struct MapInverse {
   // FP32 Newton of a bilinear map (error ~1e-7 in xi); false if it did not settle
   __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
-    const float tu = (float)(du * sc), tv = (float)(dv * sc);
+    const float tu = f32_trunc(du * sc), tv = f32_trunc(dv * sc);
     float x = b00 * tu + b01 * tv, y = b10 * tu + b11 * tv;
     bool conv = false;
 #pragma unroll 1
@@ -181,8 +266,8 @@ struct MapInverse {
       y -= d1;
       if (fabsf(d0) + fabsf(d1) <= 3e-7f) { conv = true; break; }
     }
-    xi = (double)x;
-    eta = (double)y;
+    xi = f64_of_f32(x);
+    eta = f64_of_f32(y);
     return conv;
   }
 

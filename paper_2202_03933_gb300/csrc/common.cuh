@@ -116,6 +116,32 @@ __device__ __forceinline__ int band_side(double d, long long eps_bits) {
   return b < 0 ? -1 : 1;
 }
 
+// Conversions between FP64 and FP32 by integer operations, which keeps them
+// off the FP64 pipe (a conversion instruction with an FP64 operand issues
+// there, at the FP64 rate):
+//  * f32_trunc: FP64 -> FP32 with the mantissa truncated (signed zero below
+//    the FP32 normal range, infinity above it) -- for FP32 seeds and sort keys;
+//  * f64_of_f32: FP32 -> FP64, exact for normal numbers and zero (FP32
+//    subnormals become signed zero; infinity and NaN keep their class).
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffull));
+}
+
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long e64 = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 template <int NEN>
 __device__ __forceinline__ void shape_fn(double xi, double eta, double N[4]) {
   if constexpr (NEN == 4) {

@@ -8,8 +8,8 @@
 //   q  = [segment D] x_s(xi_s) - x_m(xi_m)   (x_s, x_m: isoparametric
 //        interpolation of the ORIGINAL 3D nodes).
 // The kernel recomputes the pair's geometry (nothing is stored between the
-// forward and the adjoint) while recording the Sutherland-Hodgman stages, then
-// runs the reverse sweep:
+// forward and the adjoint) while recording the clip (every intersection vertex
+// with its two parent vertices and its clip edge), then runs the reverse sweep:
 //   quadrature point -> back-projection (implicit function theorem at the
 //   converged xi: dxi = J^-1 (dx - d map)) -> cell vertices and cell area ->
 //   centroid fan -> merge (selection) -> clipping stages (vertex copies and
@@ -445,10 +445,11 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
         if (!si.solve(xu, xv, xs1, xs2)) ctr.newton_fail++;
         if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
         const double xs12 = xs1 * xs2, xm12 = xm1 * xm2;
-        // v = CY m_m, u = CY^T m_s
+        // v = CY m_m (rows 1.. only: the derivative in xi_s needs no v_0),
+        // u = CY^T m_s, and m_s^T CY m_m = u . m_m
         double v[4], u[4];
 #pragma unroll
-        for (int i = 0; i < KS; ++i) {
+        for (int i = 1; i < KS; ++i) {
           double t = fma(CYs(i, 2), xm2, fma(CYs(i, 1), xm1, CYs(i, 0)));
           if (KM == 4) t = fma(CYs(i, 3), xm12, t);
           v[i] = t;
@@ -462,21 +463,21 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
         // g = [seg] (CX + CX^T) m_s - v;  f = [seg] m_s^T w / 2 - m_s^T v
         double g[4], f;
         {
-          double fv = fma(v[2], xs2, fma(v[1], xs1, v[0]));
-          if (KS == 4) fv = fma(v[3], xs12, fv);
+          double fv = fma(u[2], xm2, fma(u[1], xm1, u[0]));
+          if (KM == 4) fv = fma(u[3], xm12, fv);
           if (SEG) {
             double fw = 0.0;
 #pragma unroll
             for (int i = 0; i < KS; ++i) {
               double t = fma(SXs(i, 2), xs2, fma(SXs(i, 1), xs1, SXs(i, 0)));
               if (KS == 4) t = fma(SXs(i, 3), xs12, t);
-              g[i] = t - v[i];
+              if (i > 0) g[i] = t - v[i];
               fw = i == 0 ? t : fma(i == 1 ? xs1 : (i == 2 ? xs2 : xs12), t, fw);
             }
             f = fma(0.5, fw, -fv);
           } else {
 #pragma unroll
-            for (int i = 0; i < KS; ++i) g[i] = -v[i];
+            for (int i = 1; i < KS; ++i) g[i] = -v[i];
             f = -fv;
           }
         }
@@ -497,24 +498,41 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
           xmb0 = -W * u[1];
           xmb1 = -W * u[2];
         }
-        // forward accumulators (nodal shape functions, W folded into N_s)
+        // forward accumulators (nodal shape functions).  The factors 1/4 of
+        // quad4 shape functions are folded into W: with ks, km = 1/4 for a
+        // quad4 side (1 for tri3), WNs = (ks km W) N_s / ks and Nm = N_m / km,
+        // so that WNs Nm = W N_s N_m
         {
+          constexpr double km = NM == 4 ? 0.25 : 1.0;
+          constexpr double kw = km * (NS == 4 ? 0.25 : 1.0);
           double WNs[4], Nm[4];
+          const double wk = kw * W;
           if constexpr (NS == 4) {
-            const double w4 = 0.25 * W;
-            const double qa = w4 * (1.0 - xs1), qb = w4 * (1.0 + xs1), c = 1.0 - xs2, d = 1.0 + xs2;
+            const double qa = fma(-wk, xs1, wk), qb = fma(wk, xs1, wk), c = 1.0 - xs2, d = 1.0 + xs2;
             WNs[0] = qa * c; WNs[1] = qb * c; WNs[2] = qb * d; WNs[3] = qa * d;
           } else {
-            WNs[0] = W * (1.0 - xs1 - xs2); WNs[1] = W * xs1; WNs[2] = W * xs2; WNs[3] = 0.0;
+            WNs[1] = wk * xs1; WNs[2] = wk * xs2; WNs[0] = wk - WNs[1] - WNs[2]; WNs[3] = 0.0;
           }
-          shape_fn<NM>(xm1, xm2, Nm);
+          if constexpr (NM == 4) {
+            const double a = 1.0 - xm1, b = 1.0 + xm1, c = 1.0 - xm2, d = 1.0 + xm2;
+            Nm[0] = a * c; Nm[1] = b * c; Nm[2] = b * d; Nm[3] = a * d;
+          } else {
+            shape_fn<NM>(xm1, xm2, Nm);
+          }
 #pragma unroll
           for (int a = 0; a < NS; ++a)
 #pragma unroll
             for (int l = 0; l < NM; ++l) G[a][l] = fma(WNs[a], Nm[l], G[a][l]);
-          if (SEG) {
+          if (SEG) {   // H = sum W N_s N_s^T = sum WNs (N_s / km)
             double Ns[4];
-            shape_fn<NS>(xs1, xs2, Ns);
+            if constexpr (NS == 4 && NM == 4) {
+              const double a = 1.0 - xs1, b = 1.0 + xs1, c = 1.0 - xs2, d = 1.0 + xs2;
+              Ns[0] = a * c; Ns[1] = b * c; Ns[2] = b * d; Ns[3] = a * d;
+            } else {
+              shape_fn<NS>(xs1, xs2, Ns);
+              if (NM == 4)
+                for (int b = 0; b < NS; ++b) Ns[b] *= 4.0;
+            }
 #pragma unroll
             for (int a = 0; a < NS; ++a)
 #pragma unroll
@@ -638,6 +656,15 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
       double2* a2 = reinterpret_cast<double2*>(ab_out + 16 * p);
       for (int k = 0; k < 8; ++k) __stcs(a2 + k, make_double2(0.0, 0.0));
     }
+    if (FWD) {
+      double2* mo = reinterpret_cast<double2*>(fo.Mblk + 16 * p);
+      for (int k = 0; k < 8; ++k) __stcs(mo + k, make_double2(0.0, 0.0));
+      if (SEG) {
+        double2* dd = reinterpret_cast<double2*>(fo.Dblk + 16 * p);
+        for (int k = 0; k < 8; ++k) __stcs(dd + k, make_double2(0.0, 0.0));
+      }
+      __stcs(fo.flag + p, (uint8_t)0);
+    }
   }
   __stcs(J_out + p, Jp);
 }
@@ -666,9 +693,10 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
   AdjCounters ctr;
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
-  // near the end of the queue a warp takes 32 pairs at a time, so that the
-  // last batches do not leave most warps idle
-  const int64_t tail = (int64_t)B * 2 * gridDim.x * (blockDim.x >> 5);
+  // guided self-scheduling: a warp takes half an even share of the pairs
+  // left (at most B, at least 32, a multiple of 32), so batches are full
+  // while there is plenty of work and shrink towards the end of the queue
+  const int64_t share = 2 * (int64_t)gridDim.x * (blockDim.x >> 5);
   const Watchdog wd(watchdog_us);
   for (;;) {   // bounded: the shared counter only grows
     if (wd.expired(&st->timeout)) break;
@@ -676,7 +704,8 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
     int fetch = B;
     if (lane == 0) {
       const unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(&st->work_ctr2);
-      if ((int64_t)seen + tail > n) fetch = 32;
+      const int64_t f = (n - (int64_t)seen) / share;
+      fetch = f >= B ? B : (f < 32 ? 32 : (int)(f & ~31ll));
       base = (int64_t)atomicAdd(&st->work_ctr2, (unsigned long long)fetch);
     }
     base = __shfl_sync(0xffffffffu, base, 0);
@@ -684,48 +713,24 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
     if (base >= n) break;
     const int64_t lim = min(n, base + (int64_t)fetch);
     const int rounds = (fetch + 31) >> 5;
-    // phase A: cell count of each pair (clip without recording); empty pairs done here
+    // phase A: sort key of each pair from an FP32 clip (its cell count; 1 =
+    // empty in FP32, 0 = no pair).  Every pair goes through phase B, where
+    // the FP64 clip decides what it contributes.
 #pragma unroll 1
     for (int rr = 0; rr < rounds; ++rr) {
       const int64_t p = base + rr * 32 + lane;
-      int nr = 0;
+      int key = 0;
       if (p < lim) {
-        const double* r = srec + (int64_t)SR_STRIDE * ps[p];
-        PlaneMap mm;
-        double Pu[kPolyS], Pv[kPolyS];
-        unsigned long long dummy = 0;
-        nr = clip_polygon<NS, NM, kPolyS>(r, xm, conn_m, pm[p], mm, Pu, Pv, dummy);
-        if (nr == 0) {
-          double2* g1 = reinterpret_cast<double2*>(gs_out + 12 * p);
-          double2* g2 = reinterpret_cast<double2*>(gm_out + 12 * p);
-#pragma unroll
-          for (int k = 0; k < 6; ++k) { __stcs(g1 + k, make_double2(0.0, 0.0)); __stcs(g2 + k, make_double2(0.0, 0.0)); }
-          if (DUAL) {
-            double2* a2 = reinterpret_cast<double2*>(ab_out + 16 * p);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) __stcs(a2 + k, make_double2(0.0, 0.0));
-          }
-          __stcs(J_out + p, 0.0);
-          if (FWD) {
-            double2* mo = reinterpret_cast<double2*>(fo.Mblk + 16 * p);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) __stcs(mo + k, make_double2(0.0, 0.0));
-            if (SEG) {
-              double2* dd = reinterpret_cast<double2*>(fo.Dblk + 16 * p);
-#pragma unroll
-              for (int k = 0; k < 8; ++k) __stcs(dd + k, make_double2(0.0, 0.0));
-            }
-            __stcs(fo.flag + p, (uint8_t)0);
-          }
-        }
+        const int nr = clip_count_f32<NS, NM>(srec + (int64_t)SR_STRIDE * ps[p], xm, conn_m, pm[p]);
+        key = 1 + (nr == 0 ? 0 : (nr == 3 ? 1 : min(nr, kPolyS)));
       }
-      keys[rr * 32 + lane] = (uint8_t)(nr == 0 ? 0 : (nr == 3 ? 1 : nr));
+      keys[rr * 32 + lane] = (uint8_t)key;
     }
     __syncwarp();
     // counting sort of the batch by cell count, descending (ballots per value)
     int basecnt = 0;
 #pragma unroll 1
-    for (int v = kPolyS; v >= 1; --v) {
+    for (int v = kPolyS + 1; v >= 1; --v) {
       int before = 0;
 #pragma unroll 1
       for (int rr = 0; rr < rounds; ++rr) {
@@ -739,7 +744,7 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
     }
     const int n_live = basecnt;
     __syncwarp();
-    // phase B: full adjoint of each non-empty pair, rounds of similar cell counts
+    // phase B: full adjoint of each pair, rounds of similar cell counts
     for (int i0 = 0; i0 < n_live; i0 += 32) {
       const int i = i0 + lane;
       if (i < n_live)
@@ -1092,7 +1097,8 @@ void launch_batched_f(mortar_ctx* c, int rounds) {
   else if (rounds == 2) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 2>);
   else if (rounds == 4) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 4>);
   else if (rounds == 8) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 8>);
-  else go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 16>);
+  else if (rounds == 16) go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 16>);
+  else go(k_adjoint_batched<NS, NM, SEG, DUAL, FWD, 32>);
 }
 
 // The warp-batched adjoint always produces the forward blocks as well (the

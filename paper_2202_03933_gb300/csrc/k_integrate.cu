@@ -245,15 +245,17 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_integrate_batched(
   const int64_t n = ok ? (int64_t)min((unsigned long long)pair_cap, st->n_pairs) : 0;
   const unsigned lt_mask = (1u << lane) - 1u;
   const Watchdog wd(rp.watchdog_us);
-  // near the end of the queue a warp takes 32 pairs at a time
-  const int64_t tail = (int64_t)B * 2 * gridDim.x * (blockDim.x >> 5);
+  // guided self-scheduling: a warp takes half an even share of the pairs
+  // left (at most B, at least 32, a multiple of 32)
+  const int64_t share = 2 * (int64_t)gridDim.x * (blockDim.x >> 5);
   for (;;) {   // bounded: the shared counter only grows
     if (wd.expired(&st->timeout)) break;
     int64_t base = 0;
     int fetch = B;
     if (lane == 0) {
       const unsigned long long seen = *reinterpret_cast<volatile unsigned long long*>(&st->work_ctr);
-      if ((int64_t)seen + tail > n) fetch = 32;
+      const int64_t f = (n - (int64_t)seen) / share;
+      fetch = f >= B ? B : (f < 32 ? 32 : (int)(f & ~31ll));
       base = (int64_t)atomicAdd(&st->work_ctr, (unsigned long long)fetch);
     }
     base = __shfl_sync(0xffffffffu, base, 0);
