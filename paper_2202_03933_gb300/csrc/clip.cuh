@@ -107,13 +107,15 @@ __device__ __forceinline__ int clip_polygon(const double* __restrict__ r, const 
 }
 
 // Vertex count of a pair's clipped and merged polygon, computed in FP32 with
-// the steps of clip_polygon (0 when the FP32 polygon is empty).  Used only as
-// the key that groups pairs of similar cost: the FP64 clip decides what a
-// pair contributes.  Coordinates are O(element size) apart, so FP32 keeps
-// them to ~1e-4 of an element; near-degenerate pairs may get another count.
+// the steps of clip_polygon (0 when the FP32 polygon is empty), and the number
+// of edge intersections the clip created (n_int).  Used only as the key that
+// groups pairs of similar cost: the FP64 clip decides what a pair contributes.
+// Coordinates are O(element size) apart, so FP32 keeps them to ~1e-4 of an
+// element; near-degenerate pairs may get other counts.
 template <int NS, int NM>
 __device__ __forceinline__ int clip_count_f32(const double* __restrict__ r, const double* __restrict__ xm,
-                                              const int32_t* __restrict__ conn_m, int32_t m) {
+                                              const int32_t* __restrict__ conn_m, int32_t m, int& n_int) {
+  n_int = 0;
   const double eps_in = r[SR_EPSIN];
   if (!(eps_in >= 0.0)) return 0;
   const float ein = f32_trunc(eps_in);
@@ -157,6 +159,7 @@ __device__ __forceinline__ int clip_count_f32(const double* __restrict__ r, cons
         const float t = dp / (dp - dq);
         if (o < CAP) { Qu[o] = fmaf(t, Wu[k1] - Wu[k], Wu[k]); Qv[o] = fmaf(t, Wv[k1] - Wv[k], Wv[k]); }
         ++o;
+        ++n_int;
       }
       if (dq >= -ein) {
         if (o < CAP) { Qu[o] = Wu[k1]; Qv[o] = Wv[k1]; }

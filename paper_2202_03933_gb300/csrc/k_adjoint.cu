@@ -685,9 +685,11 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
   using PermT = typename std::conditional<(B > 256), uint16_t, uint8_t>::type;
   __shared__ PermT perm_s[kMaxPairBlock / 32][B];
   __shared__ uint8_t key_s[kMaxPairBlock / 32][B];
+  __shared__ unsigned pres_s[kMaxPairBlock / 32][8];   // key values present in the batch (256 bits)
   extern __shared__ double adj_coef[];   // kAdjCoef doubles per thread, interleaved
   PermT* perm = perm_s[threadIdx.x >> 5];
   uint8_t* keys = key_s[threadIdx.x >> 5];
+  unsigned* pres = pres_s[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   AdjCounters ctr;
@@ -713,38 +715,51 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
     if (base >= n) break;
     const int64_t lim = min(n, base + (int64_t)fetch);
     const int rounds = (fetch + 31) >> 5;
-    // phase A: sort key of each pair from an FP32 clip (its cell count; 1 =
-    // empty in FP32, 0 = no pair).  Every pair goes through phase B, where
-    // the FP64 clip decides what it contributes.
+    // phase A: sort key of each pair from an FP32 clip: 1 + 16 x its cell
+    // count + its edge intersections (cells 0 = empty in FP32; key 0 = no
+    // pair).  The cell count sets the quadrature work, the intersections the
+    // divergent clip and reverse-clip work.  Every pair goes through phase B,
+    // where the FP64 clip decides what it contributes.
+    if (lane < 8) pres[lane] = 0u;
+    __syncwarp();
 #pragma unroll 1
     for (int rr = 0; rr < rounds; ++rr) {
       const int64_t p = base + rr * 32 + lane;
       int key = 0;
       if (p < lim) {
-        const int nr = clip_count_f32<NS, NM>(srec + (int64_t)SR_STRIDE * ps[p], xm, conn_m, pm[p]);
-        key = 1 + (nr == 0 ? 0 : (nr == 3 ? 1 : min(nr, kPolyS)));
+        int n_int = 0;
+        const int nr = clip_count_f32<NS, NM>(srec + (int64_t)SR_STRIDE * ps[p], xm, conn_m, pm[p], n_int);
+        key = 1 + 16 * (nr == 0 ? 0 : (nr == 3 ? 1 : min(nr, kPolyS))) + min(n_int, 15);
+        atomicOr(&pres[key >> 5], 1u << (key & 31));
       }
       keys[rr * 32 + lane] = (uint8_t)key;
     }
     __syncwarp();
-    // counting sort of the batch by cell count, descending (ballots per value)
+    // counting sort of the batch by key, descending, over the key values
+    // present (ballots per value)
     int basecnt = 0;
 #pragma unroll 1
-    for (int v = kPolyS + 1; v >= 1; --v) {
-      int before = 0;
+    for (int w = 7; w >= 0; --w) {
+      unsigned bits = pres[w];
+      while (bits != 0u) {   // uniform across the warp
+        const int b = 31 - __clz(bits);
+        bits &= ~(1u << b);
+        const int v = 32 * w + b;
+        int before = 0;
 #pragma unroll 1
-      for (int rr = 0; rr < rounds; ++rr) {
-        const int slot = rr * 32 + lane;
-        const bool hit = keys[slot] == v;
-        const unsigned mk = __ballot_sync(0xffffffffu, hit);
-        if (hit) perm[basecnt + before + __popc(mk & lt_mask)] = (PermT)slot;
-        before += __popc(mk);
+        for (int rr = 0; rr < rounds; ++rr) {
+          const int slot = rr * 32 + lane;
+          const bool hit = keys[slot] == v;
+          const unsigned mk = __ballot_sync(0xffffffffu, hit);
+          if (hit) perm[basecnt + before + __popc(mk & lt_mask)] = (PermT)slot;
+          before += __popc(mk);
+        }
+        basecnt += before;
       }
-      basecnt += before;
     }
     const int n_live = basecnt;
     __syncwarp();
-    // phase B: full adjoint of each pair, rounds of similar cell counts
+    // phase B: full adjoint of each pair, rounds of similar cost
     for (int i0 = 0; i0 < n_live; i0 += 32) {
       const int i = i0 + lane;
       if (i < n_live)

@@ -48,6 +48,7 @@ struct TanArgs {
   const double* ym;
   double* Kp;          // per pair 288: [a][c][k][d], k < 4 slave node, k >= 4 master node k - 4
   double* Op;          // per pair 12: O_e,c (dual LMs)
+  const uint8_t* flag; // per pair: non-empty in the forward run (FP64 clip)
   int64_t pair_cap;
   DevStatus* st;
   int32_t watchdog_us;
@@ -356,7 +357,9 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_pairs(TanArgs g) {
   extern __shared__ double tan_acc[];
   constexpr int B = 32 * R;
   __shared__ uint8_t perm_s[kTanWarps][B];
+  __shared__ unsigned pres_s[kTanWarps][8];   // key values present in the batch (256 bits)
   uint8_t* perm = perm_s[threadIdx.x >> 5];
+  unsigned* pres = pres_s[threadIdx.x >> 5];
   double* acc = tan_acc + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -374,32 +377,45 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_pairs(TanArgs g) {
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= items) break;
     const int64_t base = item * B;
+    // sort key: 0 for pairs the forward run found empty (their blocks are
+    // never read), else 1 + 16 x the cell count + the edge intersections of
+    // an FP32 clip (a cost estimate only; the FP64 clip of the pair kernel
+    // decides)
+    if (lane < 8) pres[lane] = 0u;
+    __syncwarp();
     int key[R];
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
       const int64_t p = base + rr * 32 + lane;
-      int nr = 0;
-      if (p < n) {
-        const double* r = g.srec + (int64_t)SR_STRIDE * g.ps[p];
-        PlaneMap mm;
-        double Pu[kPolyS], Pv[kPolyS];
-        unsigned long long dummy = 0;
-        nr = clip_polygon<NS, NM, kPolyS>(r, g.xm, g.conn_m, g.pm[p], mm, Pu, Pv, dummy);
+      int k = 0;
+      if (p < n && g.flag[p]) {
+        int n_int = 0;
+        const int nr = clip_count_f32<NS, NM>(g.srec + (int64_t)SR_STRIDE * g.ps[p], g.xm, g.conn_m, g.pm[p],
+                                              n_int);
+        k = 1 + 16 * (nr == 0 ? 0 : (nr == 3 ? 1 : min(nr, kPolyS))) + min(n_int, 15);
+        atomicOr(&pres[k >> 5], 1u << (k & 31));
       }
-      key[rr] = nr == 0 ? 0 : (nr == 3 ? 1 : nr);
+      key[rr] = k;
     }
+    __syncwarp();
     int pos[R];
     int basecnt = 0;
 #pragma unroll 1
-    for (int v = kPolyS; v >= 1; --v) {
-      int before = 0;
+    for (int w = 7; w >= 0; --w) {
+      unsigned bits = pres[w];
+      while (bits != 0u) {   // uniform across the warp
+        const int b = 31 - __clz(bits);
+        bits &= ~(1u << b);
+        const int v = 32 * w + b;
+        int before = 0;
 #pragma unroll
-      for (int rr = 0; rr < R; ++rr) {
-        const unsigned mk = __ballot_sync(0xffffffffu, key[rr] == v);
-        if (key[rr] == v) pos[rr] = basecnt + before + __popc(mk & lt_mask);
-        before += __popc(mk);
+        for (int rr = 0; rr < R; ++rr) {
+          const unsigned mk = __ballot_sync(0xffffffffu, key[rr] == v);
+          if (key[rr] == v) pos[rr] = basecnt + before + __popc(mk & lt_mask);
+          before += __popc(mk);
+        }
+        basecnt += before;
       }
-      basecnt += before;
     }
     const int n_live = basecnt;
 #pragma unroll
@@ -810,8 +826,8 @@ template <int NS, int NM, bool SEG, bool DUAL>
 void launch_pairs_t(mortar_ctx* c) {
   TanArgs g{c->pairs_s.as<int32_t>(), c->pairs_m.as<int32_t>(), c->srec.as<double>(), c->xs.as<double>(),
             c->xm.as<double>(), c->conn_s.as<int32_t>(), c->conn_m.as<int32_t>(), c->tan_ys.as<double>(),
-            c->tan_ym.as<double>(), c->tan_Kp.as<double>(), c->tan_Op.as<double>(), c->tan_pair_cap,
-            c->dstat.as<DevStatus>(), c->watchdog_us};
+            c->tan_ym.as<double>(), c->tan_Kp.as<double>(), c->tan_Op.as<double>(), c->flag.as<uint8_t>(),
+            c->tan_pair_cap, c->dstat.as<DevStatus>(), c->watchdog_us};
   // batches of 160 pairs: 16 full rounds of 10 pair groups (lanes 30, 31 idle)
   auto kern = k_tangent_pairs<NS, NM, SEG, DUAL, 5>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTanSmem);
