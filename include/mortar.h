@@ -303,10 +303,8 @@ int mortar_set_watchdog(mortar_ctx* ctx, int32_t watchdog_us);
 
 /* Launch shape of the pair kernels (used by the autotuner; 0 = default):
  * variant 0 = integration and adjoint in warp batches of up to 32 * rounds
- * pairs sorted by cell count (rounds 1, 2, 4, 8, 16 or 32; the forward-only
- * integration kernel, which keeps a batch's polygons in shared memory, uses
- * at most 4, and fewer where a 256-thread block would not fit), variant 1 =
- * one pair per thread; block_size = threads per block of either variant (a
+ * pairs sorted by their clip's cell count and edge intersections (rounds 1,
+ * 2, 4, 8, 16 or 32), variant 1 = one pair per thread; block_size = threads per block of either variant (a
  * multiple of 32 up to 256; default 128); chunk_pairs = pairs per
  * work-counter fetch of variant 1 (default 32).  MORTAR_ERR_INVALID_ARG for
  * other values. */
@@ -354,7 +352,7 @@ int mortar_integrate_pairs_static(const mortar_options* o, void* stream,
 /* Autotuner (the batched persistent schedule of many uneven interfaces picks
  * its launch shape on the workload itself): runs the context's workload three
  * times per candidate shape -- warp batches of 32 to 1024 pairs (rounds 1, 2,
- * 4, 8, 16, 32; 8 to 32 only with lambda, i.e. for the adjoint kernel) with 64,
+ * 4, 8, 16, 32) with 64,
  * 128 or 256 threads per block, and one pair per thread with 64, 128 or 256
  * threads per block and 32 or 128 pairs per work fetch --
  * times the pair kernels (integration, plus the adjoint's per-pair kernel when

@@ -836,11 +836,9 @@ int mortar_autotune(mortar_ctx* c, const double* lambda, int32_t on_device, int3
   // 32 or 128 pairs per work-counter fetch
   struct Cand { int32_t variant, rounds, block, chunk; };
   std::vector<Cand> cands;
-  // (8 to 32 rounds only for the adjoint pair kernel: the forward-only
-  // integration kernel runs at most 4, see integrate_rounds)
   for (int32_t r : {1, 2, 4, 8, 16, 32})
     for (int32_t b : {64, 128, 256})
-      if (ph.adjoint ? true : (r <= 4 && integrate_batched_fits(r, b))) cands.push_back({0, r, b, 0});
+      if (integrate_batched_fits(r, b)) cands.push_back({0, r, b, 0});
   for (int32_t b : {64, 128, 256})
     for (int32_t k : {32, 128}) cands.push_back({1, 0, b, k});
   const bool timing = c->timing;

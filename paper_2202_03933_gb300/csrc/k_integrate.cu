@@ -15,11 +15,12 @@
 // costs the same with 1 or 32 active lanes, so the kernels are written to
 // issue few FP64 instructions with full warps:
 //
-//  * variant 0 (default): each warp takes a batch of 32 R consecutive pairs.
-//    Phase A clips one pair per lane and leaves the merged polygon and the
-//    master map in shared memory; the warp then sorts its pairs by cell count
-//    (ballot counting sort) and phase B integrates them in rounds of 32 lanes
-//    with (nearly) equal cell counts.  Affine element maps are inverted with
+//  * variant 0 (default): each warp takes a batch of up to 32 R pairs
+//    (guided self-scheduling).  Phase A clips one pair per lane in FP32 for
+//    a sort key (cell count and edge intersections); the warp sorts its
+//    pairs by key (ballot counting sort) and phase B clips in FP64 and
+//    integrates them in rounds of 32 lanes of similar cost.  Affine element
+//    maps are inverted with
 //    one precomputed 2x2 inverse; bilinear ones by Newton in FP32 on
 //    power-of-two-scaled coordinates, then one FP64 Newton step with an
 //    FP64 residual (the converged xi agrees with a full FP64 Newton to
@@ -29,6 +30,8 @@
 //
 // Both are persistent grids taking work from a global counter; the loops are
 // bounded by the pair count.
+#include <type_traits>
+
 #include "clip.cuh"
 #include "context.h"
 
@@ -207,16 +210,119 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_integrate(const int32_t* __re
 }
 
 // ---------------------------------------------------------------- variant 0
+// Shared memory of a warp: the sort keys of its batch, the sorted order and
+// the set of key values present.
 template <int R>
-struct BatchSmem {   // per-warp shared layout for 32 R pairs
+struct BatchSmem {
   static constexpr int B = 32 * R;
-  static constexpr int kPu = 0;
-  static constexpr int kPv = kPu + B * kPolyS;
-  static constexpr int kCen = kPv + B * kPolyS;
-  static constexpr int kMap = kCen + B * 2;
-  static constexpr int kDoubles = kMap + B * 8;
-  static constexpr int kBytes = kDoubles * 8 + B * 4 * 2 + B * 2;   // + pidx, sidx (int32), nr/perm (int8)
+  using PermT = typename std::conditional<(B > 256), uint16_t, uint8_t>::type;
+  static constexpr int kBytes = B * (1 + (int)sizeof(PermT)) + 8 * 4;
 };
+
+// One pair of a sorted round: FP64 clip, then the 7-point rule on the
+// centroid fan with the map inversions of MapInverse.
+template <int NS, int NM, bool SEG>
+__device__ __forceinline__ void integrate_pair_sorted(int64_t p, const int32_t* __restrict__ ps,
+                                                      const int32_t* __restrict__ pm,
+                                                      const double* __restrict__ srec, const double* __restrict__ xm,
+                                                      const int32_t* __restrict__ conn_m, const RunParams& rp,
+                                                      double* __restrict__ Mblk, double* __restrict__ Dblk,
+                                                      uint8_t* __restrict__ flag, PairCounters& ctr) {
+  const double* r = srec + (int64_t)SR_STRIDE * ps[p];
+  PlaneMap mmap;
+  double pu[kPolyS], pv[kPolyS];
+  const int nr = clip_polygon<NS, NM, kPolyS>(r, xm, conn_m, pm[p], mmap, pu, pv, ctr.clip_over);
+  if (nr == 0) {
+    write_zero_blocks(p, SEG, Mblk, Dblk);
+    flag[p] = 0;
+    return;
+  }
+  MapInverse mi;
+  mi.setup(mmap, NM == 3 || map_is_affine(mmap));
+  MapInverse si;
+  {
+    PlaneMap smap;
+    smap.c0u = r[SR_C + 0]; smap.c0v = r[SR_C + 1]; smap.c1u = r[SR_C + 2]; smap.c1v = r[SR_C + 3];
+    smap.c2u = r[SR_C + 4]; smap.c2v = r[SR_C + 5]; smap.c3u = r[SR_C + 6]; smap.c3v = r[SR_C + 7];
+    if (r[SR_AFF] != 0.0) {
+      si.m = smap;
+      si.affine = true;
+      si.i00 = r[SR_BINV]; si.i01 = r[SR_BINV + 1]; si.i10 = r[SR_BINV + 2]; si.i11 = r[SR_BINV + 3];
+    } else {
+      si.setup(smap, false);
+    }
+  }
+  double G[4][4], H[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { G[a][b] = 0.0; H[a][b] = 0.0; }
+  const int ncell = nr == 3 ? 1 : nr;
+  double cu = pu[0], cv = pv[0];
+  if (nr > 3) {
+    double su = 0.0, sv = 0.0;
+    for (int k = 0; k < nr; ++k) { su += pu[k]; sv += pv[k]; }
+    cu = su / (double)nr;
+    cv = sv / (double)nr;
+  }
+  ctr.cells += ncell;
+  ctr.nonempty++;
+  // the quad4 factors 1/4 of both sides are folded into the weight
+  constexpr double km = NM == 4 ? 0.25 : 1.0;
+  constexpr double kw = km * (NS == 4 ? 0.25 : 1.0);
+  for (int cI = 0; cI < ncell; ++cI) {
+    const int ib = nr == 3 ? 1 : cI;
+    const int iw = nr == 3 ? 2 : (cI + 1 == nr ? 0 : cI + 1);
+    const double e1u = pu[ib] - cu, e1v = pv[ib] - cv, e2u = pu[iw] - cu, e2v = pv[iw] - cv;
+    const double area = 0.5 * fabs(cross2(e1u, e1v, e2u, e2v));
+#pragma unroll 1
+    for (int q = 0; q < 7; ++q) {
+      double l1, l2, w;
+      tri7_point(q, l1, l2, w);
+      const double xu = cu + l1 * e1u + l2 * e2u;
+      const double xv = cv + l1 * e1v + l2 * e2v;
+      double xs1, xs2, xm1, xm2;
+      if (!si.solve(xu, xv, xs1, xs2)) ctr.newton_fail++;
+      if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
+      const double wk = kw * (w * area);
+      double Ns[4], Nm[4];   // Ns = (kw W) N_s / ks, Nm = N_m / km
+      if constexpr (NS == 4) {
+        const double qa = fma(-wk, xs1, wk), qb = fma(wk, xs1, wk), c = 1.0 - xs2, dd = 1.0 + xs2;
+        Ns[0] = qa * c; Ns[1] = qb * c; Ns[2] = qb * dd; Ns[3] = qa * dd;
+      } else {
+        Ns[1] = wk * xs1; Ns[2] = wk * xs2; Ns[0] = wk - Ns[1] - Ns[2]; Ns[3] = 0.0;
+      }
+      if constexpr (NM == 4) {
+        const double a = 1.0 - xm1, b = 1.0 + xm1, c = 1.0 - xm2, d = 1.0 + xm2;
+        Nm[0] = a * c; Nm[1] = b * c; Nm[2] = b * d; Nm[3] = a * d;
+      } else {
+        shape_fn<NM>(xm1, xm2, Nm);
+      }
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+#pragma unroll
+        for (int l = 0; l < NM; ++l) G[a][l] = fma(Ns[a], Nm[l], G[a][l]);
+      if (SEG) {   // H = sum W N_s N_s^T = sum Ns (N_s / km)
+        double Nu[4];
+        if constexpr (NS == 4 && NM == 4) {
+          const double a = 1.0 - xs1, b = 1.0 + xs1, c = 1.0 - xs2, d = 1.0 + xs2;
+          Nu[0] = a * c; Nu[1] = b * c; Nu[2] = b * d; Nu[3] = a * d;
+        } else {
+          shape_fn<NS>(xs1, xs2, Nu);
+          if (NM == 4)
+            for (int b = 0; b < NS; ++b) Nu[b] *= 4.0;
+        }
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+          for (int b = 0; b < NS; ++b) H[a][b] = fma(Ns[a], Nu[b], H[a][b]);
+      }
+      ctr.gp++;
+    }
+  }
+  write_blocks<NS, NM, SEG>(p, r, G, H, rp.lm == 1, Mblk, Dblk);
+  flag[p] = 1;
+}
 
 template <int NS, int NM, bool SEG, int R>
 __global__ void __launch_bounds__(kMaxPairBlock) k_integrate_batched(
@@ -226,19 +332,14 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_integrate_batched(
     unsigned long long* cta_t) {
   cta_mark(cta_t, 0);
   using L = BatchSmem<R>;
+  using PermT = typename L::PermT;
   constexpr int B = L::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* my = smem_raw + (size_t)warp * L::kBytes;
-  double* sd = reinterpret_cast<double*>(my);
-  double* Pu = sd + L::kPu;
-  double* Pv = sd + L::kPv;
-  double* Cen = sd + L::kCen;
-  double* Map = sd + L::kMap;
-  int32_t* pidx = reinterpret_cast<int32_t*>(sd + L::kDoubles);
-  int32_t* sidx = pidx + B;
-  int8_t* nrs = reinterpret_cast<int8_t*>(sidx + B);
-  uint8_t* perm = reinterpret_cast<uint8_t*>(nrs + B);
+  unsigned* pres = reinterpret_cast<unsigned*>(my);
+  PermT* perm = reinterpret_cast<PermT*>(my + 32);
+  uint8_t* keys = reinterpret_cast<uint8_t*>(perm + B);
 
   PairCounters ctr;
   const bool ok = st->over_pairs == 0 && st->over_bins == 0;
@@ -262,139 +363,53 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_integrate_batched(
     fetch = __shfl_sync(0xffffffffu, fetch, 0);
     if (base >= n) break;
     const int64_t lim = min(n, base + (int64_t)fetch);
-    // ---- phase A: clip one pair per lane, results to shared memory
-    int key[R];
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      const int slot = rr * 32 + lane;
-      const int64_t p = base + slot;
-      int nr = 0;
+    const int rounds = (fetch + 31) >> 5;
+    // ---- phase A: sort key of each pair from an FP32 clip: 1 + 16 x its
+    //      cell count + its edge intersections (0 = no pair); a cost
+    //      estimate only, the FP64 clip of phase B decides
+    if (lane < 8) pres[lane] = 0u;
+    __syncwarp();
+#pragma unroll 1
+    for (int rr = 0; rr < rounds; ++rr) {
+      const int64_t p = base + rr * 32 + lane;
+      int key = 0;
       if (p < lim) {
-        const int32_t s = ps[p];
-        const double* r = srec + (int64_t)SR_STRIDE * s;
-        PlaneMap mm;
-        nr = clip_polygon<NS, NM, kPolyS>(r, xm, conn_m, pm[p], mm, Pu + slot * kPolyS, Pv + slot * kPolyS,
-                                          ctr.clip_over);
-        if (nr == 0) {
-          write_zero_blocks(p, SEG, Mblk, Dblk);
-          flag[p] = 0;
-        } else {
-          double* mp = Map + slot * 8;
-          mp[0] = mm.c0u; mp[1] = mm.c0v; mp[2] = mm.c1u; mp[3] = mm.c1v;
-          mp[4] = mm.c2u; mp[5] = mm.c2v; mp[6] = mm.c3u; mp[7] = mm.c3v;
-          if (nr > 3) {
-            double su = 0.0, sv = 0.0;
-            for (int k = 0; k < nr; ++k) { su += Pu[slot * kPolyS + k]; sv += Pv[slot * kPolyS + k]; }
-            Cen[2 * slot] = su / (double)nr;
-            Cen[2 * slot + 1] = sv / (double)nr;
-          }
-          pidx[slot] = (int32_t)p;
-          sidx[slot] = s;
-        }
+        int n_int = 0;
+        const int nr = clip_count_f32<NS, NM>(srec + (int64_t)SR_STRIDE * ps[p], xm, conn_m, pm[p], n_int);
+        key = 1 + 16 * (nr == 0 ? 0 : (nr == 3 ? 1 : min(nr, kPolyS))) + min(n_int, 15);
+        atomicOr(&pres[key >> 5], 1u << (key & 31));
       }
-      nrs[slot] = (int8_t)nr;
-      key[rr] = nr == 0 ? 0 : (nr == 3 ? 1 : nr);   // cells of the pair
+      keys[rr * 32 + lane] = (uint8_t)key;
     }
-    // ---- sort slots by cell count, descending (ballot counting sort)
-    int pos[R];
+    __syncwarp();
+    // ---- sort by key, descending, over the key values present (ballots)
     int basecnt = 0;
 #pragma unroll 1
-    for (int v = kPolyS; v >= 1; --v) {
-      int before = 0;
-#pragma unroll
-      for (int rr = 0; rr < R; ++rr) {
-        const unsigned mk = __ballot_sync(0xffffffffu, key[rr] == v);
-        if (key[rr] == v) pos[rr] = basecnt + before + __popc(mk & lt_mask);
-        before += __popc(mk);
+    for (int w = 7; w >= 0; --w) {
+      unsigned bits = pres[w];
+      while (bits != 0u) {   // uniform across the warp
+        const int b = 31 - __clz(bits);
+        bits &= ~(1u << b);
+        const int v = 32 * w + b;
+        int before = 0;
+#pragma unroll 1
+        for (int rr = 0; rr < rounds; ++rr) {
+          const int slot = rr * 32 + lane;
+          const bool hit = keys[slot] == v;
+          const unsigned mk = __ballot_sync(0xffffffffu, hit);
+          if (hit) perm[basecnt + before + __popc(mk & lt_mask)] = (PermT)slot;
+          before += __popc(mk);
+        }
+        basecnt += before;
       }
-      basecnt += before;
     }
     const int n_live = basecnt;
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr)
-      if (key[rr] > 0) perm[pos[rr]] = (uint8_t)(rr * 32 + lane);
     __syncwarp();
-    // ---- phase B: integrate, one pair per lane, rounds of similar cell counts
+    // ---- phase B: one pair per lane, rounds of similar cost
     for (int i0 = 0; i0 < n_live; i0 += 32) {
       const int i = i0 + lane;
-      if (i >= n_live) continue;
-      const int slot = perm[i];
-      const int nr = nrs[slot];
-      const int64_t p = pidx[slot];
-      const double* r = srec + (int64_t)SR_STRIDE * sidx[slot];
-      const double* mp = Map + slot * 8;
-      PlaneMap mmap;
-      mmap.c0u = mp[0]; mmap.c0v = mp[1]; mmap.c1u = mp[2]; mmap.c1v = mp[3];
-      mmap.c2u = mp[4]; mmap.c2v = mp[5]; mmap.c3u = mp[6]; mmap.c3v = mp[7];
-      MapInverse mi;
-      mi.setup(mmap, NM == 3 || map_is_affine(mmap));
-      MapInverse si;
-      {
-        PlaneMap smap;
-        smap.c0u = r[SR_C + 0]; smap.c0v = r[SR_C + 1]; smap.c1u = r[SR_C + 2]; smap.c1v = r[SR_C + 3];
-        smap.c2u = r[SR_C + 4]; smap.c2v = r[SR_C + 5]; smap.c3u = r[SR_C + 6]; smap.c3v = r[SR_C + 7];
-        if (r[SR_AFF] != 0.0) {
-          si.m = smap;
-          si.affine = true;
-          si.i00 = r[SR_BINV]; si.i01 = r[SR_BINV + 1]; si.i10 = r[SR_BINV + 2]; si.i11 = r[SR_BINV + 3];
-        } else {
-          si.setup(smap, false);
-        }
-      }
-      double G[4][4], H[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) { G[a][b] = 0.0; H[a][b] = 0.0; }
-      const double* pu = Pu + slot * kPolyS;
-      const double* pv = Pv + slot * kPolyS;
-      const int ncell = nr == 3 ? 1 : nr;
-      const double cu = nr == 3 ? pu[0] : Cen[2 * slot], cv = nr == 3 ? pv[0] : Cen[2 * slot + 1];
-      ctr.cells += ncell;
-      ctr.nonempty++;
-      for (int cI = 0; cI < ncell; ++cI) {
-        const int ib = nr == 3 ? 1 : cI;
-        const int iw = nr == 3 ? 2 : (cI + 1 == nr ? 0 : cI + 1);
-        const double au = cu, av = cv;
-        const double e1u = pu[ib] - au, e1v = pv[ib] - av, e2u = pu[iw] - au, e2v = pv[iw] - av;
-        const double area = 0.5 * fabs(cross2(e1u, e1v, e2u, e2v));
-#pragma unroll 1
-        for (int q = 0; q < 7; ++q) {
-          double l1, l2, w;
-          tri7_point(q, l1, l2, w);
-          const double xu = au + l1 * e1u + l2 * e2u;
-          const double xv = av + l1 * e1v + l2 * e2v;
-          double xs1, xs2, xm1, xm2;
-          if (!si.solve(xu, xv, xs1, xs2)) ctr.newton_fail++;
-          if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
-          const double w4 = 0.25 * (w * area);
-          double Ns[4], Nm[4];
-          if constexpr (NS == 4) {   // W * N_s
-            const double qa = w4 * (1.0 - xs1), qb = w4 * (1.0 + xs1), c = 1.0 - xs2, dd = 1.0 + xs2;
-            Ns[0] = qa * c; Ns[1] = qb * c; Ns[2] = qb * dd; Ns[3] = qa * dd;
-          } else {
-            const double W = 4.0 * w4;
-            Ns[0] = W * (1.0 - xs1 - xs2); Ns[1] = W * xs1; Ns[2] = W * xs2; Ns[3] = 0.0;
-          }
-          shape_fn<NM>(xm1, xm2, Nm);
-#pragma unroll
-          for (int a = 0; a < NS; ++a) {
-#pragma unroll
-            for (int l = 0; l < NM; ++l) G[a][l] = fma(Ns[a], Nm[l], G[a][l]);
-          }
-          if (SEG) {   // H = sum W N_s N_s^T = sum (W N_s) N_s^T, N_s = (W N_s) / W
-            double Nu[4];
-            shape_fn<NS>(xs1, xs2, Nu);
-#pragma unroll
-            for (int a = 0; a < NS; ++a)
-#pragma unroll
-              for (int b = 0; b < NS; ++b) H[a][b] = fma(Ns[a], Nu[b], H[a][b]);
-          }
-          ctr.gp++;
-        }
-      }
-      write_blocks<NS, NM, SEG>(p, r, G, H, rp.lm == 1, Mblk, Dblk);
-      flag[p] = 1;
+      if (i < n_live)
+        integrate_pair_sorted<NS, NM, SEG>(base + perm[i], ps, pm, srec, xm, conn_m, rp, Mblk, Dblk, flag, ctr);
     }
     __syncwarp();
   }
@@ -427,7 +442,10 @@ template <int NS, int NM, bool SEG>
 void launch_batched_r(const IntegrateArgs& a, const RunParams& rp, int n_sm, int rounds, int warps) {
   if (rounds <= 1) launch_batched_t<NS, NM, SEG, 1>(a, rp, n_sm, warps);
   else if (rounds == 2) launch_batched_t<NS, NM, SEG, 2>(a, rp, n_sm, warps);
-  else launch_batched_t<NS, NM, SEG, 4>(a, rp, n_sm, warps);
+  else if (rounds == 4) launch_batched_t<NS, NM, SEG, 4>(a, rp, n_sm, warps);
+  else if (rounds == 8) launch_batched_t<NS, NM, SEG, 8>(a, rp, n_sm, warps);
+  else if (rounds == 16) launch_batched_t<NS, NM, SEG, 16>(a, rp, n_sm, warps);
+  else launch_batched_t<NS, NM, SEG, 32>(a, rp, n_sm, warps);
 }
 
 template <int NS, int NM, bool SEG>
@@ -469,16 +487,14 @@ void launch_dispatch(const IntegrateArgs& a, const RunParams& rp, int nen_s, int
 }  // namespace
 
 bool integrate_batched_fits(int rounds, int block) {
-  const size_t per_warp = rounds <= 1 ? BatchSmem<1>::kBytes : (rounds == 2 ? BatchSmem<2>::kBytes : BatchSmem<4>::kBytes);
+  const size_t per_warp = (size_t)BatchSmem<32>::kBytes;   // the largest batch
+  (void)rounds;
   return block >= 32 && block <= kMaxPairBlock && (size_t)(block / 32) * per_warp <= kMaxDynSmem;
 }
 
 int integrate_rounds(int rounds, int block) {
-  // the integration kernel keeps each batch's polygons in shared memory:
-  // at most 4 rounds (128 pairs per warp), fewer where 8 warps would not fit
-  int r = rounds <= 1 ? 1 : (rounds == 2 ? 2 : 4);
-  while (r > 1 && !integrate_batched_fits(r, block)) r >>= 1;
-  return r;
+  (void)block;
+  return rounds <= 1 ? 1 : (rounds >= 32 ? 32 : rounds);
 }
 
 void launch_integrate_raw(const IntegrateArgs& a, const RunParams& rp, int nen_s, int nen_m, int n_sm) {

@@ -277,9 +277,8 @@ def test_launch_variants_agree(mt, orc, variant, rounds, block):
 
 def test_launch_shape_validation(mt, orc):
     """Shapes outside the documented set are refused (blocks above 256 threads,
-    blocks that are not whole warps, round counts other than 1, 2, 4, 8, 16, 32).
-    A shape whose batches the forward kernel cannot hold in shared memory is
-    accepted and that kernel runs fewer rounds."""
+    blocks that are not whole warps, round counts other than 1, 2, 4, 8, 16, 32);
+    the largest accepted shape evaluates correctly."""
     m = mt.Mortar()
     for args in ((0, 512, 0, 2), (1, 96 + 16, 0, 0), (0, 128, 0, 64), (0, 128, 0, 3), (0, 128, 0, 12)):
         with pytest.raises(mt._native.MortarError, match="INVALID_ARG"):
@@ -290,7 +289,7 @@ def test_launch_shape_validation(mt, orc):
     itf = inputs.planar_noisy(20, 17, 1, 49, "shape")
     m = mt.Mortar(lm=1, delta=itf.delta)
     m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
-    m.set_launch(0, 256, 0, 16)   # forward kernel: 2 rounds at 8 warps
+    m.set_launch(0, 256, 0, 32)
     m.evaluate()
     o = orc.make_opts(lm=1, delta=itf.delta)
     check_dm(mt, m, orc, itf, o, orc.evaluate(itf, o))
