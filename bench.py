@@ -189,7 +189,7 @@ def oracle_sample_step(itf, rows: int, threads: int):
     import oracle
     from paper_2202_03933_gb300 import inputs
     n = int(round(len(itf.conn_s) ** 0.5))
-    ne = rows * n
+    ne = min(rows * n, len(itf.conn_s))   # the whole slave mesh at most
     sub = inputs.Interface("sample", itf.xs, itf.conn_s[:ne], itf.type_s, itf.xm, itf.conn_m, itf.type_m,
                            lm=itf.lm, delta=itf.delta)
     lam = np.random.default_rng(0).uniform(-1, 1, itf.xs.shape)
@@ -206,6 +206,7 @@ def cpu_baseline(itf, target_s: float = 12.0) -> dict:
     pairs, dt, ne = oracle_sample_step(itf, 2, threads)
     rows = max(2, min(200, int(2 * target_s / max(dt, 1e-3))))
     pairs, dt, ne = oracle_sample_step(itf, rows, threads)
+    rows = -(-ne // max(1, int(round(len(itf.conn_s) ** 0.5))))   # rows actually taken
     p1, d1, _ = oracle_sample_step(itf, 1, 1)   # one host thread, one element row
     return {"value": pairs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{ne} of {len(itf.conn_s)} slave elements ({rows} element rows) x all master "
