@@ -53,8 +53,8 @@ UNIT = "pairs/s"
 # this build on planar_600x520 (same element types and density as the full
 # workload, so per-pair figures carry over); see profiles/.
 EXEC_PER_PAIR = {
-    "fused": {"flops": 9391.0, "dram_bytes": 876.0},
-    "integrate": {"flops": 3577.0, "dram_bytes": 284.0},
+    "fused": {"flops": 9365.0, "dram_bytes": 881.0},
+    "integrate": {"flops": 3629.0, "dram_bytes": 283.0},
 }
 
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes
@@ -86,7 +86,8 @@ def parse():
     ap.add_argument("--workload", default="planar_2000x1733")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--sections", default="forward,dynamic,element_based,linearisation,batched,probe",
+    ap.add_argument("--sections",
+                    default="forward,dynamic,element_based,linearisation,batched,quadratic,contact,probe",
                     help="extra sections measured after the timed step (comma list; 'none' for the step only)")
     return ap.parse_args()
 
@@ -625,6 +626,88 @@ def run_ours(args, world, rank, local):
     except Exception as ex_:   # reported, not fatal
         bat = {"error": str(ex_)}
 
+    # ---- quadratic slave elements (quad8 on the unit square: 1000 x 1000 with
+    #      the full workload, 450 x 450 otherwise) against a noisy quad4 master
+    #      (h_m / h_s = 1.155): forward graph (search + sub-element integration
+    #      + assembly), and the oracle on a strip
+    qd = None
+    try:
+        if "quadratic" not in sections:
+            raise _Skip()
+        nq = 1000 if args.workload == "planar_2000x1733" else 450
+        nqm = int(round(nq / 1.155))
+        q = inputs.quadratic_planar(nq, nqm, "quad8", name=f"quad8_{nq}x{nqm}")
+        mq = mortar.Mortar(lm=0, delta=q.delta, stream=stream.cuda_stream)
+        mq.set_interface(torch.from_numpy(q.xs).to(dev), torch.from_numpy(q.conn_s).to(dev),
+                         torch.from_numpy(q.xm).to(dev), torch.from_numpy(q.conn_m).to(dev))
+        mq.set_timing(True)
+        for _ in range(3):
+            mq.run_graph()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_q = []
+        q0.record(stream)
+        for _ in range(args.steps):
+            mq.run_graph()
+            t_q.append(mq.stats()["ms_integrate"])
+        q1.record(stream)
+        torch.cuda.synchronize()
+        ms_q = q0.elapsed_time(q1) / args.steps
+        sq = mq.stats()
+        qd = {"workload": f"quad8 {nq}x{nq} slave vs noisy quad4 {nqm}x{nqm} master, standard LMs",
+              "pairs": sq["n_pairs"], "nonempty_pairs": sq["n_nonempty"], "gauss_points": sq["n_gauss_points"],
+              "forward_ms_per_step": round(ms_q, 3), "ms_integrate": round(med(t_q), 3),
+              "pairs_per_s": world * sq["n_pairs"] / (ms_q / 1e3)}
+        mq.close()
+        if rank == 0 and not args.no_cpu_baseline:
+            import oracle
+            threads = os.cpu_count() or 1
+            sub = inputs.Interface("sample", q.xs, q.conn_s[:2 * nq], q.type_s, q.xm, q.conn_m, q.type_m,
+                                   lm=0, delta=q.delta)
+            t0 = time.perf_counter()
+            rq = oracle.evaluate(sub, oracle.make_opts(lm=0, delta=q.delta, n_threads=threads))
+            dt = time.perf_counter() - t0
+            qd["oracle"] = {"pairs_per_s": rq.s.size / dt, "s": round(dt, 2),
+                            "sample": f"{2 * nq} of {nq * nq} slave elements (2 element rows), {rq.s.size} pairs, "
+                                      f"search + integration + assembly, {threads} host threads"}
+        del q
+    except _Skip:
+        pass
+    except Exception as ex_:   # reported, not fatal
+        qd = {"error": str(ex_)}
+
+    # ---- contact-specific terms on the evaluated interface: nodal normals,
+    #      weighted normal gap, active set and complementarity residual; device
+    #      inputs, no host copies; CUDA-event time of the call
+    con = None
+    try:
+        if "contact" not in sections:
+            raise _Skip()
+        import ctypes
+        m.run_graph()   # forward blocks of the current coordinates
+        lam_n = torch.from_numpy(np.random.default_rng(2).uniform(-1.0, 0.0, itf.xs.shape[0])).to(dev)
+
+        def contact_call():
+            mortar.call("mortar_contact_terms", m.h, ctypes.c_void_p(lam_n.data_ptr()), 1.0, None, None, None,
+                        None, 1, ok=(0, -2, -3))
+
+        contact_call()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        K_c = max(min(args.steps, 10), 3)
+        c0.record(stream)
+        for _ in range(K_c):
+            contact_call()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ms_c = c0.elapsed_time(c1) / K_c
+        con = {"ms": round(ms_c, 3), "slave_nodes": int(itf.xs.shape[0]),
+               "nodes_per_s": world * itf.xs.shape[0] / (ms_c / 1e3),
+               "what": "averaged nodal normals, weighted normal gap, active set and NCP residual per slave node"}
+    except _Skip:
+        pass
+    except Exception as ex_:   # reported, not fatal
+        con = {"error": str(ex_)}
+
     # ---- FP64 probe (measured peak, for context)
     probe = None
     try:
@@ -706,6 +789,8 @@ def run_ours(args, world, rank, local):
         "batched": bat,
         "element_based": ebi,
         "dynamic": dyn,
+        "quadratic": qd,
+        "contact": con,
         "roofline": roof,
         "fp64_probe": probe,
         "e2e": e2e,

@@ -251,6 +251,22 @@ struct MapInverse {
     a00 = j11 * id; a01 = -j01 * id; a10 = -j10 * id; a11 = j00 * id;
   }
 
+  // J^-T b at (xi, eta) (the implicit-function step of a reverse sweep):
+  // (j11 b0 - j10 b1, j00 b1 - j01 b0) / det, without forming the inverse
+  __device__ __forceinline__ void jinvT(double xi, double eta, double b0, double b1, double& mu,
+                                        double& mv) const {
+    if (affine) {
+      mu = fma(i00, b0, i10 * b1);
+      mv = fma(i01, b0, i11 * b1);
+      return;
+    }
+    const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
+    const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
+    const double id = inv_det(fma(j00, j11, -j01 * j10));
+    mu = id * fma(j11, b0, -j10 * b1);
+    mv = id * fma(j00, b1, -j01 * b0);
+  }
+
   // FP32 Newton of a bilinear map (error ~1e-7 in xi); false if it did not settle
   __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
@@ -274,15 +290,18 @@ struct MapInverse {
     return conv;
   }
 
-  // one FP64 Newton step of a bilinear map from (xi, eta)
+  // one FP64 Newton step of a bilinear map from (xi, eta): with the Jacobian
+  // J = [c1 + c3 eta, c2 + c3 xi] the residual is r = J[:,0] xi + c2 eta - d,
+  // and the step J^-1 r is applied without forming the inverse
   __device__ __forceinline__ void polish(double xu, double xv, double& xi, double& eta) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
-    double k00, k01, k10, k11;
-    jinv(xi, eta, k00, k01, k10, k11);
-    const double ru = fma(fma(m.c3u, eta, m.c1u), xi, fma(m.c2u, eta, -du));
-    const double rv = fma(fma(m.c3v, eta, m.c1v), xi, fma(m.c2v, eta, -dv));
-    xi -= fma(k00, ru, k01 * rv);
-    eta -= fma(k10, ru, k11 * rv);
+    const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
+    const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
+    const double id = inv_det(fma(j00, j11, -j01 * j10));
+    const double ru = fma(j00, xi, fma(m.c2u, eta, -du));
+    const double rv = fma(j10, xi, fma(m.c2v, eta, -dv));
+    xi -= id * fma(j11, ru, -j01 * rv);
+    eta -= id * fma(j00, rv, -j10 * ru);
   }
 
   // FP64 Newton from the current (xi, eta), with the oracle's stopping rule:

@@ -508,14 +508,16 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
           double WNs[4], Nm[4];
           const double wk = kw * W;
           if constexpr (NS == 4) {
-            const double qa = fma(-wk, xs1, wk), qb = fma(wk, xs1, wk), c = 1.0 - xs2, d = 1.0 + xs2;
-            WNs[0] = qa * c; WNs[1] = qb * c; WNs[2] = qb * d; WNs[3] = qa * d;
+            // products of (1 -+ xi)(1 -+ eta) as FMAs: q (1 -+ eta) = q -+ q eta
+            const double qa = fma(-wk, xs1, wk), qb = fma(wk, xs1, wk);
+            WNs[0] = fma(-qa, xs2, qa); WNs[1] = fma(-qb, xs2, qb); WNs[2] = fma(qb, xs2, qb);
+            WNs[3] = fma(qa, xs2, qa);
           } else {
             WNs[1] = wk * xs1; WNs[2] = wk * xs2; WNs[0] = wk - WNs[1] - WNs[2]; WNs[3] = 0.0;
           }
           if constexpr (NM == 4) {
-            const double a = 1.0 - xm1, b = 1.0 + xm1, c = 1.0 - xm2, d = 1.0 + xm2;
-            Nm[0] = a * c; Nm[1] = b * c; Nm[2] = b * d; Nm[3] = a * d;
+            const double a = 1.0 - xm1, b = 1.0 + xm1;
+            Nm[0] = fma(-a, xm2, a); Nm[1] = fma(-b, xm2, b); Nm[2] = fma(b, xm2, b); Nm[3] = fma(a, xm2, a);
           } else {
             shape_fn<NM>(xm1, xm2, Nm);
           }
@@ -526,8 +528,8 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
           if (SEG) {   // H = sum W N_s N_s^T = sum WNs (N_s / km)
             double Ns[4];
             if constexpr (NS == 4 && NM == 4) {
-              const double a = 1.0 - xs1, b = 1.0 + xs1, c = 1.0 - xs2, d = 1.0 + xs2;
-              Ns[0] = a * c; Ns[1] = b * c; Ns[2] = b * d; Ns[3] = a * d;
+              const double a = 1.0 - xs1, b = 1.0 + xs1;
+              Ns[0] = fma(-a, xs2, a); Ns[1] = fma(-b, xs2, b); Ns[2] = fma(b, xs2, b); Ns[3] = fma(a, xs2, a);
             } else {
               shape_fn<NS>(xs1, xs2, Ns);
               if (NM == 4)
@@ -539,11 +541,9 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
               for (int b = 0; b < NS; ++b) H[a][b] = fma(WNs[a], Ns[b], H[a][b]);
           }
         }
-        double a00, a01, a10, a11;
-        si.jinv(xs1, xs2, a00, a01, a10, a11);
-        const double msu = a00 * xsb0 + a10 * xsb1, msv = a01 * xsb0 + a11 * xsb1;   // J^-T xib
-        mi.jinv(xm1, xm2, a00, a01, a10, a11);
-        const double mmu = a00 * xmb0 + a10 * xmb1, mmv = a01 * xmb0 + a11 * xmb1;
+        double msu, msv, mmu, mmv;   // J^-T xib on both sides
+        si.jinvT(xs1, xs2, xsb0, xsb1, msu, msv);
+        mi.jinvT(xm1, xm2, xmb0, xmb1, mmu, mmv);
         smb[0] -= msu; smb[1] -= msv;
         smb[2] = fma(-xs1, msu, smb[2]); smb[3] = fma(-xs1, msv, smb[3]);
         smb[4] = fma(-xs2, msu, smb[4]); smb[5] = fma(-xs2, msv, smb[5]);

@@ -286,15 +286,15 @@ __device__ __forceinline__ void integrate_pair_sorted(int64_t p, const int32_t* 
       if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
       const double wk = kw * (w * area);
       double Ns[4], Nm[4];   // Ns = (kw W) N_s / ks, Nm = N_m / km
-      if constexpr (NS == 4) {
-        const double qa = fma(-wk, xs1, wk), qb = fma(wk, xs1, wk), c = 1.0 - xs2, dd = 1.0 + xs2;
-        Ns[0] = qa * c; Ns[1] = qb * c; Ns[2] = qb * dd; Ns[3] = qa * dd;
+      if constexpr (NS == 4) {   // (1 -+ xi)(1 -+ eta) products as FMAs
+        const double qa = fma(-wk, xs1, wk), qb = fma(wk, xs1, wk);
+        Ns[0] = fma(-qa, xs2, qa); Ns[1] = fma(-qb, xs2, qb); Ns[2] = fma(qb, xs2, qb); Ns[3] = fma(qa, xs2, qa);
       } else {
         Ns[1] = wk * xs1; Ns[2] = wk * xs2; Ns[0] = wk - Ns[1] - Ns[2]; Ns[3] = 0.0;
       }
       if constexpr (NM == 4) {
-        const double a = 1.0 - xm1, b = 1.0 + xm1, c = 1.0 - xm2, d = 1.0 + xm2;
-        Nm[0] = a * c; Nm[1] = b * c; Nm[2] = b * d; Nm[3] = a * d;
+        const double a = 1.0 - xm1, b = 1.0 + xm1;
+        Nm[0] = fma(-a, xm2, a); Nm[1] = fma(-b, xm2, b); Nm[2] = fma(b, xm2, b); Nm[3] = fma(a, xm2, a);
       } else {
         shape_fn<NM>(xm1, xm2, Nm);
       }
@@ -305,8 +305,8 @@ __device__ __forceinline__ void integrate_pair_sorted(int64_t p, const int32_t* 
       if (SEG) {   // H = sum W N_s N_s^T = sum Ns (N_s / km)
         double Nu[4];
         if constexpr (NS == 4 && NM == 4) {
-          const double a = 1.0 - xs1, b = 1.0 + xs1, c = 1.0 - xs2, d = 1.0 + xs2;
-          Nu[0] = a * c; Nu[1] = b * c; Nu[2] = b * d; Nu[3] = a * d;
+          const double a = 1.0 - xs1, b = 1.0 + xs1;
+          Nu[0] = fma(-a, xs2, a); Nu[1] = fma(-b, xs2, b); Nu[2] = fma(b, xs2, b); Nu[3] = fma(a, xs2, a);
         } else {
           shape_fn<NS>(xs1, xs2, Nu);
           if (NM == 4)
