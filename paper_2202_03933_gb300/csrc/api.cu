@@ -108,6 +108,10 @@ int alloc_pair_buffers(mortar_ctx* c, int64_t cap) {
   MORTAR_TRY(buf_reserve(c->pairs_s, n * 4));
   MORTAR_TRY(buf_reserve(c->pairs_m, n * 4));
   MORTAR_TRY(buf_reserve(c->Mblk, n * mblk_stride(c) * 8));
+  if (quadratic_slave(c)) {   // four sub-element blocks per pair, summed into Mblk
+    MORTAR_TRY(buf_reserve(c->Qunit, n * 4 * 32 * 8));
+    MORTAR_TRY(buf_reserve(c->Qflag, n * 4));
+  }
   if (c->opt.d_domain == MORTAR_D_SEGMENT) MORTAR_TRY(buf_reserve(c->Dblk, n * 16 * 8));
   MORTAR_TRY(buf_reserve(c->flag, n));
   c->pair_cap = cap;
@@ -392,7 +396,8 @@ int set_common(mortar_ctx* c, int32_t n_if, const int64_t* sn_off, const int64_t
   MORTAR_TRY(buf_reserve(c->n2e_m_ent, Em * type_m * 8));
   const int64_t scan_n = std::max<int64_t>({c->bin_cap, c->Es, c->Ns, c->Nm, c->Em, 1});
   MORTAR_TRY(buf_reserve(c->scan_tmp, (size_t)scan_temp_words(scan_n) * 8));
-  if (c->pair_cap < 8 * c->Es + 1024 || c->Mblk.bytes < (size_t)c->pair_cap * mblk_stride(c) * 8)
+  if (c->pair_cap < 8 * c->Es + 1024 || c->Mblk.bytes < (size_t)c->pair_cap * mblk_stride(c) * 8 ||
+      (quad_s && c->Qunit.bytes < (size_t)c->pair_cap * 4 * 32 * 8))
     MORTAR_TRY(alloc_pair_buffers(c, std::max<int64_t>(c->pair_cap, 8 * c->Es + 1024)));
   if (c->nnz_cap_D < 9 * c->Ns + 64 || c->nnz_cap_M < 16 * c->Ns + 64)
     MORTAR_TRY(alloc_csr_buffers(c, std::max(c->nnz_cap_D, 9 * c->Ns + 64), std::max(c->nnz_cap_M, 16 * c->Ns + 64)));
@@ -493,7 +498,7 @@ void mortar_destroy(mortar_ctx* c) {
                     &c->J_pair, &c->ge_elem, &c->mp_cnt, &c->mp_off, &c->mp_list, &c->grad_s, &c->grad_m,
                     &c->J_part, &c->dstat, &c->cta_t, &c->tan_ys, &c->tan_ym, &c->tan_Kp, &c->tan_Op,
                     &c->tan_Ke, &c->tan_rowptr, &c->tan_col, &c->tan_val, &c->rule_1d, &c->nrm_m,
-                    &c->cn_normals, &c->cn_gap, &c->cn_lam, &c->cn_active, &c->cn_ncp};
+                    &c->cn_normals, &c->cn_gap, &c->cn_lam, &c->cn_active, &c->cn_ncp, &c->Qunit, &c->Qflag};
   for (DevBuf* b : bufs) buf_free(*b);
   if (c->hstat) cudaFreeHost(c->hstat);
   for (int i = 0; i < 8; ++i)

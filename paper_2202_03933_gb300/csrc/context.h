@@ -72,7 +72,8 @@ struct mortar_ctx {
   mortar::DevBuf cand_cnt, pair_off;        // int32 (Es), int64 (Es + 1)
   mortar::DevBuf pairs_s, pairs_m;          // int32 (pair_cap)
   int64_t pair_cap = 0;
-  mortar::DevBuf Mblk, Dblk, flag;          // FP64 16/pair, uint8/pair
+  mortar::DevBuf Mblk, Dblk, flag;          // FP64 16/pair (quadratic slaves 32), uint8/pair
+  mortar::DevBuf Qunit, Qflag;              // quadratic slaves: per (pair, sub-element) 32 FP64, uint8
   mortar::DevBuf row_cnt, row_cnt2;         // int32 (max(Ns, Nm)), int32 (Ns)
   mortar::DevBuf rowptr_D, col_D, val_D;
   mortar::DevBuf rowptr_M, col_M, val_M;
