@@ -207,6 +207,7 @@ struct MapInverse {
   double sc, sc2;                   // power-of-two scale and its square
   float f1u, f1v, f2u, f2v, f3u, f3v;
   float b00, b01, b10, b11;         // FP32 inverse of the scaled [c1 c2]
+  double id_last;                   // 1 / det J of the last solve's final Newton step (seed for jinvT)
 
   __device__ __forceinline__ void setup(const PlaneMap& mp, bool is_affine) {
     m = mp;
@@ -251,8 +252,11 @@ struct MapInverse {
     a00 = j11 * id; a01 = -j01 * id; a10 = -j10 * id; a11 = j00 * id;
   }
 
-  // J^-T b at (xi, eta) (the implicit-function step of a reverse sweep):
-  // (j11 b0 - j10 b1, j00 b1 - j01 b0) / det, without forming the inverse
+  // J^-T b at the (xi, eta) of the last solve (the implicit-function step of
+  // a reverse sweep): (j11 b0 - j10 b1, j00 b1 - j01 b0) / det, without
+  // forming the inverse.  1 / det is one Newton-Raphson reciprocal iteration
+  // from the last Newton step's 1 / det, whose point differs from (xi, eta)
+  // by that step (~1e-7): the seed's relative error ~1e-7 becomes ~1e-14.
   __device__ __forceinline__ void jinvT(double xi, double eta, double b0, double b1, double& mu,
                                         double& mv) const {
     if (affine) {
@@ -262,13 +266,16 @@ struct MapInverse {
     }
     const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
     const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
-    const double id = inv_det(fma(j00, j11, -j01 * j10));
+    const double det = fma(j00, j11, -j01 * j10);
+    const double id = fma(id_last, fma(-det, id_last, 1.0), id_last);
     mu = id * fma(j11, b0, -j10 * b1);
     mv = id * fma(j00, b1, -j01 * b0);
   }
 
-  // FP32 Newton of a bilinear map (error ~1e-7 in xi); false if it did not settle
-  __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta) const {
+  // FP32 Newton of a bilinear map (error ~1e-7 in xi); false if it did not
+  // settle.  idf: FP32 reciprocal of the scaled Jacobian determinant of the
+  // last iteration.
+  __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta, float& idf) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
     const float tu = f32_trunc(du * sc), tv = f32_trunc(dv * sc);
     float x = b00 * tu + b01 * tv, y = b10 * tu + b11 * tv;
@@ -280,6 +287,7 @@ struct MapInverse {
       const float j00 = fmaf(f3u, y, f1u), j01 = fmaf(f3u, x, f2u);
       const float j10 = fmaf(f3v, y, f1v), j11 = fmaf(f3v, x, f2v);
       const float id = __frcp_rn(j00 * j11 - j01 * j10);
+      idf = id;
       const float d0 = (j11 * ru - j01 * rv) * id, d1 = (j00 * rv - j10 * ru) * id;
       x -= d0;
       y -= d1;
@@ -292,12 +300,18 @@ struct MapInverse {
 
   // one FP64 Newton step of a bilinear map from (xi, eta): with the Jacobian
   // J = [c1 + c3 eta, c2 + c3 xi] the residual is r = J[:,0] xi + c2 eta - d,
-  // and the step J^-1 r is applied without forming the inverse
-  __device__ __forceinline__ void polish(double xu, double xv, double& xi, double& eta) const {
+  // and the step J^-1 r is applied without forming the inverse.  1 / det J:
+  // one Newton-Raphson reciprocal iteration from the FP32 iteration's last
+  // reciprocal idf (relative error ~1e-7 -> ~1e-13; the step's own error is
+  // that times |r| ~ 1e-7).
+  __device__ __forceinline__ void polish(double xu, double xv, double& xi, double& eta, float idf) {
     const double du = xu - m.c0u, dv = xv - m.c0v;
     const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
     const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
-    const double id = inv_det(fma(j00, j11, -j01 * j10));
+    const double det = fma(j00, j11, -j01 * j10);
+    const double id0 = f64_of_f32(idf) * sc2;
+    const double id = fma(id0, fma(-det, id0, 1.0), id0);
+    id_last = id;
     const double ru = fma(j00, xi, fma(m.c2u, eta, -du));
     const double rv = fma(j10, xi, fma(m.c2v, eta, -dv));
     xi -= id * fma(j11, ru, -j01 * rv);
@@ -309,7 +323,7 @@ struct MapInverse {
   // updates.  Taken only when the FP32 iteration did not settle (strongly
   // distorted elements: a corner angle near 180 degrees makes the FP32
   // Jacobian too inaccurate for its 3e-7 step test).
-  __device__ __forceinline__ bool newton64(double xu, double xv, double& xi, double& eta) const {
+  __device__ __forceinline__ bool newton64(double xu, double xv, double& xi, double& eta) {
     const double du = xu - m.c0u, dv = xv - m.c0v;
     bool last = false;
     for (int it = 0; it < 20; ++it) {
@@ -318,6 +332,7 @@ struct MapInverse {
       const double ru = fma(j00, xi, fma(m.c2u, eta, -du));
       const double rv = fma(j10, xi, fma(m.c2v, eta, -dv));
       const double id = 1.0 / (j00 * j11 - j01 * j10);
+      id_last = id;
       const double d0 = (j11 * ru - j01 * rv) * id, d1 = (j00 * rv - j10 * ru) * id;
       xi -= d0;
       eta -= d1;
@@ -329,15 +344,16 @@ struct MapInverse {
 
   // Converged xi of a point; false only if the FP64 fallback did not converge
   // either (xi then is the last iterate).
-  __device__ __forceinline__ bool solve(double xu, double xv, double& xi, double& eta) const {
+  __device__ __forceinline__ bool solve(double xu, double xv, double& xi, double& eta) {
     if (affine) {
       const double du = xu - m.c0u, dv = xv - m.c0v;
       xi = i00 * du + i01 * dv;
       eta = i10 * du + i11 * dv;
       return true;
     }
-    if (!coarse(xu, xv, xi, eta)) return newton64(xu, xv, xi, eta);
-    polish(xu, xv, xi, eta);
+    float idf = 0.0f;
+    if (!coarse(xu, xv, xi, eta, idf)) return newton64(xu, xv, xi, eta);
+    polish(xu, xv, xi, eta, idf);
     return true;
   }
 };

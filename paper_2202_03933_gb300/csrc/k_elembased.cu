@@ -124,16 +124,17 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
           double m1 = 0.0, m2 = 0.0;
           for (int k = 0; k < kc && owner < 0; ++k) {
             if (fu < box[k][0] || fu > box[k][1] || fv < box[k][2] || fv > box[k][3]) continue;
-            const MapInverse& mi = mic[k];
+            MapInverse& mi = mic[k];
             double a1, a2;
+            float idf = 0.0f;
             if (mi.affine) {
               mi.solve(xu, xv, a1, a2);
-            } else if (mi.coarse(xu, xv, a1, a2)) {   // FP32 iterate first: points clearly outside skip the FP64 step
+            } else if (mi.coarse(xu, xv, a1, a2, idf)) {   // FP32 iterate first: points clearly outside skip the FP64 step
               const bool near = NM == 4
                   ? (fabs(a1) <= 1.0 + 1e-5 && fabs(a2) <= 1.0 + 1e-5)
                   : (a1 >= -1e-5 && a2 >= -1e-5 && a1 + a2 <= 1.0 + 1e-5);
               if (!near) continue;
-              mi.polish(xu, xv, a1, a2);
+              mi.polish(xu, xv, a1, a2, idf);
             } else if (!mi.newton64(xu, xv, a1, a2)) {   // FP32 did not settle: FP64 Newton from its iterate
               continue;
             }
