@@ -222,9 +222,10 @@ struct MapInverse {
     frexp(L, &e);
     sc = ldexp(1.0, -e);   // exact power of two, L * sc in [0.5, 1)
     sc2 = sc * sc;
-    f1u = (float)(m.c1u * sc); f1v = (float)(m.c1v * sc);
-    f2u = (float)(m.c2u * sc); f2v = (float)(m.c2v * sc);
-    f3u = (float)(m.c3u * sc); f3v = (float)(m.c3v * sc);
+    const float scf = ldexpf(1.0f, -e);   // the same scale in FP32 (exact)
+    f1u = f32_trunc(m.c1u) * scf; f1v = f32_trunc(m.c1v) * scf;
+    f2u = f32_trunc(m.c2u) * scf; f2v = f32_trunc(m.c2v) * scf;
+    f3u = f32_trunc(m.c3u) * scf; f3v = f32_trunc(m.c3v) * scf;
     const float fd = 1.0f / (f1u * f2v - f2u * f1v);
     b00 = f2v * fd; b01 = -f2u * fd; b10 = -f1v * fd; b11 = f1u * fd;
   }

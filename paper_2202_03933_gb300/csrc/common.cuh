@@ -262,6 +262,13 @@ __device__ __forceinline__ void tri7_point(int q, double& l1, double& l2, double
   }
 }
 
+// 1 / n for the vertex counts of a clip polygon (the vertex-mean centroid of
+// the fan): a constant-memory load and a multiplication instead of an
+// integer-to-FP64 conversion and a division on the FP64 pipe
+static __constant__ double kInvCount[17] = {0.0,       1.0,       1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,
+                                            1.0 / 6,   1.0 / 7,   1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11,
+                                            1.0 / 12,  1.0 / 13,  1.0 / 14, 1.0 / 15, 1.0 / 16};
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -409,8 +409,8 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
     if (nr > 3) {
       double su = 0.0, sv = 0.0;
       for (int k = 0; k < nr; ++k) { su += cp.u(k); sv += cp.v(k); }
-      cu = su / (double)nr;
-      cv = sv / (double)nr;
+      cu = su * kInvCount[nr];
+      cv = sv * kInvCount[nr];
       ncell = nr;
     }
     // forward accumulators G = sum W N_s N_m^T, H = sum W N_s N_s^T, summed
@@ -567,7 +567,7 @@ __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, con
       if (nr == 3) { const int s0 = cp.id(0); Bu[s0] += abu; Bv[s0] += abv; } else { cbu += abu; cbv += abv; }
     }
     if (nr > 3) {
-      const double inv = 1.0 / (double)nr;
+      const double inv = kInvCount[nr];
       for (int k = 0; k < nr; ++k) { const int sk = cp.id(k); Bu[sk] += cbu * inv; Bv[sk] += cbv * inv; }
     }
     // Outputs go out with streaming (evict-first) stores: each is written once

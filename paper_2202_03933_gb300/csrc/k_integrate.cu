@@ -262,8 +262,8 @@ __device__ __forceinline__ void integrate_pair_sorted(int64_t p, const int32_t* 
   if (nr > 3) {
     double su = 0.0, sv = 0.0;
     for (int k = 0; k < nr; ++k) { su += pu[k]; sv += pv[k]; }
-    cu = su / (double)nr;
-    cv = sv / (double)nr;
+    cu = su * kInvCount[nr];
+    cv = sv * kInvCount[nr];
   }
   ctr.cells += ncell;
   ctr.nonempty++;

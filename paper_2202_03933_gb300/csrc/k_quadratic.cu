@@ -83,8 +83,8 @@ __device__ void integrate_unit(int64_t u, const int32_t* __restrict__ ps, const 
   if (nr > 3) {
     double su = 0.0, sv = 0.0;
     for (int j = 0; j < nr; ++j) { su += Pu[j]; sv += Pv[j]; }
-    cu = su / (double)nr;
-    cv = sv / (double)nr;
+    cu = su * kInvCount[nr];
+    cv = sv * kInvCount[nr];
     ncell = nr;
   }
   ctr.cells += ncell;

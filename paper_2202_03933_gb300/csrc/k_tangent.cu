@@ -125,8 +125,8 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
   if (nr > 3) {
     double su = 0.0, sv = 0.0;
     for (int k = 0; k < nr; ++k) { su += clip.u(k); sv += clip.v(k); }
-    cu = su / (double)nr;
-    cv = sv / (double)nr;
+    cu = su * kInvCount[nr];
+    cv = sv * kInvCount[nr];
     ncell = nr;
   }
   if (!live) ncell = 0;
@@ -211,28 +211,32 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
           dx[0] = -1.0; dx[1] = 1.0; dx[2] = 0.0; dx[3] = 0.0;
           de[0] = -1.0; de[1] = 0.0; de[2] = 1.0; de[3] = 0.0;
         }
-        double gu[4], gv[4], gYsu = 0.0, gYsv = 0.0;
+        // gu_e = J_s^-T grad N_e = (a00 dx_e + a10 de_e, a01 dx_e + a11 de_e) enters
+        // only scaled by W Z (and, segment mode, through sum_e yS_e gu_e): the
+        // scale is folded into the coefficients once per point
+        const double WZ = W * Z, wZ = w * Z;
+        const double p00 = WZ * a00, p10 = WZ * a10, p01 = WZ * a01, p11 = WZ * a11;
+        double WgYsu = 0.0, WgYsv = 0.0;
+        if (SEG) {
+          double sdx = 0.0, sde = 0.0;
 #pragma unroll
-        for (int e = 0; e < NS; ++e) {
-          gu[e] = a00 * dx[e] + a10 * de[e];
-          gv[e] = a01 * dx[e] + a11 * de[e];
-          if (SEG) { gYsu = fma(yS[e], gu[e], gYsu); gYsv = fma(yS[e], gv[e], gYsv); }
+          for (int e = 0; e < NS; ++e) { sdx = fma(yS[e], dx[e], sdx); sde = fma(yS[e], de[e], sde); }
+          WgYsu = W * fma(a00, sdx, a10 * sde);
+          WgYsv = W * fma(a01, sdx, a11 * sde);
         }
         double ym0, ym1;
         MA.pull(yM, ym0, ym1);
         const double b00 = x.b[0], b01 = x.b[1], b10 = x.b[2], b11 = x.b[3];
-        const double gYmu = b00 * ym0 + b10 * ym1, gYmv = b01 * ym0 + b11 * ym1;
-        const double WZ = W * Z, wZ = w * Z;
+        const double mWu = -W * fma(b00, ym0, b10 * ym1), mWv = -W * fma(b01, ym0, b11 * ym1);
         const double s12 = xs1 * xs2, m12 = xm1 * xm2;
 #pragma unroll
         for (int e = 0; e < NS; ++e) {
           const double ne = SA.N[e];
-          const double wn = W * ne;
-          O[e] = fma(wn, Z, O[e]);
+          O[e] = fma(ne, WZ, O[e]);
           arb[e] = fma(wZ, ne, arb[e]);
-          double su = WZ * gu[e], sv = WZ * gv[e];   // J_s^-T (adjoint of xi_s)
-          if (SEG) { su = fma(wn, gYsu, su); sv = fma(wn, gYsv, sv); }
-          const double tu = -wn * gYmu, tv = -wn * gYmv;   // J_m^-T (adjoint of xi_m)
+          double su = fma(p00, dx[e], p10 * de[e]), sv = fma(p01, dx[e], p11 * de[e]);   // J_s^-T (adjoint of xi_s)
+          if (SEG) { su = fma(ne, WgYsu, su); sv = fma(ne, WgYsv, sv); }
+          const double tu = ne * mWu, tv = ne * mWv;   // J_m^-T (adjoint of xi_m)
           double* A = acc + (16 * e) * kTanThreads;
           A[0 * kTanThreads] -= su;
           A[1 * kTanThreads] -= sv;
@@ -285,7 +289,7 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
     return;
   }
   if (nr > 3) {
-    const double inv = 1.0 / (double)nr;
+    const double inv = kInvCount[nr];
     for (int e = 0; e < NS; ++e)
       for (int k = 0; k < nr; ++k) {
         const int sk = clip.id(k);
