@@ -197,14 +197,19 @@ __device__ __forceinline__ int clip_count_f32(const double* __restrict__ r, cons
 // Inverse of an element map in the plane for many query points: affine maps
 // by a 2x2 inverse, bilinear ones by FP32 Newton on coordinates scaled by a
 // power of two (error e0 ~ 1e-7 in xi), then one FP64 Newton step with the
-// FP64 residual and the FP64 Jacobian at the FP32 solution, whose inverse uses
-// an FP32 reciprocal refined once in FP64 (relative error ~1e-14): the step
-// leaves ~1e-14 e0 + |c3|/|J| e0^2 ~ 1e-15 in xi, i.e. rounding level.
+// FP64 residual and the FP64 Jacobian at the FP32 solution, whose 1 / det is
+// the FP32 iteration's reciprocal refined once in FP64 (relative error
+// ~1e-13): the step leaves ~1e-13 e0 + |c3|/|J| e0^2 ~ 1e-15 in xi, i.e.
+// rounding level.  The reverse sweep's Jacobian inverse at the converged xi
+// refines that step's 1 / det once more (~1e-14).  Conversions between FP32
+// and FP64 are integer operations (f32_trunc, f64_of_f32): a conversion
+// instruction with an FP64 operand issues on the FP64 pipe.
 struct MapInverse {
   PlaneMap m;
   bool affine;
   double i00, i01, i10, i11;        // affine: exact inverse of [c1 c2]
   double sc, sc2;                   // power-of-two scale and its square
+  float scf;                        // the scale in FP32
   float f1u, f1v, f2u, f2v, f3u, f3v;
   float b00, b01, b10, b11;         // FP32 inverse of the scaled [c1 c2]
   double id_last;                   // 1 / det J of the last solve's final Newton step (seed for jinvT)
@@ -222,7 +227,7 @@ struct MapInverse {
     frexp(L, &e);
     sc = ldexp(1.0, -e);   // exact power of two, L * sc in [0.5, 1)
     sc2 = sc * sc;
-    const float scf = ldexpf(1.0f, -e);   // the same scale in FP32 (exact)
+    scf = ldexpf(1.0f, -e);   // the same scale in FP32 (exact)
     f1u = f32_trunc(m.c1u) * scf; f1v = f32_trunc(m.c1v) * scf;
     f2u = f32_trunc(m.c2u) * scf; f2v = f32_trunc(m.c2v) * scf;
     f3u = f32_trunc(m.c3u) * scf; f3v = f32_trunc(m.c3v) * scf;
@@ -230,17 +235,8 @@ struct MapInverse {
     b00 = f2v * fd; b01 = -f2u * fd; b10 = -f1v * fd; b11 = f1u * fd;
   }
 
-  // FP64 reciprocal of a Jacobian determinant: FP32 seed on the scaled value,
-  // then one Newton-Raphson reciprocal iteration r <- r + r (1 - d r) in FP64,
-  // which squares the seed's relative error (~1e-7 -> ~1e-14).
-  __device__ __forceinline__ double inv_det(double det) const {
-    double id = f64_of_f32(__frcp_rn((float)(det * sc2))) * sc2;
-    const double e = fma(-det, id, 1.0);
-    return fma(id, e, id);
-  }
-
-  // Inverse of the Jacobian at (xi, eta) to ~1e-14 (the reverse sweep's
-  // implicit-function step)
+  // Inverse of the Jacobian at the (xi, eta) of the last solve to ~1e-14 (the
+  // reverse sweep's implicit-function step)
   __device__ __forceinline__ void jinv(double xi, double eta, double& a00, double& a01, double& a10,
                                        double& a11) const {
     if (affine) {
@@ -249,7 +245,8 @@ struct MapInverse {
     }
     const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
     const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
-    const double id = inv_det(fma(j00, j11, -j01 * j10));
+    const double det = fma(j00, j11, -j01 * j10);
+    const double id = fma(id_last, fma(-det, id_last, 1.0), id_last);   // seeded as in jinvT
     a00 = j11 * id; a01 = -j01 * id; a10 = -j10 * id; a11 = j00 * id;
   }
 
@@ -278,7 +275,7 @@ struct MapInverse {
   // last iteration.
   __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta, float& idf) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
-    const float tu = f32_trunc(du * sc), tv = f32_trunc(dv * sc);
+    const float tu = f32_trunc(du) * scf, tv = f32_trunc(dv) * scf;
     float x = b00 * tu + b01 * tv, y = b10 * tu + b11 * tv;
     bool conv = false;
 #pragma unroll 1
