@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
         // box of the projected master element in FP32, widened far beyond the
         // inside tolerance and the FP32 rounding of the test point: a quick reject only
         const double band = 1e-4 * fmax(hi_u - lo_u, hi_v - lo_v);
-        box[k][0] = (float)(lo_u - band); box[k][1] = (float)(hi_u + band);
-        box[k][2] = (float)(lo_v - band); box[k][3] = (float)(hi_v + band);
+        box[k][0] = f32_trunc(lo_u - band); box[k][1] = f32_trunc(hi_u + band);
+        box[k][2] = f32_trunc(lo_v - band); box[k][3] = f32_trunc(hi_v + band);
         const PlaneMap mmap = plane_map<NM>(mu, mv);
         mic[k].setup(mmap, NM == 3 || map_is_affine(mmap));
       }
@@ -119,21 +119,42 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
           const double xe = xi * eta;
           const double xu = smap.c0u + smap.c1u * xi + smap.c2u * eta + smap.c3u * xe;
           const double xv = smap.c0v + smap.c1v * xi + smap.c2v * eta + smap.c3v * xe;
-          const float fu = (float)xu, fv = (float)xv;
+          const float fu = f32_trunc(xu), fv = f32_trunc(xv);
+          // Owner search in two parts: an FP32 scan (box reject, FP32 Newton
+          // iterate within 1e-5 of the element) finds the next candidate, then
+          // its FP64 step and inside test run for all lanes together; a
+          // candidate that fails the FP64 test (a point within 1e-5 of a
+          // master edge) resumes the scan after it.  Same owner as testing
+          // the candidates one by one in pair order.
           int owner = -1;
           double m1 = 0.0, m2 = 0.0;
-          for (int k = 0; k < kc && owner < 0; ++k) {
-            if (fu < box[k][0] || fu > box[k][1] || fv < box[k][2] || fv > box[k][3]) continue;
-            MapInverse& mi = mic[k];
-            double a1, a2;
+          int k = 0;
+          while (owner < 0 && k < kc) {
+            int kn = -1, mode = 0;   // 1: affine (solved), 2: FP32 iterate near, 3: FP32 did not settle
+            double a1 = 0.0, a2 = 0.0;
             float idf = 0.0f;
-            if (mi.affine) {
+            for (; k < kc; ++k) {
+              if (fu < box[k][0] || fu > box[k][1] || fv < box[k][2] || fv > box[k][3]) continue;
+              const MapInverse& mk = mic[k];
+              if (mk.affine) { mode = 1; kn = k; break; }
+              if (mk.coarse(xu, xv, a1, a2, idf)) {   // points clearly outside skip the FP64 step
+                const bool near = NM == 4
+                    ? (fabs(a1) <= 1.0 + 1e-5 && fabs(a2) <= 1.0 + 1e-5)
+                    : (a1 >= -1e-5 && a2 >= -1e-5 && a1 + a2 <= 1.0 + 1e-5);
+                if (!near) continue;
+                mode = 2;
+              } else {
+                mode = 3;
+              }
+              kn = k;
+              break;
+            }
+            if (kn < 0) break;
+            k = kn + 1;
+            MapInverse& mi = mic[kn];
+            if (mode == 1) {
               mi.solve(xu, xv, a1, a2);
-            } else if (mi.coarse(xu, xv, a1, a2, idf)) {   // FP32 iterate first: points clearly outside skip the FP64 step
-              const bool near = NM == 4
-                  ? (fabs(a1) <= 1.0 + 1e-5 && fabs(a2) <= 1.0 + 1e-5)
-                  : (a1 >= -1e-5 && a2 >= -1e-5 && a1 + a2 <= 1.0 + 1e-5);
-              if (!near) continue;
+            } else if (mode == 2) {
               mi.polish(xu, xv, a1, a2, idf);
             } else if (!mi.newton64(xu, xv, a1, a2)) {   // FP32 did not settle: FP64 Newton from its iterate
               continue;
@@ -142,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
                 ? (fabs(a1) <= 1.0 + kInsideTol && fabs(a2) <= 1.0 + kInsideTol)
                 : (a1 >= -kInsideTol && a2 >= -kInsideTol && a1 + a2 <= 1.0 + kInsideTol);
             if (!inside) continue;
-            owner = k;
+            owner = kn;
             m1 = a1;
             m2 = a2;
           }
