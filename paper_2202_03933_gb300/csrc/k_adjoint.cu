@@ -294,9 +294,11 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_pairs(
 //      dJ/dLambda_c = sum_b H[c][b] X_b - sum_l G[c][l] Y_l,  J = sum_c Lambda_c . dJ/dLambda_c;
 //  * element maps are inverted as in the batched integration kernel (affine
 //    2x2 inverse, or FP32 Newton + one FP64 Newton step), and the
-//    implicit-function step uses the exact FP64 inverse Jacobian;
+//    implicit-function step applies the FP64 inverse Jacobian at the
+//    converged xi (MapInverse::jinvT);
 //  * the clip is recorded as a compact vertex pool (ClipPool);
-//  * a warp sorts its batch of pairs by cell count before the sweep.
+//  * a warp sorts its batch of pairs by the cell count and edge
+//    intersections of an FP32 clip before the sweep.
 template <int NS, int NM, bool SEG, bool DUAL, bool FWD>
 __device__ void adjoint_pair_fast(int64_t p, const int32_t* __restrict__ ps, const int32_t* __restrict__ pm,
                                   const double* __restrict__ srec, const double* __restrict__ xs,
@@ -898,11 +900,13 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
   if (DUAL) {
     // A = Dh K, K = Me^-1 = Dh^-1 A
     double K[4][4], Kb[4][4];
-    for (int a = 0; a < NS; ++a)
+    for (int a = 0; a < NS; ++a) {
+      const double inv = 1.0 / Dh[a];   // one division per row
       for (int b = 0; b < NS; ++b) {
-        K[a][b] = A[a][b] / Dh[a];
+        K[a][b] = A[a][b] * inv;
         Kb[a][b] = Dh[a] * Ab[a][b];
       }
+    }
     for (int a = 0; a < NS; ++a) {
       double s = 0.0;
       for (int b = 0; b < NS; ++b) s += Ab[a][b] * K[a][b];

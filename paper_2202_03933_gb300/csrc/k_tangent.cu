@@ -354,8 +354,9 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
     for (int e = 0; e < 4; ++e) __stcs(g.Op + 12 * p + 3 * e + cp, e < NS ? O[e] : 0.0);
 }
 
-// Persistent kernel over warp batches of 32 R pairs, each sorted by cell count
-// (ballot counting sort) and swept in rounds of 10 pairs x 3 components.
+// Persistent kernel over warp batches of 32 R pairs, each sorted by the cell
+// count and edge intersections of an FP32 clip (ballot counting sort) and
+// swept in rounds of 10 pairs x 3 components.
 template <int NS, int NM, bool SEG, bool DUAL, int R>
 __global__ void __launch_bounds__(kTanThreads) k_tangent_pairs(TanArgs g) {
   extern __shared__ double tan_acc[];
