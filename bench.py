@@ -250,10 +250,11 @@ def run_reference(args, world, rank):
     from paper_2202_03933_gb300 import inputs
     itf = inputs.by_name(args.workload)
     threads = os.cpu_count() or 1
-    # rows per step: about 2 s of oracle work, so that the step's fixed cost
-    # (binning all master elements) is spread over enough pairs
+    # rows per step: about 5 s of oracle work by the 2-row estimate, so that
+    # the step's fixed cost (binning all master elements) is spread over
+    # enough pairs
     _, dt2, _ = oracle_sample_step(itf, 2, threads)
-    rows = max(4, min(200, int(2 * 2.0 / max(dt2, 1e-3))))
+    rows = max(4, min(200, int(2 * 5.0 / max(dt2, 1e-3))))
     for _ in range(args.warmup):
         oracle_sample_step(itf, rows, threads)
     tot_pairs, tot_s = 0, 0.0

@@ -104,16 +104,20 @@ __device__ void integrate_unit(int64_t u, const int32_t* __restrict__ ps, const 
       if (!mi.solve(xu, xv, xm1, xm2)) ctr.newton_fail++;
       double xp, ep;
       sub_to_parent<NP>(k, xs1, xs2, xp, ep);
-      double Np[8], Nm[4];
+      double Np[8], WNm[4];   // W folded into the master side (4 products instead of NP)
       shape_quadratic<NP>(xp, ep, Np);
-      shape_fn<NM>(xm1, xm2, Nm);
-      const double W = w * area;
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        const double wn = W * Np[a];
-#pragma unroll
-        for (int l = 0; l < NM; ++l) Mq[a][l] = fma(wn, Nm[l], Mq[a][l]);
+      if constexpr (NM == 4) {   // 1/4 of the quad4 shape functions folded into W
+        const double wq = 0.25 * (w * area);
+        const double qa = fma(-wq, xm1, wq), qb = fma(wq, xm1, wq);
+        WNm[0] = fma(-qa, xm2, qa); WNm[1] = fma(-qb, xm2, qb); WNm[2] = fma(qb, xm2, qb); WNm[3] = fma(qa, xm2, qa);
+      } else {
+        const double W = w * area;
+        WNm[1] = W * xm1; WNm[2] = W * xm2; WNm[0] = W - WNm[1] - WNm[2]; WNm[3] = 0.0;
       }
+#pragma unroll
+      for (int a = 0; a < NP; ++a)
+#pragma unroll
+        for (int l = 0; l < NM; ++l) Mq[a][l] = fma(Np[a], WNm[l], Mq[a][l]);
       ctr.gp++;
     }
   }
