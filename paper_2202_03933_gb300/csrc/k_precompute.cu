@@ -354,6 +354,8 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute_quadratic(
       degenerate |= dg;
       if (bad) r[SR_EPSIN] = -1.0;
     }
+    if (degenerate)   // a degenerate sub-element makes the whole element contribute nothing
+      for (int k = 0; k < 4; ++k) srec[(int64_t)SR_STRIDE * (4 * e + k) + SR_EPSIN] = -1.0;
     // element-domain D, standard LMs: De[a][b] = sum_q w J N_a N_b
     double D[8][8];
     for (int a = 0; a < 8; ++a)

@@ -174,3 +174,39 @@ def test_quadratic_refusals(mt):
     m.evaluate()
     assert m.pair_blocks()[0].shape[1:] == (4, 4)
     assert abs(m.scipy(mt.MATRIX_D).sum() - 1.0) < 1e-13
+
+
+def test_quadratic_nonfinite_and_folded(mt, orc):
+    """A non-finite slave coordinate gives MORTAR_ERR_INVALID_ARG and the same
+    context gives the oracle's result once it is finite again; a quad8 element
+    with two corners swapped (folded sub-elements) gives MORTAR_ERR_DEGENERATE,
+    its pairs come out empty and every other pair equals the oracle."""
+    itf = inputs.quadratic_planar(8, 7, "quad8", name="q8nf")
+    o = orc.make_opts(lm=0, d_domain=0, delta=itf.delta)
+    m = mt.Mortar(lm=0, d_domain=0, delta=itf.delta)
+    m.set_interface(itf.xs, itf.conn_s, itf.xm, itf.conn_m)
+    xs = itf.xs.copy()
+    xs[int(itf.conn_s[20, 5]), 0] = np.nan
+    m.set_coordinates(xs, itf.xm)
+    with pytest.raises(mt._native.MortarError, match="INVALID_ARG"):
+        m.evaluate()
+    m.set_coordinates(itf.xs, itf.xm)
+    m.evaluate()
+    ref = orc.evaluate(itf, o)
+    forward_parity(m.scipy(mt.MATRIX_D), m.scipy(mt.MATRIX_M), ref.D, ref.M,
+                   lambda x: (lambda r: (r.D, r.M))(orc.evaluate(x, o, pairs=(ref.s, ref.m))), itf)
+    cs = itf.conn_s.copy()
+    e = 27
+    cs[e, [0, 2]] = cs[e, [2, 0]]   # corners 0 and 2 swapped: the sub-elements fold
+    bad = inputs.Interface("q8fold", itf.xs, cs, itf.type_s, itf.xm, itf.conn_m, itf.type_m, lm=0,
+                           delta=itf.delta)
+    mb = mt.Mortar(lm=0, d_domain=0, delta=itf.delta)
+    mb.set_interface(bad.xs, bad.conn_s, bad.xm, bad.conn_m)
+    assert mb.evaluate() == -2   # MORTAR_ERR_DEGENERATE
+    s, mm = mb.pairs()
+    Mb, _, ne = mb.pair_blocks()
+    assert (s == e).any() and not ne[s == e].any()
+    keep = s != e
+    rMb, rne, _ = orc.quadratic_pair_blocks(bad, s[keep], mm[keep], o)
+    assert np.array_equal(ne[keep], rne)
+    blocks_parity(Mb[keep], rMb)
