@@ -240,7 +240,17 @@ __global__ void __launch_bounds__(kThreads) k_slave_precompute(
     double A[4][4];
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) A[a][b] = a == b ? 1.0 : 0.0;
-    if (rp.lm == 1 && !degenerate) {
+    if (rp.lm == 1 && !degenerate && flat_jac) {
+      // constant Jacobian: Me = J0 Mref, Dh = J0 dref, so A = dref Mref^-1 is a
+      // constant -- the tensor product of the 1D duals 2 N_1 - N_2 on a
+      // parallelogram (4 on the diagonal, -2 for edge neighbours, 1 across),
+      // Phi_a = 3 N_a - N_b - N_c on a triangle
+      for (int a = 0; a < NS; ++a)
+        for (int b = 0; b < NS; ++b) {
+          const int dd = (a - b + NS) % NS;
+          A[a][b] = NS == 4 ? (dd == 0 ? 4.0 : (dd == 2 ? 1.0 : -2.0)) : (dd == 0 ? 3.0 : -1.0);
+        }
+    } else if (rp.lm == 1 && !degenerate) {
       double K[4][4], B[4][4];
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) {
