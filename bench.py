@@ -53,8 +53,8 @@ UNIT = "pairs/s"
 # this build on planar_600x520 (same element types and density as the full
 # workload, so per-pair figures carry over); see profiles/.
 EXEC_PER_PAIR = {
-    "fused": {"flops": 8831.0, "dram_bytes": 881.0},
-    "integrate": {"flops": 3364.0, "dram_bytes": 286.0},
+    "fused": {"flops": 8492.3, "dram_bytes": 880.0},
+    "integrate": {"flops": 2994.6, "dram_bytes": 283.0},
 }
 
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA lanes

@@ -204,6 +204,14 @@ __device__ __forceinline__ int clip_count_f32(const double* __restrict__ r, cons
 // refines that step's 1 / det once more (~1e-14).  Conversions between FP32
 // and FP64 are integer operations (f32_trunc, f64_of_f32): a conversion
 // instruction with an FP64 operand issues on the FP64 pipe.
+// The FP32 Newton iteration's last Jacobian inverse of a bilinear map, in the
+// map's own (unscaled) units, and the FP32 reciprocal of its scaled
+// determinant.
+struct CoarseInv {
+  float g00, g01, g10, g11;
+  float idf;
+};
+
 struct MapInverse {
   PlaneMap m;
   bool affine;
@@ -212,7 +220,7 @@ struct MapInverse {
   float scf;                        // the scale in FP32
   float f1u, f1v, f2u, f2v, f3u, f3v;
   float b00, b01, b10, b11;         // FP32 inverse of the scaled [c1 c2]
-  double id_last;                   // 1 / det J of the last solve's final Newton step (seed for jinvT)
+  double id_seed;                   // 1 / det J near the last solve's point, to ~1e-7 (seed for jinv, jinvT)
 
   __device__ __forceinline__ void setup(const PlaneMap& mp, bool is_affine) {
     m = mp;
@@ -235,8 +243,8 @@ struct MapInverse {
     b00 = f2v * fd; b01 = -f2u * fd; b10 = -f1v * fd; b11 = f1u * fd;
   }
 
-  // Inverse of the Jacobian at the (xi, eta) of the last solve to ~1e-14 (the
-  // reverse sweep's implicit-function step)
+  // Inverse of the Jacobian at the (xi, eta) of the last solve to ~1e-13 (the
+  // reverse sweep's implicit-function step); 1 / det as in jinvT
   __device__ __forceinline__ void jinv(double xi, double eta, double& a00, double& a01, double& a10,
                                        double& a11) const {
     if (affine) {
@@ -246,15 +254,15 @@ struct MapInverse {
     const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
     const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
     const double det = fma(j00, j11, -j01 * j10);
-    const double id = fma(id_last, fma(-det, id_last, 1.0), id_last);   // seeded as in jinvT
+    const double id = fma(id_seed, fma(-det, id_seed, 1.0), id_seed);
     a00 = j11 * id; a01 = -j01 * id; a10 = -j10 * id; a11 = j00 * id;
   }
 
   // J^-T b at the (xi, eta) of the last solve (the implicit-function step of
   // a reverse sweep): (j11 b0 - j10 b1, j00 b1 - j01 b0) / det, without
   // forming the inverse.  1 / det is one Newton-Raphson reciprocal iteration
-  // from the last Newton step's 1 / det, whose point differs from (xi, eta)
-  // by that step (~1e-7): the seed's relative error ~1e-7 becomes ~1e-14.
+  // from id_seed (the FP32 iteration's last reciprocal, ~1e-7 relative
+  // error, which the iteration squares to ~1e-14).
   __device__ __forceinline__ void jinvT(double xi, double eta, double b0, double b1, double& mu,
                                         double& mv) const {
     if (affine) {
@@ -265,55 +273,57 @@ struct MapInverse {
     const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
     const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
     const double det = fma(j00, j11, -j01 * j10);
-    const double id = fma(id_last, fma(-det, id_last, 1.0), id_last);
+    const double id = fma(id_seed, fma(-det, id_seed, 1.0), id_seed);
     mu = id * fma(j11, b0, -j10 * b1);
     mv = id * fma(j00, b1, -j01 * b0);
   }
 
   // FP32 Newton of a bilinear map (error ~1e-7 in xi); false if it did not
-  // settle.  idf: FP32 reciprocal of the scaled Jacobian determinant of the
-  // last iteration.
-  __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta, float& idf) const {
+  // settle.  ci: the last iteration's FP32 Jacobian inverse (taken at a point
+  // within that iteration's step, <= 3e-7, of the returned xi) and 1 / det.
+  __device__ __forceinline__ bool coarse(double xu, double xv, double& xi, double& eta, CoarseInv& ci) const {
     const double du = xu - m.c0u, dv = xv - m.c0v;
     const float tu = f32_trunc(du) * scf, tv = f32_trunc(dv) * scf;
     float x = b00 * tu + b01 * tv, y = b10 * tu + b11 * tv;
+    float j00 = f1u, j01 = f2u, j10 = f1v, j11 = f2v, id = 0.0f;
     bool conv = false;
 #pragma unroll 1
     for (int it = 0; it < 16; ++it) {
       const float ru = fmaf(f3u * x, y, fmaf(f1u, x, fmaf(f2u, y, -tu)));
       const float rv = fmaf(f3v * x, y, fmaf(f1v, x, fmaf(f2v, y, -tv)));
-      const float j00 = fmaf(f3u, y, f1u), j01 = fmaf(f3u, x, f2u);
-      const float j10 = fmaf(f3v, y, f1v), j11 = fmaf(f3v, x, f2v);
-      const float id = __frcp_rn(j00 * j11 - j01 * j10);
-      idf = id;
+      j00 = fmaf(f3u, y, f1u); j01 = fmaf(f3u, x, f2u);
+      j10 = fmaf(f3v, y, f1v); j11 = fmaf(f3v, x, f2v);
+      id = __frcp_rn(j00 * j11 - j01 * j10);
       const float d0 = (j11 * ru - j01 * rv) * id, d1 = (j00 * rv - j10 * ru) * id;
       x -= d0;
       y -= d1;
       if (fabsf(d0) + fabsf(d1) <= 3e-7f) { conv = true; break; }
     }
+    // the scaled map is scf J: J^-1 = scf (scf J)^-1 (scf a power of two)
+    const float is = id * scf;
+    ci.g00 = j11 * is; ci.g01 = -j01 * is; ci.g10 = -j10 * is; ci.g11 = j00 * is;
+    ci.idf = id;
     xi = f64_of_f32(x);
     eta = f64_of_f32(y);
     return conv;
   }
 
-  // one FP64 Newton step of a bilinear map from (xi, eta): with the Jacobian
-  // J = [c1 + c3 eta, c2 + c3 xi] the residual is r = J[:,0] xi + c2 eta - d,
-  // and the step J^-1 r is applied without forming the inverse.  1 / det J:
-  // one Newton-Raphson reciprocal iteration from the FP32 iteration's last
-  // reciprocal idf (relative error ~1e-7 -> ~1e-13; the step's own error is
-  // that times |r| ~ 1e-7).
-  __device__ __forceinline__ void polish(double xu, double xv, double& xi, double& eta, float idf) {
+  // One Newton step of a bilinear map from the FP32 iterate (xi, eta): FP64
+  // residual r = (c1 + c3 eta) xi + c2 eta - d, step G r with G the FP32
+  // iteration's last Jacobian inverse.  G differs from J(xi, eta)^-1 by a
+  // relative ~1e-7 (FP32 rounding, and the last FP32 step <= 3e-7), so the
+  // step leaves an error of ~1e-7 x the iterate's own ~1e-7 error, the same
+  // order as the quadratic term of an exact-Jacobian step.
+  __device__ __forceinline__ void polish(double xu, double xv, double& xi, double& eta, const CoarseInv& ci) {
     const double du = xu - m.c0u, dv = xv - m.c0v;
-    const double j00 = fma(m.c3u, eta, m.c1u), j01 = fma(m.c3u, xi, m.c2u);
-    const double j10 = fma(m.c3v, eta, m.c1v), j11 = fma(m.c3v, xi, m.c2v);
-    const double det = fma(j00, j11, -j01 * j10);
-    const double id0 = f64_of_f32(idf) * sc2;
-    const double id = fma(id0, fma(-det, id0, 1.0), id0);
-    id_last = id;
+    const double j00 = fma(m.c3u, eta, m.c1u), j10 = fma(m.c3v, eta, m.c1v);
     const double ru = fma(j00, xi, fma(m.c2u, eta, -du));
     const double rv = fma(j10, xi, fma(m.c2v, eta, -dv));
-    xi -= id * fma(j11, ru, -j01 * rv);
-    eta -= id * fma(j00, rv, -j10 * ru);
+    const double g00 = f64_of_f32(ci.g00), g01 = f64_of_f32(ci.g01);
+    const double g10 = f64_of_f32(ci.g10), g11 = f64_of_f32(ci.g11);
+    xi = fma(-g00, ru, fma(-g01, rv, xi));
+    eta = fma(-g10, ru, fma(-g11, rv, eta));
+    id_seed = f64_of_f32(ci.idf) * sc2;
   }
 
   // FP64 Newton from the current (xi, eta), with the oracle's stopping rule:
@@ -330,7 +340,7 @@ struct MapInverse {
       const double ru = fma(j00, xi, fma(m.c2u, eta, -du));
       const double rv = fma(j10, xi, fma(m.c2v, eta, -dv));
       const double id = 1.0 / (j00 * j11 - j01 * j10);
-      id_last = id;
+      id_seed = id;
       const double d0 = (j11 * ru - j01 * rv) * id, d1 = (j00 * rv - j10 * ru) * id;
       xi -= d0;
       eta -= d1;
@@ -349,9 +359,9 @@ struct MapInverse {
       eta = i10 * du + i11 * dv;
       return true;
     }
-    float idf = 0.0f;
-    if (!coarse(xu, xv, xi, eta, idf)) return newton64(xu, xv, xi, eta);
-    polish(xu, xv, xi, eta, idf);
+    CoarseInv ci;
+    if (!coarse(xu, xv, xi, eta, ci)) return newton64(xu, xv, xi, eta);
+    polish(xu, xv, xi, eta, ci);
     return true;
   }
 };

@@ -132,12 +132,12 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
           while (owner < 0 && k < kc) {
             int kn = -1, mode = 0;   // 1: affine (solved), 2: FP32 iterate near, 3: FP32 did not settle
             double a1 = 0.0, a2 = 0.0;
-            float idf = 0.0f;
+            CoarseInv ci;
             for (; k < kc; ++k) {
               if (fu < box[k][0] || fu > box[k][1] || fv < box[k][2] || fv > box[k][3]) continue;
               const MapInverse& mk = mic[k];
               if (mk.affine) { mode = 1; kn = k; break; }
-              if (mk.coarse(xu, xv, a1, a2, idf)) {   // points clearly outside skip the FP64 step
+              if (mk.coarse(xu, xv, a1, a2, ci)) {   // points clearly outside skip the FP64 step
                 const bool near = NM == 4
                     ? (fabs(a1) <= 1.0 + 1e-5 && fabs(a2) <= 1.0 + 1e-5)
                     : (a1 >= -1e-5 && a2 >= -1e-5 && a1 + a2 <= 1.0 + 1e-5);
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
             if (mode == 1) {
               mi.solve(xu, xv, a1, a2);
             } else if (mode == 2) {
-              mi.polish(xu, xv, a1, a2, idf);
+              mi.polish(xu, xv, a1, a2, ci);
             } else if (!mi.newton64(xu, xv, a1, a2)) {   // FP32 did not settle: FP64 Newton from its iterate
               continue;
             }
