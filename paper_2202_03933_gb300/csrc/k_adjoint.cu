@@ -927,9 +927,49 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
         Meb[a][b] -= s;
       }
   }
-  // element integrals -> nodes
-  double S1[4] = {0, 0, 0, 0}, S2[4] = {0, 0, 0, 0};   // flat: sum_q jb_q dN_a/dxi, dN_a/deta
-  for (int q = 0; q < nq; ++q) {
+  // element integrals -> nodes.  The adjoint of the surface Jacobian at a
+  // point is jb = sum_ab (Dhb_a + Meb_ab N_b) N_a; a flat element only needs
+  // S1_c = int jb dN_c/dxi and S2_c = int jb dN_c/deta over the reference
+  // element, which are exact polynomial integrals:
+  //   quad4 (corners (xi_a, eta_a) = (-1,-1), (1,-1), (1,1), (-1,1)):
+  //     int N_a dN_c/dxi         = xi_c / 4 (1 + eta_a eta_c / 3)
+  //     int N_a N_b dN_c/dxi     = xi_c / 64 (2 + 2/3 xi_a xi_b)(2 + 2/3 (eta_a eta_b + eta_c (eta_a + eta_b)))
+  //   (and the same with xi and eta exchanged for dN_c/deta);
+  //   tri3: dN_c constant, int N_a = 1/6, int N_a N_b = 1/12 (a = b) or 1/24.
+  double S1[4] = {0, 0, 0, 0}, S2[4] = {0, 0, 0, 0};
+  if (flat) {
+    if constexpr (NS == 4) {
+      constexpr double cx[4] = {-1.0, 1.0, 1.0, -1.0}, cy[4] = {-1.0, -1.0, 1.0, 1.0};
+      double A0 = 0.0, A1 = 0.0, C1 = 0.0, B0 = 0.0, Bx = 0.0, By = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        B0 += Dhb[a];
+        Bx = fma(cx[a], Dhb[a], Bx);
+        By = fma(cy[a], Dhb[a], By);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const double px = 2.0 + (2.0 / 3.0) * cx[a] * cx[b], py = 2.0 + (2.0 / 3.0) * cy[a] * cy[b];
+          A0 = fma(px * py, Meb[a][b], A0);
+          A1 = fma(px * (cy[a] + cy[b]), Meb[a][b], A1);
+          C1 = fma(py * (cx[a] + cx[b]), Meb[a][b], C1);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        S1[c] = cx[c] * fma(1.0 / 64.0, fma((2.0 / 3.0) * cy[c], A1, A0), 0.25 * fma(cy[c] / 3.0, By, B0));
+        S2[c] = cy[c] * fma(1.0 / 64.0, fma((2.0 / 3.0) * cx[c], C1, A0), 0.25 * fma(cx[c] / 3.0, Bx, B0));
+      }
+    } else {
+      double T = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        T = fma(1.0 / 6.0, Dhb[a], T);
+        for (int b = 0; b < 3; ++b) T = fma(a == b ? 1.0 / 12.0 : 1.0 / 24.0, Meb[a][b], T);
+      }
+      S1[0] = -T; S1[1] = T; S1[2] = 0.0;
+      S2[0] = -T; S2[1] = 0.0; S2[2] = T;
+    }
+  }
+  for (int q = 0; q < nq && !flat; ++q) {
     double xi, eta, w;
     elem_point_a<NS>(q, xi, eta, w);
     double N[4], dN[4][2];
@@ -942,10 +982,6 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
       jb = fma(v, N[a], jb);
     }
     jb *= w;
-    if (flat) {
-      for (int a = 0; a < NS; ++a) { S1[a] = fma(jb, dN[a][0], S1[a]); S2[a] = fma(jb, dN[a][1], S2[a]); }
-      continue;
-    }
     if (jb == 0.0) continue;
     V3 g1 = v3(0, 0, 0), g2 = v3(0, 0, 0);
     for (int a = 0; a < NS; ++a) { g1 = g1 + dN[a][0] * X[a]; g2 = g2 + dN[a][1] * X[a]; }
