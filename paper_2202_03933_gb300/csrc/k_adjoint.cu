@@ -782,6 +782,49 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_batched(
   cta_mark(cta_t, 1);
 }
 
+// Constant tables of a flat element with dual LMs.  There Dh_a = d for every
+// a, Me = d Mref and A is the constant matrix ac (quad4: 4 on the diagonal,
+// -2 for edge neighbours, 1 across; tri3: 3 and -1), so the adjoint of the
+// element integrals through A = Dh Me^-1 is Meb = -(1/d) ac Ab ac.  The flat
+// reverse below needs Meb only through weighted sums sum_ab w_ab Meb_ab, which
+// equal -(1/d) sum_cd Ab_cd (ac w ac)_cd: w[k] holds ac w_k ac for the weights
+// of the closed-form reference integrals (quad4: the three of S1 / S2; tri3:
+// int N_a N_b).
+struct FlatDualTables {
+  double ac[4][4];
+  double w[3][4][4];
+};
+
+template <int NS>
+constexpr FlatDualTables flat_dual_tables() {
+  FlatDualTables t{};
+  const double cx[4] = {-1.0, 1.0, 1.0, -1.0}, cy[4] = {-1.0, -1.0, 1.0, 1.0};
+  double wk[3][4][4] = {};
+  for (int a = 0; a < NS; ++a)
+    for (int b = 0; b < NS; ++b) {
+      if (NS == 4) {
+        const int dd = (a - b + 4) % 4;
+        t.ac[a][b] = dd == 0 ? 4.0 : (dd == 2 ? 1.0 : -2.0);
+        const double px = 2.0 + (2.0 / 3.0) * cx[a] * cx[b], py = 2.0 + (2.0 / 3.0) * cy[a] * cy[b];
+        wk[0][a][b] = px * py;
+        wk[1][a][b] = px * (cy[a] + cy[b]);
+        wk[2][a][b] = py * (cx[a] + cx[b]);
+      } else {
+        t.ac[a][b] = a == b ? 3.0 : -1.0;
+        wk[0][a][b] = a == b ? 1.0 / 12.0 : 1.0 / 24.0;
+      }
+    }
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < NS; ++c)
+      for (int d = 0; d < NS; ++d) {
+        double v = 0.0;
+        for (int a = 0; a < NS; ++a)
+          for (int b = 0; b < NS; ++b) v += t.ac[a][c] * wk[k][a][b] * t.ac[d][b];
+        t.w[k][c][d] = v;
+      }
+  return t;
+}
+
 // Per slave element: sum dJ/dA over its pairs, add the element-domain D term,
 // propagate through A = Dh Me^-1 and the element integrals to the nodes.
 template <int NS, bool DUAL, bool ELEMD>
@@ -897,7 +940,19 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
         }
       }
   }
-  if (DUAL) {
+  constexpr FlatDualTables kFD = flat_dual_tables<NS>();
+  const bool flat_dual = DUAL && flat;
+  const double inv_d = flat_dual ? 1.0 / Dh[0] : 0.0;
+  if (flat_dual) {
+    // Dhb_a += sum_b Ab_ab K_ab with K = ac / d; Meb enters below as weighted sums
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+      double t = 0.0;
+#pragma unroll
+      for (int b = 0; b < NS; ++b) t = fma(kFD.ac[a][b], Ab[a][b], t);
+      Dhb[a] = fma(t, inv_d, Dhb[a]);
+    }
+  } else if (DUAL) {
     // A = Dh K, K = Me^-1 = Dh^-1 A
     double K[4][4], Kb[4][4];
     for (int a = 0; a < NS; ++a) {
@@ -948,23 +1003,32 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_elems(
         By = fma(cy[a], Dhb[a], By);
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          const double px = 2.0 + (2.0 / 3.0) * cx[a] * cx[b], py = 2.0 + (2.0 / 3.0) * cy[a] * cy[b];
-          A0 = fma(px * py, Meb[a][b], A0);
-          A1 = fma(px * (cy[a] + cy[b]), Meb[a][b], A1);
-          C1 = fma(py * (cx[a] + cx[b]), Meb[a][b], C1);
+          if (flat_dual) {
+            A0 = fma(kFD.w[0][a][b], Ab[a][b], A0);
+            A1 = fma(kFD.w[1][a][b], Ab[a][b], A1);
+            C1 = fma(kFD.w[2][a][b], Ab[a][b], C1);
+          } else {
+            const double px = 2.0 + (2.0 / 3.0) * cx[a] * cx[b], py = 2.0 + (2.0 / 3.0) * cy[a] * cy[b];
+            A0 = fma(px * py, Meb[a][b], A0);
+            A1 = fma(px * (cy[a] + cy[b]), Meb[a][b], A1);
+            C1 = fma(py * (cx[a] + cx[b]), Meb[a][b], C1);
+          }
         }
       }
+      if (flat_dual) { A0 *= -inv_d; A1 *= -inv_d; C1 *= -inv_d; }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         S1[c] = cx[c] * fma(1.0 / 64.0, fma((2.0 / 3.0) * cy[c], A1, A0), 0.25 * fma(cy[c] / 3.0, By, B0));
         S2[c] = cy[c] * fma(1.0 / 64.0, fma((2.0 / 3.0) * cx[c], C1, A0), 0.25 * fma(cx[c] / 3.0, Bx, B0));
       }
     } else {
-      double T = 0.0;
+      double T = 0.0, Tm = 0.0;
       for (int a = 0; a < 3; ++a) {
         T = fma(1.0 / 6.0, Dhb[a], T);
-        for (int b = 0; b < 3; ++b) T = fma(a == b ? 1.0 / 12.0 : 1.0 / 24.0, Meb[a][b], T);
+        for (int b = 0; b < 3; ++b)
+          Tm = flat_dual ? fma(kFD.w[0][a][b], Ab[a][b], Tm) : fma(a == b ? 1.0 / 12.0 : 1.0 / 24.0, Meb[a][b], Tm);
       }
+      T = flat_dual ? fma(-inv_d, Tm, T) : T + Tm;
       S1[0] = -T; S1[1] = T; S1[2] = 0.0;
       S2[0] = -T; S2[1] = 0.0; S2[2] = T;
     }
