@@ -40,7 +40,10 @@ constexpr int kChunk = 8;   // candidate pairs held per pass over the points
 // the owner's block in global memory (this thread's own blocks, L1-resident)
 // in point order.  Elements with more than kChunk pairs take further passes
 // over the points not yet owned, so "first covering pair in pair order" holds.
-template <int NS, int NM, bool SEG, bool DUAL>
+// NODAL (dual LMs only): accumulate G = sum W N_s N_m^T in the nodal basis and
+// apply A once per pair, instead of forming the dual basis at every point;
+// chosen for rules with about ten or more points per pair (n >= 6).
+template <int NS, int NM, bool SEG, bool DUAL, bool NODAL>
 __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
     const int64_t* __restrict__ pair_off, const int32_t* __restrict__ pm, const double* __restrict__ srec,
     const double* __restrict__ xm, const int32_t* __restrict__ conn_m, const double* __restrict__ rule, int n,
@@ -173,17 +176,19 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
           const double j00 = smap.c1u + smap.c3u * eta, j01 = smap.c2u + smap.c3u * xi;
           const double j10 = smap.c1v + smap.c3v * eta, j11 = smap.c2v + smap.c3v * xi;
           const double W = wq * fabs(j00 * j11 - j01 * j10);
+          // dual LMs: Phi_a = A N_s per point, or (NODAL) G = sum W N_s N_m^T
+          // and H = sum W N_s N_s^T in the nodal basis, turned into A G, A H
+          // once the chunk is done
           double Ns[4], Nm[4], Phi[4];
           shape_fn<NS>(xi, eta, Ns);
           shape_fn<NM>(m1, m2, Nm);
 #pragma unroll
           for (int a = 0; a < NS; ++a) {
-            double v = 0.0;
-            if (DUAL) {
+            double v = Ns[a];
+            if (DUAL && !NODAL) {
+              v = 0.0;
 #pragma unroll
               for (int c = 0; c < NS; ++c) v = fma(Phi_c[a][c], Ns[c], v);
-            } else {
-              v = Ns[a];
             }
             Phi[a] = W * v;
           }
@@ -200,6 +205,41 @@ __global__ void __launch_bounds__(kThreads) k_integrate_elembased(
               for (int b = 0; b < NS; ++b) dout[4 * a + b] = fma(Phi[a], Ns[b], dout[4 * a + b]);
           }
         }
+        if (DUAL && NODAL)   // every point of this chunk's pairs is in: M = A G, D = A H
+          for (int k = 0; k < kc; ++k) {
+            if (got[k] == 0) continue;
+            double* mo = Mblk + 16 * (c0 + k);
+            double G[4][4];
+#pragma unroll
+            for (int c = 0; c < NS; ++c)
+#pragma unroll
+              for (int l = 0; l < NM; ++l) G[c][l] = mo[4 * c + l];
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+#pragma unroll
+              for (int l = 0; l < NM; ++l) {
+                double v = 0.0;
+#pragma unroll
+                for (int c = 0; c < NS; ++c) v = fma(Phi_c[a][c], G[c][l], v);
+                mo[4 * a + l] = v;
+              }
+            if (SEG) {
+              double* dout = Dblk + 16 * (c0 + k);
+#pragma unroll
+              for (int c = 0; c < NS; ++c)
+#pragma unroll
+                for (int b = 0; b < NS; ++b) G[c][b] = dout[4 * c + b];
+#pragma unroll
+              for (int a = 0; a < NS; ++a)
+#pragma unroll
+                for (int b = 0; b < NS; ++b) {
+                  double v = 0.0;
+#pragma unroll
+                  for (int c = 0; c < NS; ++c) v = fma(Phi_c[a][c], G[c][b], v);
+                  dout[4 * a + b] = v;
+                }
+            }
+          }
       }
       for (int k = 0; k < kc; ++k) {
         flag[c0 + k] = got[k] > 0 ? 1 : 0;
@@ -221,10 +261,13 @@ void launch_nsnm(mortar_ctx* c, const RunParams& rp, unsigned grid) {
                                            c->rule_1d_n, c->Es, c->Mblk.as<double>(), c->Dblk.as<double>(),
                                            c->flag.as<uint8_t>(), c->dstat.as<DevStatus>());
   };
-  if (seg && dual) go(k_integrate_elembased<NS, NM, true, true>);
-  else if (seg) go(k_integrate_elembased<NS, NM, true, false>);
-  else if (dual) go(k_integrate_elembased<NS, NM, false, true>);
-  else go(k_integrate_elembased<NS, NM, false, false>);
+  const bool nodal = c->rule_1d_n >= 6;
+  if (seg && dual && nodal) go(k_integrate_elembased<NS, NM, true, true, true>);
+  else if (seg && dual) go(k_integrate_elembased<NS, NM, true, true, false>);
+  else if (seg) go(k_integrate_elembased<NS, NM, true, false, false>);
+  else if (dual && nodal) go(k_integrate_elembased<NS, NM, false, true, true>);
+  else if (dual) go(k_integrate_elembased<NS, NM, false, true, false>);
+  else go(k_integrate_elembased<NS, NM, false, false, false>);
 }
 
 }  // namespace
@@ -273,7 +316,7 @@ int upload_gauss_legendre(mortar_ctx* c, int n) {
 void launch_integrate_element_based(mortar_ctx* c, const RunParams& rp) {
   if (c->Es == 0) return;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate_elembased<4, 4, false, true>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate_elembased<4, 4, false, true, false>, kThreads, 0);
   if (per_sm < 1) per_sm = 1;
   const int64_t need = (c->Es + kThreads - 1) / kThreads;
   const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)c->n_sm * per_sm * 8);
