@@ -260,7 +260,7 @@ __device__ void tangent_pair(const TanArgs& g, int64_t p, int cp, bool live, dou
           e2bu[e] = fma(l2, xbu, e2bu[e]); e2bv[e] = fma(l2, xbv, e2bv[e]);
         }
       }
-      __syncwarp();   // the slots are rewritten in the next round
+      __syncwarp();   // the slots are rewritten by the next three points
     }
     if (cell_ok) {
 #pragma unroll
