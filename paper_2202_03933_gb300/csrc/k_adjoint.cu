@@ -825,6 +825,30 @@ constexpr FlatDualTables flat_dual_tables() {
   return t;
 }
 
+// The tables' ac is the dual matrix of the reference element: ac Mref = dref I
+// (quad4: Mref = (4, 2, 1) / 9 by node distance, dref = 1; tri3: Mref = 1/12 on
+// the diagonal, 1/24 off it, dref = 1/6).
+template <int NS>
+constexpr bool flat_dual_biorthogonal() {
+  const FlatDualTables t = flat_dual_tables<NS>();
+  for (int a = 0; a < NS; ++a)
+    for (int c = 0; c < NS; ++c) {
+      double v = 0.0;
+      for (int b = 0; b < NS; ++b) {
+        const int dd = (b - c + NS) % NS;
+        const double mref = NS == 4 ? (dd == 0 ? 4.0 / 9.0 : (dd == 2 ? 1.0 / 9.0 : 2.0 / 9.0))
+                                    : (dd == 0 ? 1.0 / 12.0 : 1.0 / 24.0);
+        v += t.ac[a][b] * mref;
+      }
+      const double want = a == c ? (NS == 4 ? 1.0 : 1.0 / 6.0) : 0.0;
+      const double err = v - want;
+      if (err > 1e-14 || err < -1e-14) return false;
+    }
+  return true;
+}
+static_assert(flat_dual_biorthogonal<4>() && flat_dual_biorthogonal<3>(),
+              "flat-element dual coefficients are not the reference element's dual matrix");
+
 // Per slave element: sum dJ/dA over its pairs, add the element-domain D term,
 // propagate through A = Dh Me^-1 and the element integrals to the nodes.
 template <int NS, bool DUAL, bool ELEMD>
