@@ -194,16 +194,6 @@ __device__ __forceinline__ int clip_count_f32(const double* __restrict__ r, cons
   return nr;
 }
 
-// Inverse of an element map in the plane for many query points: affine maps
-// by a 2x2 inverse, bilinear ones by FP32 Newton on coordinates scaled by a
-// power of two (error e0 ~ 1e-7 in xi), then one FP64 Newton step with the
-// FP64 residual and the FP64 Jacobian at the FP32 solution, whose 1 / det is
-// the FP32 iteration's reciprocal refined once in FP64 (relative error
-// ~1e-13): the step leaves ~1e-13 e0 + |c3|/|J| e0^2 ~ 1e-15 in xi, i.e.
-// rounding level.  The reverse sweep's Jacobian inverse at the converged xi
-// refines that step's 1 / det once more (~1e-14).  Conversions between FP32
-// and FP64 are integer operations (f32_trunc, f64_of_f32): a conversion
-// instruction with an FP64 operand issues on the FP64 pipe.
 // The FP32 Newton iteration's last Jacobian inverse of a bilinear map, in the
 // map's own (unscaled) units, and the FP32 reciprocal of its scaled
 // determinant.
@@ -212,6 +202,17 @@ struct CoarseInv {
   float idf;
 };
 
+// Inverse of an element map in the plane for many query points: affine maps
+// by a 2x2 inverse, bilinear ones by FP32 Newton on coordinates scaled by a
+// power of two (error e0 ~ 1e-7 in xi), then one Newton step with the FP64
+// residual and the FP32 iteration's last Jacobian inverse (relative error
+// d ~ 1e-7): the step leaves ~d e0 + |c3|/|J| e0^2 ~ 1e-14 in xi, the same
+// converged value as a full FP64 Newton to rounding.  The reverse sweep's
+// Jacobian inverse at the converged xi uses the FP64 Jacobian there, with
+// 1 / det one Newton-Raphson reciprocal step from the FP32 reciprocal
+// (~1e-14).  Conversions between FP32 and FP64 are integer operations
+// (f32_trunc, f64_of_f32): a conversion instruction with an FP64 operand
+// issues on the FP64 pipe.
 struct MapInverse {
   PlaneMap m;
   bool affine;

@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kMaxPairBlock) k_adjoint_pairs(
 //      dJ/dY_l |direct = -sum_c G[c][l] Lambda_c,  dJ/dX_b |direct = sum_c H[c][b] Lambda_c,
 //      dJ/dLambda_c = sum_b H[c][b] X_b - sum_l G[c][l] Y_l,  J = sum_c Lambda_c . dJ/dLambda_c;
 //  * element maps are inverted as in the batched integration kernel (affine
-//    2x2 inverse, or FP32 Newton + one FP64 Newton step), and the
+//    2x2 inverse, or FP32 Newton + one Newton step on the FP64 residual), and the
 //    implicit-function step applies the FP64 inverse Jacobian at the
 //    converged xi (MapInverse::jinvT);
 //  * the clip is recorded as a compact vertex pool (ClipPool);

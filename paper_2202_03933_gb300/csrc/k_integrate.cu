@@ -22,9 +22,9 @@
 //    integrates them in rounds of 32 lanes of similar cost.  Affine element
 //    maps are inverted with
 //    one precomputed 2x2 inverse; bilinear ones by Newton in FP32 on
-//    power-of-two-scaled coordinates, then one FP64 Newton step with an
-//    FP64 residual (the converged xi agrees with a full FP64 Newton to
-//    rounding; MapInverse in clip.cuh).
+//    power-of-two-scaled coordinates, then one Newton step with an FP64
+//    residual and the FP32 Jacobian inverse (the converged xi agrees with a
+//    full FP64 Newton to rounding; MapInverse in clip.cuh).
 //  * variant 1: one pair per thread, FP64 Newton from xi = 0 at every point
 //    (the oracle's iteration), kept as the reference schedule.
 //
